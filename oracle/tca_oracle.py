@@ -1,0 +1,232 @@
+"""CPU FP64 oracle for the separable tensor-operator solve.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+definition that the CUDA library is checked against.  Only the test suite,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it; the library itself never does, and this module imports nothing from the
+library (it takes plain NumPy arrays).
+
+Everything is NumPy float64.  Tensors are C-order arrays (last mode fastest),
+so with the mode product below  vec(X x_1 A_1 ... x_d A_d) = (A_1 kron ... kron A_d) vec(X).
+
+What each function follows in the paper (Morozov & Hunziker, "Solving Tensor
+Structured Problems with Computational Tensor Algebra"):
+
+* ``mode_product`` - tensor multiplication of a tensor by a one-dimensional
+  transformation acting on one index: outer product then contraction
+  (Sec. 2, Eq. first_product), restricted to one index pair.
+* ``apply`` / ``apply_T`` - the separable transformation as a chain of
+  one-dimensional transformations (Sec. 2.1, Eq. separable_transf), and its
+  transpose (App. "Tensor transposition": A^T A patterns are a change of
+  variance, i.e. each factor transposed).
+* ``regulariser`` - a sum of single-mode finite-difference filters, the same
+  structure as the separable Poisson operator of Sec. 4.1; the finite
+  difference is one of the separable building blocks of Table 1.
+* ``normal_apply`` - the normal-equations operator A^T A + lambda R obtained
+  from differentiating the least-squares functional (App. "Differentiation in
+  respect to a tensor", Eqs. A15-A17).  It is computed the long way, through
+  sample space, and never through per-mode Gram factors.
+* ``cg`` - the tensor conjugate-gradient iteration of Fig. 2, with the inner
+  product of App. "Inner product" (Eq. A14).
+* ``kron_matrix`` / ``dense_normal_matrix`` / ``direct_solve`` - the
+  equivalent matrix form of a tensor equation "with proper reshaping" (Sec. 3,
+  after Eq. TensorEq), solved by a direct (Cholesky) method - the direct-solver
+  class of Sec. 4.1.  For tiny cases only.
+
+Readings where the paper is silent or garbled (also listed in the design notes):
+* the CG loop condition in Fig. 2 is printed inverted; CG stops when the
+  relative recursive residual sqrt(rho) / ||rhs|| <= rtol;
+* the second-difference operator is the "valid" (n-2) x n matrix with rows
+  [1, -2, 1]; modes with n < 3 carry no regulariser;
+* the same lambda weights every mode.
+"""
+from __future__ import annotations
+
+import functools
+import itertools
+
+import numpy as np
+
+__all__ = [
+    "mode_product",
+    "apply",
+    "apply_T",
+    "second_difference",
+    "regulariser",
+    "normal_apply",
+    "inner",
+    "cg",
+    "solve",
+    "rel_residual",
+    "kron_matrix",
+    "dense_normal_matrix",
+    "direct_solve",
+    "CGResult",
+]
+
+
+def mode_product(x: np.ndarray, a: np.ndarray, k: int) -> np.ndarray:
+    """Y = X x_k A:  Y[..., j, ...] = sum_i A[j, i] X[..., i, ...] on index k.
+
+    Outer product of A with X followed by contraction of A's second index with
+    X's k-th index (Sec. 2, Eq. first_product for a single index pair).  The new
+    index takes the place of the contracted one (ordered spaces, Sec. 2.1).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    if a.shape[1] != x.shape[k]:
+        raise ValueError(f"factor {a.shape} does not match mode {k} of {x.shape}")
+    y = np.tensordot(a, x, axes=([1], [k]))  # new index first
+    return np.moveaxis(y, 0, k)
+
+
+def apply(x: np.ndarray, mats, order=None) -> np.ndarray:
+    """Separable transformation A x = X x_1 A_1 x_2 A_2 ... x_d A_d (Eq. separable_transf).
+
+    ``order`` is the sequence in which the one-dimensional transformations are
+    applied; by commutativity on ordered spaces (Sec. 2.1) any order gives the
+    same result.
+    """
+    y = np.asarray(x, dtype=np.float64)
+    for k in (range(len(mats)) if order is None else order):
+        y = mode_product(y, mats[k], k)
+    return y
+
+
+def apply_T(y: np.ndarray, mats, order=None) -> np.ndarray:
+    """Transpose A^T y = Y x_1 A_1^T ... x_d A_d^T (App. "Tensor transposition")."""
+    x = np.asarray(y, dtype=np.float64)
+    for k in (range(len(mats)) if order is None else order):
+        x = mode_product(x, np.asarray(mats[k], dtype=np.float64).T, k)
+    return x
+
+
+def second_difference(n: int) -> np.ndarray:
+    """(n-2) x n second-difference matrix with rows [1, -2, 1] (Table 1, finite difference)."""
+    d = np.zeros((max(n - 2, 0), n), dtype=np.float64)
+    for i in range(n - 2):
+        d[i, i] = 1.0
+        d[i, i + 1] = -2.0
+        d[i, i + 2] = 1.0
+    return d
+
+
+def regulariser(x: np.ndarray, lam: float) -> np.ndarray:
+    """lambda * sum_k X x_k (D2_k^T D2_k), skipping modes with n_k < 3.
+
+    A sum of single-mode filters, as in the separable Poisson operator (Sec. 4.1).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    for k, n in enumerate(x.shape):
+        if n < 3:
+            continue
+        d2 = second_difference(n)
+        out += mode_product(x, d2.T @ d2, k)
+    return lam * out
+
+
+def normal_apply(x: np.ndarray, mats, lam: float) -> np.ndarray:
+    """K x = A^T (A x) + lambda R x, the long way through sample space.
+
+    K is the normal-equations operator of the regularised least-squares
+    functional ||A x - b||^2 + lambda sum_k ||X x_k D2_k||^2 (App., Eqs. A15-A17).
+    """
+    return apply_T(apply(x, mats), mats) + regulariser(x, lam)
+
+
+def inner(a: np.ndarray, b: np.ndarray) -> float:
+    """<A, B> = sum of the elementwise product (App. "Inner product", Eq. A14)."""
+    return float(np.sum(np.asarray(a, np.float64) * np.asarray(b, np.float64)))
+
+
+class CGResult:
+    """Outcome of ``cg``: solution, iteration count and relative-residual history."""
+
+    def __init__(self, x, iters, history, converged):
+        self.x = x
+        self.iters = iters
+        self.history = history
+        self.converged = converged
+
+
+def cg(kop, rhs: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-10,
+       max_iter: int = 10000) -> CGResult:
+    """Tensor conjugate gradients of Fig. 2 for K x = rhs with SPD K.
+
+    Steps, in the figure's order and names (C is the solution, B the data):
+        R = B - K C;  P = R;  rho = <R, R>
+        repeat:  Q = K P;  alpha = rho / <P, Q>;  C = C + alpha P;
+                 R = R - alpha Q;  rho1 = <R, R>;  P = R + (rho1 / rho) P;  rho = rho1
+    stopping when sqrt(rho) / ||B|| <= rtol (the figure prints this test inverted).
+    """
+    b = np.asarray(rhs, dtype=np.float64)
+    c = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.sqrt(inner(b, b))
+    if bnorm == 0.0:
+        return CGResult(np.zeros_like(b), 0, [0.0], True)
+    r = b - kop(c)
+    p = r.copy()
+    rho = inner(r, r)
+    history = [np.sqrt(rho) / bnorm]
+    it = 0
+    while history[-1] > rtol and it < max_iter:
+        q = kop(p)
+        alpha = rho / inner(p, q)
+        c = c + alpha * p
+        r = r - alpha * q
+        rho1 = inner(r, r)
+        p = r + (rho1 / rho) * p
+        rho = rho1
+        it += 1
+        history.append(np.sqrt(rho) / bnorm)
+    return CGResult(c, it, history, history[-1] <= rtol)
+
+
+def solve(b: np.ndarray, mats, lam: float, rtol: float = 1e-10, max_iter: int = 10000,
+          x0: np.ndarray | None = None) -> CGResult:
+    """Solve (A^T A + lambda R) x = A^T b by the CG of Fig. 2, from x0 = 0 unless given."""
+    rhs = apply_T(b, mats)
+    return cg(lambda v: normal_apply(v, mats, lam), rhs, x0=x0, rtol=rtol, max_iter=max_iter)
+
+
+def rel_residual(x: np.ndarray, b: np.ndarray, mats, lam: float) -> float:
+    """True relative residual ||A^T b - K x|| / ||A^T b|| of the normal equations."""
+    rhs = apply_T(b, mats)
+    r = rhs - normal_apply(x, mats, lam)
+    return float(np.sqrt(inner(r, r)) / np.sqrt(inner(rhs, rhs)))
+
+
+def kron_matrix(mats) -> np.ndarray:
+    """Explicit matrix A_1 kron ... kron A_d of the separable operator (Sec. 3, matrix form)."""
+    return functools.reduce(np.kron, [np.asarray(a, np.float64) for a in mats])
+
+
+def dense_normal_matrix(mats, lam: float, shape) -> np.ndarray:
+    """Explicit K = A^T A + lambda sum_k (I kron .. D2_k^T D2_k .. kron I) for tiny cases."""
+    a = kron_matrix(mats)
+    k = a.T @ a
+    for mode, n in enumerate(shape):
+        if n < 3:
+            continue
+        d2 = second_difference(n)
+        parts = [np.eye(s) for s in shape]
+        parts[mode] = d2.T @ d2
+        k = k + lam * functools.reduce(np.kron, parts)
+    return k
+
+
+def direct_solve(b: np.ndarray, mats, lam: float, shape) -> np.ndarray:
+    """Direct solve of the reshaped normal equations by Cholesky (Sec. 4.1 direct solvers)."""
+    from scipy import linalg
+
+    a = kron_matrix(mats)
+    k = dense_normal_matrix(mats, lam, shape)
+    rhs = a.T @ np.asarray(b, np.float64).ravel()
+    x = linalg.cho_solve(linalg.cho_factor(k), rhs)
+    return x.reshape(shape)
+
+
+def all_mode_orders(d: int):
+    """Every order of the d one-dimensional transformations (for commutativity checks)."""
+    return list(itertools.permutations(range(d)))

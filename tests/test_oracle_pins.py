@@ -1,0 +1,327 @@
+"""Pins of the CPU oracle against what the mathematics fixes (no GPU).
+
+Each test ties an oracle function to something other than itself: a library
+routine (np.kron, scipy.fft.dct, scipy.ndimage.correlate1d, Cholesky, eigh,
+lstsq, scipy's B-spline basis), an exact closed form, an invariant, or a brute
+force written directly from the definition on a tiny input.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import fft as sfft
+from scipy import interpolate, linalg, ndimage
+
+from oracle import tca_oracle as O
+from paper_1001_5460_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_mats(rng, shape, sample_shape):
+    return [rng.standard_normal((m, n)) for m, n in zip(sample_shape, shape)]
+
+
+# --- mode product / separable transformation (Sec. 2.1, Eq. separable_transf) ---
+
+def test_apply_equals_kronecker_matvec():
+    """X x_1 A1 ... x_4 A4 equals (A1 kron A2 kron A3 kron A4) vec(X) for C-order vec (Sec. 3)."""
+    rng = np.random.default_rng(1)
+    shape, sshape = (3, 4, 5, 2), (4, 2, 6, 3)
+    x = rng.standard_normal(shape)
+    mats = _rand_mats(rng, shape, sshape)
+    big = mats[0]
+    for a in mats[1:]:
+        big = np.kron(big, a)  # library Kronecker product
+    ref = (big @ x.ravel()).reshape(sshape)
+    np.testing.assert_allclose(O.apply(x, mats), ref, rtol=1e-12, atol=1e-12)
+
+
+def test_apply_equals_bruteforce_sum():
+    """Direct elementwise sum of Eq. separable_transf on a tiny 3D tensor (no chaining)."""
+    rng = np.random.default_rng(2)
+    shape, sshape = (2, 3, 2), (3, 2, 4)
+    x = rng.standard_normal(shape)
+    a, b, c = _rand_mats(rng, shape, sshape)
+    ref = np.zeros(sshape)
+    for x1, y1, z1 in itertools.product(*map(range, sshape)):
+        s = 0.0
+        for xi, yi, zi in itertools.product(*map(range, shape)):
+            s += a[x1, xi] * b[y1, yi] * c[z1, zi] * x[xi, yi, zi]
+        ref[x1, y1, z1] = s
+    np.testing.assert_allclose(O.apply(x, [a, b, c]), ref, rtol=1e-12, atol=1e-13)
+
+
+def test_commutativity_all_orders():
+    """Every order of the one-dimensional transformations gives one result (Sec. 2.1)."""
+    rng = np.random.default_rng(3)
+    shape, sshape = (3, 4, 2, 5), (5, 3, 4, 2)
+    x = rng.standard_normal(shape)
+    mats = _rand_mats(rng, shape, sshape)
+    ref = O.apply(x, mats)
+    for order in O.all_mode_orders(4):
+        np.testing.assert_allclose(O.apply(x, mats, order=order), ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2, 3])
+def test_dct_factor_equals_library_dct(axis):
+    """A factor holding the orthonormal DCT-II matrix equals scipy's DCT along that axis (Table 1)."""
+    rng = np.random.default_rng(4 + axis)
+    shape = (5, 6, 7, 4)
+    x = rng.standard_normal(shape)
+    n = shape[axis]
+    k = np.arange(n)[:, None]
+    i = np.arange(n)[None, :]
+    c = np.cos(np.pi * k * (2 * i + 1) / (2 * n)) * np.sqrt(2.0 / n)
+    c[0, :] = np.sqrt(1.0 / n)
+    ref = sfft.dct(x, type=2, norm="ortho", axis=axis)
+    np.testing.assert_allclose(O.mode_product(x, c, axis), ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_fir_factor_equals_correlate1d(axis):
+    """A banded Toeplitz factor equals 1D correlation with zero boundary (Table 1, convolution)."""
+    rng = np.random.default_rng(10 + axis)
+    shape = (9, 8, 11)
+    x = rng.standard_normal(shape)
+    w = rng.standard_normal(5)
+    n = shape[axis]
+    a = np.zeros((n, n))
+    for row in range(n):
+        for d in range(-2, 3):
+            if 0 <= row + d < n:
+                a[row, row + d] = w[d + 2]
+    ref = ndimage.correlate1d(x, w, axis=axis, mode="constant", cval=0.0)
+    np.testing.assert_allclose(O.mode_product(x, a, axis), ref, rtol=1e-12, atol=1e-12)
+
+
+def test_adjointness():
+    """<A x, y> = <x, A^T y> (App. "Tensor transposition")."""
+    rng = np.random.default_rng(5)
+    shape, sshape = (4, 3, 5, 2), (6, 5, 7, 3)
+    mats = _rand_mats(rng, shape, sshape)
+    x = rng.standard_normal(shape)
+    y = rng.standard_normal(sshape)
+    lhs = O.inner(O.apply(x, mats), y)
+    rhs = O.inner(x, O.apply_T(y, mats))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_inner_product_definition():
+    """<A, B> is the full contraction of matching indices (Eq. A13) = vdot of the flattened arrays."""
+    rng = np.random.default_rng(6)
+    a = rng.standard_normal((3, 4, 5))
+    b = rng.standard_normal((3, 4, 5))
+    assert O.inner(a, b) == pytest.approx(np.vdot(a.ravel(), b.ravel()), rel=1e-13)
+
+
+# --- regulariser and normal operator ---
+
+def test_second_difference_equals_numpy_diff():
+    rng = np.random.default_rng(7)
+    for n in (3, 4, 9):
+        v = rng.standard_normal(n)
+        np.testing.assert_allclose(O.second_difference(n) @ v, np.diff(v, n=2), rtol=0, atol=1e-14)
+    # Null space of D2^T D2: constant and linear sequences.
+    n = 12
+    d2 = O.second_difference(n)
+    l = d2.T @ d2
+    np.testing.assert_allclose(l @ np.ones(n), 0.0, atol=1e-13)
+    np.testing.assert_allclose(l @ np.arange(n, dtype=float), 0.0, atol=1e-12)
+    # A quadratic has constant second difference 2.
+    t = np.arange(n, dtype=float)
+    np.testing.assert_allclose(d2 @ (t * t), 2.0, atol=1e-12)
+
+
+def test_normal_operator_equals_dense_matrix():
+    """K x the long way equals the explicit reshaped normal matrix (Sec. 3) on a tiny B-spline case."""
+    inst = synth.instance_bspline((6, 5, 7, 4), seed=11, lam=0.3, with_truth=False)
+    mats = [f.dense() for f in inst.factors]
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(inst.shape)
+    k = O.dense_normal_matrix(mats, 0.3, inst.shape)
+    np.testing.assert_allclose(O.normal_apply(x, mats, 0.3).ravel(), k @ x.ravel(), rtol=1e-11, atol=1e-11)
+    # Symmetric positive definite.
+    np.testing.assert_allclose(k, k.T, atol=1e-12)
+    assert np.linalg.eigvalsh(k).min() > 0.0
+
+
+def test_normal_operator_symmetry_random():
+    inst = synth.instance_bspline((7, 6, 5), seed=12, lam=1e-2, with_truth=False)
+    mats = [f.dense() for f in inst.factors]
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(inst.shape)
+    y = rng.standard_normal(inst.shape)
+    a = O.inner(O.normal_apply(x, mats, 1e-2), y)
+    b = O.inner(x, O.normal_apply(y, mats, 1e-2))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert O.inner(O.normal_apply(x, mats, 1e-2), x) > 0
+
+
+# --- CG of Fig. 2 ---
+
+@pytest.mark.slow
+def test_cg_matches_cholesky_dense_3d():
+    """Dense 16^3 problem with 24x16 Gaussian factors: CG to 1e-10 vs Cholesky of the reshaped system."""
+    inst = synth.instance_dense_3d(seed=0)
+    mats = [f.dense() for f in inst.factors]
+    b = O.apply(inst.x_true, mats) + inst.noise
+    res = O.solve(b, mats, inst.lam, rtol=1e-10)
+    assert res.converged
+    x_direct = O.direct_solve(b, mats, inst.lam, inst.shape)
+    err = np.linalg.norm(res.x - x_direct) / np.linalg.norm(x_direct)
+    assert err < 1e-8, err
+    assert O.rel_residual(res.x, b, mats, inst.lam) < 1e-9
+
+
+def test_cg_matches_cholesky_small_bspline():
+    inst = synth.instance_bspline((8, 7, 6, 4), seed=13, lam=1e-3, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = O.apply(inst.x_true, mats) + inst.noise
+    res = O.solve(b, mats, inst.lam, rtol=1e-12)
+    x_direct = O.direct_solve(b, mats, inst.lam, inst.shape)
+    err = np.linalg.norm(res.x - x_direct) / np.linalg.norm(x_direct)
+    assert err < 1e-9, err
+
+
+def test_lambda_zero_closed_form():
+    """lambda = 0: the normal-equation solution is b x_k pinv(A_k) on every mode (least squares)."""
+    rng = np.random.default_rng(14)
+    shape, sshape = (5, 4, 6), (8, 7, 9)
+    mats = _rand_mats(rng, shape, sshape)
+    b = rng.standard_normal(sshape)
+    res = O.solve(b, mats, 0.0, rtol=1e-13, max_iter=5000)
+    ref = b
+    for k, a in enumerate(mats):
+        ref = np.moveaxis(np.tensordot(np.linalg.pinv(a), ref, axes=([1], [k])), 0, k)
+    np.testing.assert_allclose(res.x, ref, rtol=1e-9, atol=1e-10)
+
+
+def test_identity_factors_kronecker_sum_eigensolve():
+    """A_k = I: K = I + lambda sum_k L_k is solved exactly in the eigenbasis of each L_k."""
+    rng = np.random.default_rng(15)
+    shape = (7, 5, 6, 3)
+    lam = 0.37
+    mats = [np.eye(n) for n in shape]
+    b = rng.standard_normal(shape)
+    res = O.solve(b, mats, lam, rtol=1e-13)
+    # Exact solve: rotate into each L_k's eigenbasis, divide, rotate back.
+    evals, evecs = [], []
+    for n in shape:
+        d2 = np.diff(np.eye(n), n=2, axis=0)  # library second difference
+        mu, v = linalg.eigh(d2.T @ d2)
+        evals.append(mu)
+        evecs.append(v)
+    xh = b
+    for k, v in enumerate(evecs):
+        xh = np.moveaxis(np.tensordot(v.T, xh, axes=([1], [k])), 0, k)
+    denom = np.ones(shape)
+    for k, mu in enumerate(evals):
+        sh = [1] * len(shape)
+        sh[k] = shape[k]
+        denom = denom + lam * mu.reshape(sh)
+    xh = xh / denom
+    for k, v in enumerate(evecs):
+        xh = np.moveaxis(np.tensordot(v, xh, axes=([1], [k])), 0, k)
+    np.testing.assert_allclose(res.x, xh, rtol=1e-10, atol=1e-11)
+
+
+def test_cg_zero_rhs_and_x0():
+    mats = [np.eye(3), np.eye(4)]
+    r = O.solve(np.zeros((3, 4)), mats, 0.1)
+    assert r.iters == 0 and np.all(r.x == 0)
+    # Starting from the exact solution needs no iteration.
+    rng = np.random.default_rng(16)
+    b = rng.standard_normal((3, 4))
+    exact = O.solve(b, mats, 0.1, rtol=1e-14).x
+    r2 = O.solve(b, mats, 0.1, rtol=1e-8, x0=exact)
+    assert r2.iters == 0
+
+
+# --- B-spline factors (inputs of the spline reconstruction, Sec. 5) ---
+
+def test_bspline3_golden_values():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "bspline3_values.txt")) if l.strip() and not l.startswith("#")]
+    for u, num, den in rows:
+        assert synth.bspline3(float(u)) == pytest.approx(int(num) / int(den), abs=1e-15)
+
+
+def test_bspline3_equals_scipy_basis():
+    basis = interpolate.BSpline.basis_element([-2.0, -1.0, 0.0, 1.0, 2.0], extrapolate=False)
+    u = np.linspace(-1.999, 1.999, 401)
+    np.testing.assert_allclose(synth.bspline3(u), basis(u), rtol=1e-12, atol=1e-14)
+
+
+def test_bspline_factor_partition_of_unity_and_band():
+    rng = np.random.default_rng(17)
+    n, m = 40, 60
+    col0, w, t = synth.bspline_factor_ell4(n, m, rng)
+    a = synth.ell4_to_dense(col0, w, n)
+    interior = (t >= 1.0) & (t <= n - 2.0)
+    np.testing.assert_allclose(a[interior].sum(axis=1), 1.0, atol=1e-14)
+    assert np.all(np.diff(t) > 0)
+    # At most 4 nonzeros per row, contiguous.
+    assert (np.count_nonzero(a, axis=1) <= 4).all()
+    # Gram of a 4-wide band is 7-banded.
+    g = a.T @ a
+    i, j = np.nonzero(np.abs(g) > 0)
+    assert np.max(np.abs(i - j)) <= 3
+
+
+def test_bspline_positions_at_integers():
+    """Row of a sample sitting on grid point j reads [1/6, 2/3, 1/6] at j-1, j, j+1."""
+    t = np.array([3.0, 7.0])
+    col0 = (np.floor(t) - 1).astype(np.int32)
+    cols = col0[:, None] + np.arange(4)
+    w = synth.bspline3(t[:, None] - cols)
+    np.testing.assert_allclose(w, [[1 / 6, 2 / 3, 1 / 6, 0.0]] * 2, atol=1e-15)
+
+
+# --- the pins catch planted mistakes in the oracle (mutation checks, CPU only) ---
+
+def test_pin_catches_transposed_factor(monkeypatch):
+    rng = np.random.default_rng(18)
+    shape = (3, 3, 3)
+    mats = [rng.standard_normal((3, 3)) for _ in range(3)]
+    x = rng.standard_normal(shape)
+    good = O.apply(x, mats)
+    orig = O.mode_product
+    monkeypatch.setattr(O, "mode_product", lambda x_, a, k: orig(x_, np.asarray(a).T, k))
+    bad = O.apply(x, mats)
+    big = np.kron(np.kron(mats[0], mats[1]), mats[2])
+    ref = (big @ x.ravel()).reshape(shape)
+    assert np.allclose(good, ref) and not np.allclose(bad, ref)
+
+
+def test_pin_catches_dropped_regulariser_term(monkeypatch):
+    shape = (5, 4, 6)
+    lam = 0.5
+    mats = [np.eye(n) for n in shape]
+    rng = np.random.default_rng(19)
+    x = rng.standard_normal(shape)
+    k = O.dense_normal_matrix(mats, lam, shape)
+    assert np.allclose(O.normal_apply(x, mats, lam).ravel(), k @ x.ravel())
+    monkeypatch.setattr(O, "regulariser", lambda v, l: l * O.mode_product(v, O.second_difference(v.shape[0]).T @ O.second_difference(v.shape[0]), 0))
+    assert not np.allclose(O.normal_apply(x, mats, lam).ravel(), k @ x.ravel())
+
+
+def test_pin_catches_wrong_cg_sign():
+    """A CG with the residual update sign flipped stops matching the direct solve."""
+    rng = np.random.default_rng(20)
+    shape = (4, 5)
+    mats = [rng.standard_normal((6, 4)), rng.standard_normal((7, 5))]
+    b = rng.standard_normal((6, 7))
+    lam = 0.1
+    kop = lambda v: O.normal_apply(v, mats, lam)
+    rhs = O.apply_T(b, mats)
+    ref = O.direct_solve(b, mats, lam, shape)
+    good = O.cg(kop, rhs, rtol=1e-12).x
+    assert np.allclose(good, ref, rtol=1e-8, atol=1e-10)
+    # Planted mistake: R = R + alpha Q.
+    c = np.zeros(shape); r = rhs.copy(); p = r.copy(); rho = O.inner(r, r)
+    for _ in range(50):
+        q = kop(p); alpha = rho / O.inner(p, q); c = c + alpha * p; r = r + alpha * q
+        rho1 = O.inner(r, r); p = r + (rho1 / rho) * p; rho = rho1
+    assert not np.allclose(c, ref, rtol=1e-4)
