@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the separable tensor-operator solve on one GB300 (or N replicas).
+
+Workload (the paper's 4D spline reconstruction at its scale, Sec. 5): unknowns
+160x160x160x8 (32.8M), cubic B-spline collocation factors on a 240^3 x 12
+jittered sample grid, lambda = 1e-3 second-difference regulariser, synthetic
+smooth ground truth plus N(0, 0.01^2) noise.  A step is one full solve of
+(A^T A + lambda R) x = A^T b to a true relative residual of 1e-6 (A^T b, the
+CG iterations and the FP64 true-residual check), with b resident in HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle
+on the machine's host cores instead (bounded sample, extrapolated; see below).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution at 1e-6 rel. residual, 33M-unknown 4D; mode-sweep HBM GB/s"
+SHAPE = (160, 160, 160, 8)
+SEED = 2
+LAM = 1e-3
+RTOL = 1e-6
+SUBVOL = (40, 40, 40, 8)  # iteration-count probe for the oracle arm (same generator)
+WORKLOAD = ("bspline4d: unknowns 160x160x160x8 (32.8M) FP32, cubic B-spline factors on 240x240x240x12 "
+            "jittered samples, lambda 1e-3, noise 0.01, CG to true rel. residual 1e-6")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        self.idx = gpu_index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        loaded = [v for v in sm if mx and v >= 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_problem(shape, seed, device):
+    import torch
+
+    from paper_1001_5460_gb300 import synth, tca
+
+    inst = synth.instance_bspline(shape, seed=seed, lam=LAM, dtype=np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    xt = torch.from_numpy(inst.x_true).to(device)
+    b = torch.empty(inst.sample_shape, dtype=torch.float32, device=device)
+    plan.apply(xt, b)  # b = A x_true on the device, then the measurement noise
+    b += torch.from_numpy(inst.noise).to(device)
+    torch.cuda.synchronize()
+    del xt
+    return inst, plan, b
+
+
+def time_sweeps(plan, inst, device, reps=20):
+    """Standalone sweep timings (CUDA events on the launching stream)."""
+    import torch
+
+    from paper_1001_5460_gb300 import tca
+
+    N = int(np.prod(inst.shape))
+    x = torch.randn(inst.shape, dtype=torch.float32, device=device)
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream()
+    out = {}
+
+    def timed(fn, nbytes):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return {"ms": round(ms, 5), "gbs": round(nbytes / ms / 1e6, 1)}
+
+    out["normal_fused"] = timed(lambda: plan.apply_normal(x, y), 2 * N * 4)
+    for k in range(len(inst.shape)):
+        out[f"gram_mode{k + 1}"] = timed(lambda k=k: plan.apply_mode(k, tca.OP_GRAM, inst.shape, x, y), 2 * N * 4)
+    # collocation sweep on mode 1 (n -> 1.5 n): reads N, writes 1.5 N
+    big = torch.empty((inst.factors[0].m,) + tuple(inst.shape[1:]), dtype=torch.float32, device=device)
+    out["collocation_mode1"] = timed(lambda: plan.apply_mode(0, tca.OP_FACTOR, inst.shape, x, big),
+                                     (N + big.numel()) * 4)
+    del big, x, y
+    return out
+
+
+def oracle_sample(inst, b_host, iters, nthreads):
+    """Bounded oracle sample on the full problem: A^T b once and one application of
+    K (the long way); time-to-solution = t(A^T b) + (iters + 1) * t(K)."""
+    from oracle import tca_oracle as O
+
+    mats = [f.dense() for f in inst.factors]
+    t0 = time.perf_counter()
+    rhs = O.apply_T(b_host, mats)
+    t1 = time.perf_counter()
+    O.normal_apply(rhs, mats, inst.lam)
+    t2 = time.perf_counter()
+    t_rhs, t_k = t1 - t0, t2 - t1
+    return {"value_ms": 1e3 * (t_rhs + (iters + 1) * t_k), "t_rhs_s": t_rhs, "t_k_s": t_k,
+            "cores": nthreads}
+
+
+def oracle_iterations(seed):
+    """Iterations the oracle's CG needs on the 40x40x40x8 instance of the same generator."""
+    from oracle import tca_oracle as O
+    from paper_1001_5460_gb300 import synth
+
+    inst = synth.instance_bspline(SUBVOL, seed=seed, lam=LAM, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = O.apply(inst.x_true, mats) + inst.noise
+    return O.solve(b, mats, inst.lam, rtol=RTOL).iters
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1001_5460_gb300 import synth
+    from oracle import tca_oracle as O
+
+    inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, dtype=np.float32)
+    mats = [f.dense() for f in inst.factors]
+    b = O.apply(inst.x_true, mats) + inst.noise.astype(np.float64)
+    iters = oracle_iterations(SEED)
+    nthreads = os.cpu_count()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(inst, b, iters, nthreads)
+        if i >= args.warmup:
+            vals.append(r["value_ms"])
+    v = statistics.mean(vals)
+    sample = (f"per step: A^T b and one normal-operator application of the FP64 oracle on the full "
+              f"160x160x160x8 problem, extrapolated as t(A^T b) + (iters+1) t(K) with iters={iters} "
+              f"(oracle CG on the 40x40x40x8 instance of the same generator)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(v, 3), "unit": "ms", "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_tca(args, rank, world, local):
+    import torch
+
+    from paper_1001_5460_gb300 import tca
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    shape = (64, 64, 64, 8) if args.small else SHAPE
+    inst, plan, b = make_problem(shape, SEED + rank, device)
+    N = int(np.prod(shape))
+    M = int(np.prod(inst.sample_shape))
+    x = torch.zeros(shape, dtype=torch.float32, device=device)
+    s = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 0)):
+        st, info = plan.solve(b, x, rtol=RTOL, profile=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    tca.kernel_launches(reset=True)
+    times, sweep_ms, sweep_n, infos = [], 0.0, 0, []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            st, info = plan.solve(b, x, rtol=RTOL, profile=True)
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            sweep_ms += info["sweep_ms"]
+            sweep_n += info["sweep_launches"]
+            infos.append(info)
+        launches = tca.kernel_launches()
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(statistics.mean(times), world)
+
+    # End to end through the public API with host (pinned) buffers.
+    b_host = b.cpu().pin_memory()
+    x_host = torch.zeros(shape, dtype=torch.float32).pin_memory()
+    plan.solve(b_host, x_host, rtol=RTOL)
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t0 = time.perf_counter()
+        plan.solve(b_host, x_host, rtol=RTOL)
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms = max_over_ranks(statistics.mean(e2e), world)
+
+    sweeps = time_sweeps(plan, inst, device)
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    k2_ms = sweep_ms / max(sweep_n, 1)
+    k2_bytes = 4 * N * 4  # CG sweep: reads r and p_old, writes p_new and q (FP32)
+    achieved = k2_bytes / k2_ms / 1e6
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.small else "small 64x64x64x8 check run",
+                   "precision": "plain FP32 CG, FP64 scalars and FP64 true residual",
+                   "cg_iters": last["iters"], "restarts": last["refinements"],
+                   "rel_res_true": last["rel_res_true"],
+                   "l2": "inputs larger than L2 (b 664 MB, 5 FP32 vectors of 131 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "fused normal-operator CG sweep (p = r + beta p; q = K p; <p,q>)",
+                     "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                     "peak_source": peak_src, "avg_launch_ms": round(k2_ms, 5),
+                     "algorithmic_bytes": k2_bytes, "launches": sweep_n},
+        "sweeps": sweeps,
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": M * 4, "d2h_bytes_per_step": N * 4},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline and not args.small:
+        r = oracle_sample(inst, b.cpu().numpy().astype(np.float64), last["iters"], os.cpu_count())
+        line["cpu_baseline"] = {
+            "value": round(r["value_ms"], 1), "unit": "ms", "cores": r["cores"], "kind": "oracle",
+            "sample": (f"A^T b ({r['t_rhs_s']:.2f} s) and one normal-operator application "
+                       f"({r['t_k_s']:.2f} s) of the FP64 oracle on the full problem, scaled to the GPU's "
+                       f"{last['iters']} CG iterations + 1 residual check")}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_tca(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * tca.h - C ABI of the GB300 separable tensor-operator solver.
+ *
+ * The library computes with tensors on ordered vector spaces as in Morozov &
+ * Hunziker, "Solving Tensor Structured Problems with Computational Tensor
+ * Algebra":
+ *   - a tensor is a dense array of components on an ordered set of spaces
+ *     (Sec. 2, Sec. 2.1; App. "Tensor notation");
+ *   - the system tensor is separable, A = A_1 . A_2 . A_3 (. A_4): one
+ *     one-dimensional transformation per space, applied as chained mode
+ *     products in any order (Sec. 2.1, Eq. separable_transf and the
+ *     commutativity statement that follows it);
+ *   - the tensor equation A . U = B (Sec. 3, Eq. TensorEq) is solved in the
+ *     least-squares sense through the normal equations
+ *     (A^T A + lambda R) x = A^T b (App. "Tensor transposition", App.
+ *     "Differentiation in respect to a tensor", Eqs. A15-A17) by the tensor
+ *     conjugate gradient of Sec. 4.1, Fig. 2.
+ *
+ * Layout.  Every tensor is a dense C-order array (last mode fastest).  An
+ * order-d unknown tensor has shape n[0..d-1]; the data (sample) tensor has
+ * shape m[0..d-1], where m[k] is the row count of factor k.  With this layout
+ * vec(X x_1 A_1 ... x_d A_d) = (A_1 kron ... kron A_d) vec(X).
+ *
+ * Element type.  Data buffers hold double for a TCA_F64 plan and float for
+ * every other precision.
+ *
+ * Pointers.  Data pointers passed to tca_apply, tca_apply_T, tca_apply_normal,
+ * tca_apply_mode and tca_solve may be device pointers (cudaMalloc, torch) or
+ * host pointers (pageable or pinned).  Host buffers are staged through the
+ * plan's own device buffers on the given stream, and the call then returns
+ * only after the result is back in host memory.  Device-pointer calls are
+ * asynchronous on the stream, except tca_solve, which synchronises the stream
+ * to fill its info record.
+ *
+ * Ownership.  The caller owns every data buffer.  tca_plan copies the factors
+ * it is given (host memory) and owns its device copies and workspace;
+ * tca_destroy frees them.  A plan may be used by one stream at a time.
+ *
+ * Errors.  No call aborts or throws across this boundary: every failure comes
+ * back as a tca_status.  A CUDA error is reported as TCA_ERR_CUDA and
+ * tca_last_error_string() gives the CUDA message.  Device-side waits are
+ * bounded and end in TCA_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef TCA_H
+#define TCA_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define TCA_API __attribute__((visibility("default")))
+#else
+#define TCA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TCA_OK = 0,
+  TCA_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, negative size */
+  TCA_ERR_SHAPE = 2,         /* factor or tensor shapes do not match */
+  TCA_ERR_UNSUPPORTED = 3,   /* valid request this build does not implement */
+  TCA_ERR_ALLOC = 4,         /* device allocation failed */
+  TCA_ERR_CUDA = 5,          /* a CUDA runtime/driver call failed */
+  TCA_ERR_NOT_CONVERGED = 6, /* solve hit max_iter; x holds the last iterate */
+  TCA_ERR_BREAKDOWN = 7,     /* CG met <p, Kp> <= 0 or a non-finite scalar */
+  TCA_ERR_TIMEOUT = 8        /* a bounded device wait gave up */
+} tca_status;
+
+/* Arithmetic of a plan.  TCA_F64: double data, double arithmetic.  TCA_F32:
+ * float data and arithmetic, inner products accumulated to double.  The _IR
+ * forms keep float data at the boundary; the inner CG runs with reduced
+ * precision operands (bf16 vector storage, or tf32 tensor-core products for
+ * dense factors) and iterative refinement restores the accuracy from an FP64
+ * residual. */
+typedef enum { TCA_F64 = 0, TCA_F32 = 1, TCA_BF16_IR = 2, TCA_TF32_IR = 3 } tca_precision;
+
+typedef enum {
+  TCA_FACTOR_DENSE = 0, /* values: m*n doubles, row-major A[i][j] */
+  TCA_FACTOR_ELL4 = 1   /* values: m*4 doubles, col0: m int32; row i holds
+                           A[i][col0[i]+c] = values[4*i+c], c = 0..3.  Columns
+                           outside [0, n) are ignored.  col0 must be
+                           non-decreasing in i. */
+} tca_factor_kind;
+
+/* One mode's one-dimensional transformation A_k (m x n), in host memory. */
+typedef struct {
+  int32_t kind;          /* tca_factor_kind */
+  int32_t reserved;      /* must be 0 */
+  int64_t m;             /* rows: samples along this mode */
+  int64_t n;             /* columns: unknowns along this mode */
+  const double* values;  /* host */
+  const int32_t* col0;   /* host, ELL4 only (NULL for DENSE) */
+} tca_factor;
+
+/* Regulariser lambda * sum_k (I x .. x D2_k^T D2_k x .. x I) with D2_k the
+ * (n_k-2) x n_k second difference; a mode takes part when its bit is set in
+ * reg_mode_mask and n_k >= 3.  This is a sum of single-mode finite-difference
+ * filters, the structure of the separable Poisson operator of Sec. 4.1. */
+typedef struct {
+  double lambda;
+  uint32_t reg_mode_mask;
+  uint32_t reserved;
+} tca_reg;
+
+typedef struct tca_plan_s* tca_plan_t;
+
+/* Build a plan: define the ordered spaces (sizes n[0..order-1], as with
+ * World.DefineSpace in Sec. 4.1, Fig. 1c) and the separable system tensor
+ * (Eq. separable_transf).  Copies the factors to the device, forms each
+ * mode's Gram factor G_k = A_k^T A_k in FP64 on the device (7-banded for ELL4
+ * factors, dense otherwise; the mixed-product property makes
+ * A^T A = G_1 kron .. kron G_d) and the regulariser bands, picks the mode
+ * order of apply / apply_T by cost (Sec. 2.1: reorder commuting products to
+ * minimise work and intermediate storage) and allocates the workspace.
+ * order: 3 or 4.  Returns TCA_ERR_SHAPE if factor k's n differs from n[k].
+ * The stream orders the set-up copies and kernels; tca_plan synchronises it. */
+TCA_API tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, const tca_factor* factors,
+                    const tca_reg* reg, tca_precision prec, cudaStream_t stream);
+
+/* y = A x = X x_1 A_1 ... x_d A_d (Sec. 2.1, Eq. separable_transf).
+ * x: n-shaped, y: m-shaped, both C-order, element type of the plan. */
+TCA_API tca_status tca_apply(tca_plan_t plan, const void* x, void* y, cudaStream_t stream);
+
+/* x = A^T y = Y x_1 A_1^T ... x_d A_d^T (App. "Tensor transposition").
+ * y: m-shaped, x: n-shaped. */
+TCA_API tca_status tca_apply_T(tca_plan_t plan, const void* y, void* x, cudaStream_t stream);
+
+/* y = (A^T A + lambda R) x, the normal operator of the regularised
+ * least-squares problem (App. Eqs. A15-A17), evaluated matrix-free as
+ * (G_1 kron .. kron G_d) x + lambda R x - the "iterative application of the
+ * tensor multiplication" each CG step performs (Sec. 4.1, Fig. 2, Q = A.P).
+ * x and y: n-shaped, must not alias. */
+TCA_API tca_status tca_apply_normal(tca_plan_t plan, const void* x, void* y, cudaStream_t stream);
+
+/* One mode product of the plan's operator on mode k (0-based) - a single
+ * one-dimensional transformation of Eq. separable_transf:
+ *   op TCA_OP_FACTOR:   y = x x_k A_k     (x has n_k on mode k, y has m_k)
+ *   op TCA_OP_FACTOR_T: y = x x_k A_k^T   (x has m_k on mode k, y has n_k)
+ *   op TCA_OP_GRAM:     y = x x_k G_k     (n_k -> n_k)
+ * dims[0..order-1] is the shape of x (other modes may hold either n or m
+ * sizes).  x and y must not alias. */
+typedef enum { TCA_OP_FACTOR = 0, TCA_OP_FACTOR_T = 1, TCA_OP_GRAM = 2 } tca_mode_op;
+TCA_API tca_status tca_apply_mode(tca_plan_t plan, int mode, int op, const int64_t* dims, const void* x,
+                          void* y, cudaStream_t stream);
+
+typedef struct {
+  double rtol;          /* stop at ||A^T b - K x|| / ||A^T b|| <= rtol (true residual) */
+  int32_t max_iter;     /* cap on CG iterations, all restarts and refinements counted */
+  int32_t x0_given;     /* 1: x holds the initial guess; 0: start from x = 0 */
+  double inner_rtol;    /* _IR plans: relative tolerance of each inner solve (0: default 1e-3) */
+  int32_t max_refine;   /* _IR plans: cap on refinement steps (0: default 30) */
+  int32_t check_every;  /* iterations between host convergence reads (0: default 16) */
+  int32_t profile;      /* 1: time every normal-operator sweep with CUDA events (info->sweep_*) */
+} tca_solve_opts;
+
+typedef struct {
+  int32_t iters;             /* CG iterations run (all inner solves summed) */
+  int32_t refinements;       /* outer refinement steps / true-residual restarts */
+  double rel_res_true;       /* FP64 ||A^T b - K x|| / ||A^T b|| at exit */
+  double rel_res_recursive;  /* sqrt(rho) / ||A^T b|| of the last CG step */
+  double seconds;            /* wall time of the call (host clock) */
+  double sweep_ms;           /* profile: device time summed over the CG normal-operator sweeps */
+  int32_t sweep_launches;    /* profile: sweeps that did work (one per CG iteration) */
+  int32_t reserved;
+} tca_solve_info;
+
+/* Solve (A^T A + lambda R) x = A^T b by the tensor CG of Sec. 4.1, Fig. 2:
+ * R = B - A.C, P = R, rho = <R,R>; repeat Q = A.P, alpha = rho/<P,Q>,
+ * C += alpha P, R -= alpha Q, rho1 = <R,R>, P = R + (rho1/rho) P.  The
+ * iteration stops when the recursive residual reaches rtol; the FP64 true
+ * residual is then recomputed and, if it is still above rtol, CG restarts
+ * from the current x.  b: m-shaped data, x: n-shaped solution (in: initial
+ * guess when opts->x0_given).  Scalars alpha, beta and all inner products are
+ * kept in FP64 on the device; the host reads the convergence flag every
+ * check_every iterations.  Returns TCA_ERR_NOT_CONVERGED (x and info still
+ * filled) when max_iter is reached, TCA_ERR_BREAKDOWN when <P, Q> <= 0 or a
+ * scalar is not finite.  info may be NULL.  Synchronises the stream. */
+TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
+                     tca_solve_info* info, cudaStream_t stream);
+
+/* Free a plan and its device memory (NULL is ignored). */
+TCA_API void tca_destroy(tca_plan_t plan);
+
+/* Static text for a status code. */
+TCA_API const char* tca_status_string(tca_status status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+TCA_API const char* tca_last_error_string(void);
+
+/* Number of the library's own kernels launched by this thread since the last
+ * reset (counts every launch, including those replayed from CUDA graphs). */
+TCA_API uint64_t tca_kernel_launches(int reset);
+
+/* ABI version, (major << 16) | minor. */
+TCA_API int tca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCA_H */

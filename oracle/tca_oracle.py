@@ -227,6 +227,45 @@ def direct_solve(b: np.ndarray, mats, lam: float, shape) -> np.ndarray:
     return x.reshape(shape)
 
 
+def _support(a: np.ndarray, rows=None, cols=None):
+    """Nonzero columns of the given rows (or nonzero rows of the given columns) of a."""
+    a = np.asarray(a, np.float64)
+    if rows is not None:
+        return np.nonzero(np.any(a[rows, :] != 0.0, axis=0))[0]
+    return np.nonzero(np.any(a[:, cols] != 0.0, axis=1))[0]
+
+
+def apply_at(x: np.ndarray, mats, s_idx) -> float:
+    """(A x)[s] for one sample multi-index s, from Eq. separable_transf restricted
+    to the columns the rows s_k touch (all other terms are exact zeros)."""
+    cols = [_support(a, rows=[sk]) for a, sk in zip(mats, s_idx)]
+    blk = np.asarray(x, np.float64)[np.ix_(*cols)]
+    rows = [np.asarray(a, np.float64)[[sk]][:, c] for a, sk, c in zip(mats, s_idx, cols)]
+    return float(apply(blk, rows).reshape(()))
+
+
+def normal_apply_at(x: np.ndarray, mats, lam: float, idx) -> float:
+    """(K x)[i] for one unknown multi-index i, the long way through sample space:
+    (A^T A x)[i] = sum_s (kron_k A_k[s_k, i_k]) (A x)[s] over the samples s whose
+    rows touch i, plus lambda sum_k (x x_k D2_k^T D2_k)[i]."""
+    x = np.asarray(x, np.float64)
+    srows = [_support(a, cols=[ik]) for a, ik in zip(mats, idx)]          # samples touching i
+    ccols = [_support(a, rows=sr) for a, sr in zip(mats, srows)]          # columns those samples read
+    blk = x[np.ix_(*ccols)]
+    sub = [np.asarray(a, np.float64)[np.ix_(sr, cc)] for a, sr, cc in zip(mats, srows, ccols)]
+    ax = apply(blk, sub)                                                  # (A x) on the touching samples
+    wi = [np.asarray(a, np.float64)[sr, ik][None, :] for a, sr, ik in zip(mats, srows, idx)]
+    val = float(apply(ax, wi).reshape(()))                                # contract with A_k[s_k, i_k]
+    for k, n in enumerate(x.shape):
+        if n < 3:
+            continue
+        d2 = second_difference(n)
+        row = (d2.T @ d2)[idx[k]]
+        line = x[tuple(idx[:k]) + (slice(None),) + tuple(idx[k + 1:])]
+        val += lam * float(row @ line)
+    return val
+
+
 def all_mode_orders(d: int):
     """Every order of the d one-dimensional transformations (for commutativity checks)."""
     return list(itertools.permutations(range(d)))

@@ -1,0 +1,450 @@
+// Tensor conjugate gradients (Sec. 4.1, Fig. 2) on the normal equations
+// (A^T A + lambda R) x = A^T b, with every scalar kept on the device in FP64:
+//   R = B - K C;  P = R;  rho = <R,R>
+//   repeat  Q = K P;  alpha = rho/<P,Q>;  C += alpha P;  R -= alpha Q;
+//           rho1 = <R,R>;  P = R + (rho1/rho) P;  rho = rho1
+// The direction update P = R + beta P is folded into the next normal-operator
+// sweep; alpha and beta are formed by the last block of the reductions that
+// produce <P,Q> and <R,R>, so an iteration never waits on the host.  The host
+// replays a CUDA graph of `check_every` iterations and reads one flag word
+// between replays.  When the recursive residual meets the tolerance the true
+// residual ||A^T b - K x|| / ||A^T b|| is recomputed in FP64; CG restarts from
+// the current x while it is above the tolerance.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "tca_internal.cuh"
+
+namespace tca {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float4; static constexpr int n = 4; };
+template <> struct V2<double> { using t = double2; static constexpr int n = 2; };
+
+// x += alpha p;  r -= alpha q;  rho1 = <r, r>  (Fig. 2 update block) -> beta, stop test.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
+                                                                const T* __restrict__ p, const T* __restrict__ q,
+                                                                int64_t n, Scalars* sc, Reduce red) {
+  __shared__ double sh[kVecThreads / 32];
+  if (cg_done(sc)) return;
+  const double alpha_d = sc->alpha;
+  const T alpha = (T)alpha_d;
+  using VT = typename V2<T>::t;
+  constexpr int VN = V2<T>::n;
+  const int64_t nv = n / VN;
+  T part = T(0);
+  double acc = 0.0;
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    VT xv = reinterpret_cast<VT*>(x)[i];
+    VT rv = reinterpret_cast<VT*>(r)[i];
+    const VT pv = reinterpret_cast<const VT*>(p)[i];
+    const VT qv = reinterpret_cast<const VT*>(q)[i];
+    if constexpr (VN == 4) {
+      xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+      rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+      part += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    } else {
+      xv.x += alpha * pv.x; xv.y += alpha * pv.y;
+      rv.x -= alpha * qv.x; rv.y -= alpha * qv.y;
+      part += rv.x * rv.x + rv.y * rv.y;
+    }
+    reinterpret_cast<VT*>(x)[i] = xv;
+    reinterpret_cast<VT*>(r)[i] = rv;
+    if (++cnt == 8) {  // short FP32 runs, FP64 beyond
+      acc += (double)part;
+      part = T(0);
+      cnt = 0;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+      part += r[i] * r[i];
+    }
+  }
+  acc += (double)part;
+  double total;
+  if (dev::grid_sum_last(acc, red, &total, sh)) {
+    const double rho = sc->rho;
+    sc->rho_new = total;
+    sc->beta = total / rho;
+    sc->rho = total;
+    sc->iters += 1;
+    if (!isfinite(total)) sc->breakdown = 1;
+    if (sqrt(total) <= sc->rtol * sc->bnorm) sc->converged = 1;
+  }
+}
+
+// P_new = R + beta P_old (used when the normal operator is not the fused sweep).
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cg_direction_kernel(const T* __restrict__ r, const T* __restrict__ pold,
+                                                                   T* __restrict__ pnew, int64_t n, const Scalars* sc) {
+  if (cg_done(sc)) return;
+  const T beta = (T)sc->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    pnew[i] = r[i] + beta * pold[i];
+}
+
+// alpha = rho / <P, Q> (unfused path).
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cg_alpha_kernel(const T* __restrict__ p, const T* __restrict__ q,
+                                                               int64_t n, Scalars* sc, Reduce red) {
+  __shared__ double sh[kVecThreads / 32];
+  if (cg_done(sc)) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)p[i] * (double)q[i];
+  double total;
+  if (dev::grid_sum_last(acc, red, &total, sh)) {
+    sc->pq = total;
+    const double alpha = sc->rho / total;
+    if (!(total > 0.0) || !isfinite(alpha)) {
+      sc->breakdown = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = alpha;
+    }
+  }
+}
+
+// r = rhs - kx (kx may be null: r = rhs); rho = <r,r>; optionally bnorm = ||rhs||.
+// Resets beta = 0 (fresh direction) and the stop flags.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cg_start_kernel(const T* __restrict__ rhs, const T* __restrict__ kx,
+                                                               T* __restrict__ r, int64_t n, Scalars* sc, Reduce red,
+                                                               int set_bnorm, Reduce red2) {
+  __shared__ double sh[kVecThreads / 32];
+  double a_rr = 0.0, a_bb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T b = rhs[i];
+    const T v = kx ? (T)(b - kx[i]) : b;
+    r[i] = v;
+    a_rr += (double)v * (double)v;
+    a_bb += (double)b * (double)b;
+  }
+  // Two independent reductions, each with its own scratch and ticket.
+  double t_rr, t_bb;
+  const bool last1 = dev::grid_sum_last(a_rr, red, &t_rr, sh);
+  const bool last2 = dev::grid_sum_last(a_bb, red2, &t_bb, sh);
+  if (last1) {
+    sc->rho = t_rr;
+    sc->beta = 0.0;
+    sc->converged = 0;
+    sc->breakdown = 0;
+  }
+  if (last2 && set_bnorm) sc->bnorm = sqrt(t_bb);
+}
+
+// ||rhs64 - kx64|| / ||rhs64||  -> sc->aux; optionally r = rhs64 - kx64 (cast).
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) true_residual_kernel(const double* __restrict__ rhs,
+                                                                    const double* __restrict__ kx, T* __restrict__ r,
+                                                                    int64_t n, Scalars* sc, Reduce red, Reduce red2) {
+  __shared__ double sh[kVecThreads / 32];
+  double a_rr = 0.0, a_bb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double b = rhs[i];
+    const double v = b - kx[i];
+    if (r) r[i] = (T)v;
+    a_rr += v * v;
+    a_bb += b * b;
+  }
+  double t_rr, t_bb;
+  const bool l1 = dev::grid_sum_last(a_rr, red, &t_rr, sh);
+  if (l1) red2.partials[red2.max_blocks - 1] = t_rr;  // park the first total past the used slots
+  const bool l2 = dev::grid_sum_last(a_bb, red2, &t_bb, sh);
+  if (l2) {
+    __threadfence();
+    sc->aux = sqrt(((volatile double*)red2.partials)[red2.max_blocks - 1]) / sqrt(t_bb);
+  }
+}
+
+__global__ void cg_setup_kernel(Scalars* sc, double rtol, int max_iter) {
+  sc->rtol = rtol;
+  sc->max_iter = max_iter;
+  sc->iters = 0;
+  sc->converged = 0;
+  sc->breakdown = 0;
+  sc->beta = 0.0;
+  sc->alpha = 0.0;
+}
+
+}  // namespace
+
+// Second reduction scratch lives after the first one's slots.
+static Reduce second_reduce(const tca_plan_s* p) {
+  Reduce r = p->red;
+  r.partials = p->red.partials + p->red.max_blocks / 2;
+  r.ticket = p->red.ticket + 1;
+  r.max_blocks = p->red.max_blocks / 2;
+  return r;
+}
+static Reduce first_reduce(const tca_plan_s* p) {
+  Reduce r = p->red;
+  r.max_blocks = p->red.max_blocks / 2;
+  return r;
+}
+
+// One CG iteration.  ev_begin/ev_end (may be null) bracket the normal-operator
+// sweep so that a profiled solve can time it on the device.
+template <typename T>
+static tca_status enqueue_iteration(tca_plan_s* p, T* x, const T* pold, T* pnew, cudaStream_t s,
+                                    cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+  const int64_t N = p->N;
+  T* r = (T*)p->r;
+  T* q = (T*)p->q;
+  const int grid = std::min(vector_grid(p, N), first_reduce(p).max_blocks);
+  const bool fused = sizeof(T) == 4 && p->fused_ok;
+  if (ev_begin) TCA_CUDA_TRY(cudaEventRecord(ev_begin, s));
+  if constexpr (sizeof(T) == 4) {
+    if (fused) TCA_TRY(normal_fused_f32(p, r, pold, pnew, q, true, s));
+  }
+  if (!fused) {
+    cg_direction_kernel<T><<<grid, kVecThreads, 0, s>>>(r, pold, pnew, N, p->scal);
+    TCA_LAUNCH_CHECK();
+    TCA_TRY(normal_generic<T>(p, pnew, q, s));
+    cg_alpha_kernel<T><<<grid, kVecThreads, 0, s>>>(pnew, q, N, p->scal, first_reduce(p));
+    TCA_LAUNCH_CHECK();
+  }
+  if (ev_end) TCA_CUDA_TRY(cudaEventRecord(ev_end, s));
+  cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p));
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+template <typename T>
+static tca_status ensure_solver_buffers(tca_plan_s* p) {
+  if (p->r) return TCA_OK;
+  const size_t bytes = sizeof(T) * (size_t)p->N;
+  cudaError_t e = cudaMalloc(&p->rhs, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->r, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->p[0], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->p[1], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->q, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->res64, sizeof(double) * (size_t)p->N);
+  if (e == cudaSuccess && sizeof(T) == 4) e = cudaMalloc((void**)&p->rhs64, sizeof(double) * (size_t)p->N);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return TCA_ERR_ALLOC;
+  }
+  return TCA_OK;
+}
+
+// Build (or reuse) the graph of `iters` iterations (an even count: the two
+// direction buffers alternate) for this x buffer.
+template <typename T>
+static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaStream_t s) {
+  if (p->graph_exec && p->graph_x == x && p->graph_iters == iters && p->graph_profiled == profile) return TCA_OK;
+  if (p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  if (profile && !p->sweep_ev[0]) {
+    for (int i = 0; i < 2 * kMaxProfiledIters; ++i) TCA_CUDA_TRY(cudaEventCreate(&p->sweep_ev[i]));
+  }
+  cudaStream_t cs;
+  TCA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const uint64_t before = tca_kernel_launches(0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  tca_status st = TCA_OK;
+  if (e == cudaSuccess) {
+    for (int it = 0; it < iters && st == TCA_OK; ++it) {
+      const T* pold = (const T*)p->p[it & 1];
+      T* pnew = (T*)p->p[(it + 1) & 1];
+      st = enqueue_iteration<T>(p, x, pold, pnew, cs, profile ? p->sweep_ev[2 * it] : nullptr,
+                                profile ? p->sweep_ev[2 * it + 1] : nullptr);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  const uint64_t after = tca_kernel_launches(0);
+  tca_kernel_launches(1);
+  note_launches(before);  // captured launches are counted per replay instead
+  cudaStreamDestroy(cs);
+  if (st != TCA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    if (g) cudaGraphDestroy(g);
+    return TCA_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    p->graph_exec = nullptr;
+    return TCA_ERR_CUDA;
+  }
+  p->graph_x = x;
+  p->graph_iters = iters;
+  p->graph_profiled = profile;
+  p->graph_launches = after - before;
+  return TCA_OK;
+}
+
+// FP64 true relative residual of x into p->scal->aux; optionally r = residual.
+template <typename T>
+static tca_status true_residual(tca_plan_s* p, const T* x, bool write_r, cudaStream_t s) {
+  const double* rhs64 = sizeof(T) == 8 ? (const double*)p->rhs : p->rhs64;
+  TCA_TRY(normal_fp64<T>(p, x, p->res64, s));
+  const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks - 1);
+  true_residual_kernel<T><<<grid, kVecThreads, 0, s>>>(rhs64, p->res64, write_r ? (T*)p->r : nullptr, p->N, p->scal,
+                                                        first_reduce(p), second_reduce(p));
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+template <typename T>
+static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_solve_opts* o, tca_solve_info* info,
+                             cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  TCA_TRY(ensure_solver_buffers<T>(p));
+  const int64_t N = p->N;
+  const double rtol = o ? o->rtol : 1e-6;
+  const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
+  const bool x0 = o && o->x0_given;
+  int every = (o && o->check_every > 0) ? o->check_every : 16;
+  every = std::max(2, (every + 1) / 2 * 2);
+  const bool profile = o && o->profile;
+  if (profile) every = std::min(every, kMaxProfiledIters);
+  if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
+  double sweep_ms = 0.0;
+  int sweep_n = 0;
+
+  // rhs = A^T b (FP32 for the iteration; FP64 for the true residual).
+  TCA_TRY((apply_chain<T, T, T>(p, true, (const T*)b_in, (T*)p->rhs, p->ws, p->ws_elems, s)));
+  if constexpr (sizeof(T) == 4) {
+    TCA_TRY(ensure_ws64_public(p));
+    TCA_TRY((apply_chain<float, double, double>(p, true, (const float*)b_in, p->rhs64, (void* const*)p->ws64,
+                                                 p->ws64_elems, s)));
+  }
+  cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, rtol, max_iter);
+  TCA_LAUNCH_CHECK();
+  TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(T) * N, s));
+  TCA_CUDA_TRY(cudaMemsetAsync(p->p[1], 0, sizeof(T) * N, s));
+  const int vgrid = std::min(vector_grid(p, N), second_reduce(p).max_blocks - 1);
+  if (x0) {
+    if constexpr (sizeof(T) == 4) {
+      if (p->fused_ok) TCA_TRY(normal_fused_f32(p, nullptr, (const float*)x, nullptr, (float*)p->q, false, s));
+      else TCA_TRY(normal_generic<T>(p, x, (T*)p->q, s));
+    } else {
+      TCA_TRY(normal_generic<T>(p, x, (T*)p->q, s));
+    }
+    cg_start_kernel<T><<<vgrid, kVecThreads, 0, s>>>((const T*)p->rhs, (const T*)p->q, (T*)p->r, N, p->scal,
+                                                      first_reduce(p), 1, second_reduce(p));
+  } else {
+    TCA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * N, s));
+    cg_start_kernel<T><<<vgrid, kVecThreads, 0, s>>>((const T*)p->rhs, nullptr, (T*)p->r, N, p->scal,
+                                                      first_reduce(p), 1, second_reduce(p));
+  }
+  TCA_LAUNCH_CHECK();
+  TCA_TRY(get_graph<T>(p, x, every, profile, s));
+
+  tca_status status = TCA_OK;
+  int restarts = 0;
+  Scalars* hs = p->scal_host;
+  for (;;) {
+    // Start-of-iteration stop test (a zero right-hand side or an exact x0).
+    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    bool conv = hs->bnorm == 0.0 || std::sqrt(hs->rho) <= rtol * hs->bnorm;
+    while (!conv && !hs->breakdown && hs->iters < max_iter) {
+      const int it_before = hs->iters;
+      TCA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, s));
+      note_launches(p->graph_launches);
+      TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+      TCA_CUDA_TRY(cudaStreamSynchronize(s));
+      conv = hs->converged != 0;
+      if (profile) {
+        // Iterations of this replay that did work; the rest returned at entry.
+        const int ran = std::min(every, hs->iters - it_before + (hs->breakdown ? 1 : 0));
+        for (int i = 0; i < ran; ++i) {
+          float ms = 0.f;
+          TCA_CUDA_TRY(cudaEventElapsedTime(&ms, p->sweep_ev[2 * i], p->sweep_ev[2 * i + 1]));
+          sweep_ms += ms;
+          ++sweep_n;
+        }
+      }
+    }
+    if (hs->breakdown) {
+      status = TCA_ERR_BREAKDOWN;
+      break;
+    }
+    if (hs->bnorm == 0.0) {
+      hs->aux = 0.0;
+      break;
+    }
+    // True residual in FP64; restart from x while it misses the tolerance.
+    TCA_TRY(true_residual<T>(p, x, true, s));
+    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs->aux <= rtol) break;
+    if (hs->iters >= max_iter) {
+      status = TCA_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++restarts;
+    // r already holds the FP64 residual (cast); recompute rho, keep bnorm.
+    cg_start_kernel<T><<<vgrid, kVecThreads, 0, s>>>((const T*)p->r, nullptr, (T*)p->r, N, p->scal,
+                                                      first_reduce(p), 0, second_reduce(p));
+    TCA_LAUNCH_CHECK();
+  }
+  if (info) {
+    info->iters = hs->iters;
+    info->refinements = restarts;
+    info->rel_res_true = hs->aux;
+    info->rel_res_recursive = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho, 0.0)) / hs->bnorm : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->sweep_ms = sweep_ms;
+    info->sweep_launches = sweep_n;
+    info->reserved = 0;
+  }
+  return status;
+}
+
+}  // namespace tca
+
+using namespace tca;
+
+extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
+                                tca_solve_info* info, cudaStream_t stream) {
+  if (!plan || !b || !x) return TCA_ERR_INVALID_ARG;
+  tca_plan_s* p = plan;
+  if (p->prec == TCA_BF16_IR || p->prec == TCA_TF32_IR) return TCA_ERR_UNSUPPORTED;
+  const size_t es = elem_size(p);
+  // Host buffers, and device buffers the vector kernels cannot address with
+  // 16-byte accesses, go through the plan's staging buffers.
+  const bool b_dev = is_device_ptr(b);
+  const bool x_dev = is_device_ptr(x) && ((uintptr_t)x % 16 == 0);
+  const void* db = b;
+  void* dx = x;
+  if (!b_dev || !x_dev) TCA_TRY(ensure_stage(p));
+  if (!b_dev) {
+    TCA_CUDA_TRY(cudaMemcpyAsync(p->stage_b, b, es * (size_t)p->M, cudaMemcpyHostToDevice, stream));
+    db = p->stage_b;
+  }
+  if (!x_dev) {
+    if (opts && opts->x0_given)
+      TCA_CUDA_TRY(cudaMemcpyAsync(p->stage_x, x, es * (size_t)p->N, cudaMemcpyDefault, stream));
+    dx = p->stage_x;
+  }
+  tca_status st = p->prec == TCA_F64 ? solve_impl<double>(p, db, (double*)dx, opts, info, stream)
+                                     : solve_impl<float>(p, db, (float*)dx, opts, info, stream);
+  if (!x_dev && (st == TCA_OK || st == TCA_ERR_NOT_CONVERGED || st == TCA_ERR_BREAKDOWN)) {
+    TCA_CUDA_TRY(cudaMemcpyAsync(x, p->stage_x, es * (size_t)p->N, cudaMemcpyDefault, stream));
+    TCA_CUDA_TRY(cudaStreamSynchronize(stream));
+  }
+  return st;
+}

@@ -1,0 +1,425 @@
+// Plan construction and lifetime: factor ingest, Gram and regulariser bands,
+// mode ordering, workspace.  Implements tca_plan / tca_destroy and the small
+// status helpers of tca.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "tca_internal.cuh"
+
+namespace tca {
+
+static thread_local char g_last_error[256] = "";
+static thread_local uint64_t g_launches = 0;
+
+void set_cuda_error(cudaError_t e) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+void note_launches(uint64_t count) { g_launches += count; }
+
+int vector_grid(const tca_plan_s* p, int64_t n) {
+  const int64_t want = (n + 1023) / 1024;  // ~4 float4 per thread at 256 threads
+  const int64_t cap = (int64_t)p->num_sms * 8;
+  return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+// ---- Gram formation G = A^T A in FP64 (plan step; App. "Tensor transposition")
+
+// Banded Gram of an ELL4 factor.  One thread per (column i, offset e): entry
+// G[i][i-3+e] = sum over rows r touching both columns of A[r][i] A[r][i-3+e],
+// rows taken in ascending order so that G[i][c] and G[c][i] are bit-identical.
+__global__ void gram_ell4_kernel(const int32_t* __restrict__ col0, const double* __restrict__ w,
+                                 const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
+                                 int64_t n, double* __restrict__ g64, float* __restrict__ g32) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * 7) return;
+  const int64_t i = t / 7;
+  const int e = (int)(t % 7);
+  const int64_t c = i - kGramHalf + e;
+  double s = 0.0;
+  if (c >= 0 && c < n) {
+    const int64_t r0 = tstart[i], r1 = r0 + tcount[i];
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t oi = i - col0[r], oc = c - col0[r];
+      if (oc >= 0 && oc < 4) s += w[r * 4 + oi] * w[r * 4 + oc];
+    }
+  }
+  g64[t] = s;
+  g32[t] = (float)s;
+}
+
+// Dense Gram G[i][c] = sum_r A[r][i] A[r][c] (ascending r; exactly symmetric).
+__global__ void gram_dense_kernel(const double* __restrict__ a, int64_t m, int64_t n,
+                                  double* __restrict__ g64, float* __restrict__ g32) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int64_t i = t / n, c = t % n;
+  double s = 0.0;
+  for (int64_t r = 0; r < m; ++r) s += a[r * n + i] * a[r * n + c];
+  g64[t] = s;
+  g32[t] = (float)s;
+}
+
+// lambda * (D2^T D2) as a 5-band: entry [i][e] couples i with c = i-2+e;
+// (D2^T D2)[i][c] = sum_r D2[r][i] D2[r][c], D2[r][r..r+2] = (1, -2, 1).
+__global__ void lap_band_kernel(int64_t n, double lam, double* __restrict__ l64, float* __restrict__ l32,
+                                int32_t* __restrict__ start) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * 5) return;
+  const int64_t i = t / 5;
+  const int e = (int)(t % 5);
+  const int64_t c = i - kLapHalf + e;
+  double s = 0.0;
+  if (c >= 0 && c < n) {
+    for (int64_t r = 0; r + 2 < n; ++r) {
+      const int64_t di = i - r, dc = c - r;
+      if (di < 0 || di > 2 || dc < 0 || dc > 2) continue;
+      const double vi = di == 1 ? -2.0 : 1.0, vc = dc == 1 ? -2.0 : 1.0;
+      s += vi * vc;
+    }
+  }
+  l64[t] = lam * s;
+  l32[t] = (float)(lam * s);
+  if (e == 0) start[i] = (int32_t)(i - kLapHalf);
+}
+
+__global__ void cast_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+
+__global__ void transpose_kernel(const double* __restrict__ a, int64_t rows, int64_t cols,
+                                 double* __restrict__ at64, float* __restrict__ at32) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * cols) return;
+  const int64_t r = t / cols, c = t % cols;
+  at64[c * rows + r] = a[t];
+  at32[c * rows + r] = (float)a[t];
+}
+
+__global__ void iota_kernel(int32_t* __restrict__ s, int64_t n, int shift) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) s[t] = (int32_t)(t - shift);
+}
+
+static int nblk(int64_t n, int b = 256) { return (int)((n + b - 1) / b); }
+
+template <typename T>
+static tca_status dmalloc(T** ptr, int64_t count) {
+  *ptr = nullptr;
+  if (count <= 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)ptr, sizeof(T) * (size_t)count);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return TCA_ERR_ALLOC;
+  }
+  return TCA_OK;
+}
+
+static void free_band(Band& b) {
+  cudaFree(b.start);
+  cudaFree(b.w32);
+  cudaFree(b.w64);
+  b = Band();
+}
+static void free_dense(Dense& d) {
+  cudaFree(d.a32);
+  cudaFree(d.a64);
+  d = Dense();
+}
+static void free_op(ModeOp& o) {
+  free_band(o.band);
+  free_dense(o.dense);
+}
+
+static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool reg, cudaStream_t s) {
+  Mode& md = p->mode[k];
+  md.n = f.n;
+  md.m = f.m;
+  md.factor_kind = f.kind;
+  const int64_t m = f.m, n = f.n;
+  if (f.kind == TCA_FACTOR_ELL4) {
+    // Forward band: row r reads columns col0[r] .. col0[r]+3.
+    std::vector<double> w((size_t)m * 4);
+    std::vector<int32_t> c0(f.col0, f.col0 + m);
+    for (int64_t r = 0; r < m; ++r) {
+      if (r > 0 && c0[r] < c0[r - 1]) return TCA_ERR_INVALID_ARG;  // must be non-decreasing
+      for (int c = 0; c < 4; ++c) {
+        const int64_t col = (int64_t)c0[r] + c;
+        w[r * 4 + c] = (col >= 0 && col < n) ? f.values[r * 4 + c] : 0.0;
+      }
+    }
+    Band& fb = md.fwd.band;
+    md.fwd.kind = OP_BAND;
+    fb.n_out = m;
+    fb.n_in = n;
+    fb.W = 4;
+    TCA_TRY(dmalloc(&fb.start, m));
+    TCA_TRY(dmalloc(&fb.w64, m * 4));
+    TCA_TRY(dmalloc(&fb.w32, m * 4));
+    TCA_CUDA_TRY(cudaMemcpyAsync(fb.start, c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    TCA_CUDA_TRY(cudaMemcpyAsync(fb.w64, w.data(), sizeof(double) * m * 4, cudaMemcpyHostToDevice, s));
+    cast_kernel<<<nblk(m * 4), 256, 0, s>>>(fb.w64, fb.w32, m * 4);
+    TCA_LAUNCH_CHECK();
+
+    // Transposed band: column i is touched by the contiguous rows jlo..jhi
+    // (col0 non-decreasing), so A^T is again a band in gather form.
+    std::vector<int32_t> ts((size_t)n), tc((size_t)n);
+    int W = 1;
+    {
+      int64_t lo = 0;
+      for (int64_t i = 0; i < n; ++i) {
+        while (lo < m && (int64_t)c0[lo] + 3 < i) ++lo;
+        int64_t hi = lo;
+        while (hi < m && (int64_t)c0[hi] <= i) ++hi;
+        ts[i] = (int32_t)lo;
+        tc[i] = (int32_t)std::max<int64_t>(0, hi - lo);
+        W = std::max<int>(W, tc[i]);
+      }
+    }
+    if (W > kMaxBandW) return TCA_ERR_UNSUPPORTED;
+    std::vector<double> wt((size_t)n * W, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+      for (int e = 0; e < tc[i]; ++e) {
+        const int64_t r = ts[i] + e;
+        const int64_t off = i - c0[r];
+        if (off >= 0 && off < 4) wt[i * W + e] = w[r * 4 + off];
+      }
+    Band& bb = md.bwd.band;
+    md.bwd.kind = OP_BAND;
+    bb.n_out = n;
+    bb.n_in = m;
+    bb.W = W;
+    TCA_TRY(dmalloc(&bb.start, n));
+    TCA_TRY(dmalloc(&bb.w64, n * W));
+    TCA_TRY(dmalloc(&bb.w32, n * W));
+    TCA_CUDA_TRY(cudaMemcpyAsync(bb.start, ts.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    TCA_CUDA_TRY(cudaMemcpyAsync(bb.w64, wt.data(), sizeof(double) * n * W, cudaMemcpyHostToDevice, s));
+    cast_kernel<<<nblk(n * W), 256, 0, s>>>(bb.w64, bb.w32, n * W);
+    TCA_LAUNCH_CHECK();
+
+    // Gram band on the device (FP64).
+    int32_t* dcount = nullptr;
+    TCA_TRY(dmalloc(&dcount, n));
+    TCA_CUDA_TRY(cudaMemcpyAsync(dcount, tc.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    Band& gb = md.gram.band;
+    md.gram.kind = OP_BAND;
+    gb.n_out = n;
+    gb.n_in = n;
+    gb.W = 2 * kGramHalf + 1;
+    TCA_TRY(dmalloc(&gb.start, n));
+    TCA_TRY(dmalloc(&gb.w64, n * 7));
+    TCA_TRY(dmalloc(&gb.w32, n * 7));
+    iota_kernel<<<nblk(n), 256, 0, s>>>(gb.start, n, kGramHalf);
+    TCA_LAUNCH_CHECK();
+    gram_ell4_kernel<<<nblk(n * 7), 256, 0, s>>>(fb.start, fb.w64, bb.start, dcount, n, gb.w64, gb.w32);
+    TCA_LAUNCH_CHECK();
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(dcount);
+  } else if (f.kind == TCA_FACTOR_DENSE) {
+    Dense& fd = md.fwd.dense;
+    md.fwd.kind = OP_DENSE;
+    fd.n_out = m;
+    fd.n_in = n;
+    TCA_TRY(dmalloc(&fd.a64, m * n));
+    TCA_TRY(dmalloc(&fd.a32, m * n));
+    TCA_CUDA_TRY(cudaMemcpyAsync(fd.a64, f.values, sizeof(double) * m * n, cudaMemcpyHostToDevice, s));
+    cast_kernel<<<nblk(m * n), 256, 0, s>>>(fd.a64, fd.a32, m * n);
+    TCA_LAUNCH_CHECK();
+    Dense& bd = md.bwd.dense;
+    md.bwd.kind = OP_DENSE;
+    bd.n_out = n;
+    bd.n_in = m;
+    TCA_TRY(dmalloc(&bd.a64, m * n));
+    TCA_TRY(dmalloc(&bd.a32, m * n));
+    transpose_kernel<<<nblk(m * n), 256, 0, s>>>(fd.a64, m, n, bd.a64, bd.a32);
+    TCA_LAUNCH_CHECK();
+    Dense& gd = md.gram.dense;
+    md.gram.kind = OP_DENSE;
+    gd.n_out = n;
+    gd.n_in = n;
+    TCA_TRY(dmalloc(&gd.a64, n * n));
+    TCA_TRY(dmalloc(&gd.a32, n * n));
+    gram_dense_kernel<<<nblk(n * n), 256, 0, s>>>(fd.a64, m, n, gd.a64, gd.a32);
+    TCA_LAUNCH_CHECK();
+  } else {
+    return TCA_ERR_INVALID_ARG;
+  }
+  // Regulariser band (zeros when the mode is not regularised).
+  md.reg = reg && n >= 3;
+  Band& lb = md.lap;
+  lb.n_out = n;
+  lb.n_in = n;
+  lb.W = 2 * kLapHalf + 1;
+  TCA_TRY(dmalloc(&lb.start, n));
+  TCA_TRY(dmalloc(&lb.w64, n * 5));
+  TCA_TRY(dmalloc(&lb.w32, n * 5));
+  lap_band_kernel<<<nblk(n * 5), 256, 0, s>>>(n, md.reg ? p->lambda : 0.0, lb.w64, lb.w32, lb.start);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+// Largest intermediate of a chain of mode products applied in `order`.
+static int64_t chain_peak(const int64_t* start, const int64_t* end, const int* order, int d) {
+  int64_t cur[kMaxModes];
+  for (int k = 0; k < d; ++k) cur[k] = start[k];
+  int64_t peak = 0;
+  for (int s = 0; s < d; ++s) {
+    cur[order[s]] = end[order[s]];
+    int64_t sz = 1;
+    for (int k = 0; k < d; ++k) sz *= cur[k];
+    if (s + 1 < d) peak = std::max(peak, sz);
+  }
+  return peak;
+}
+
+static void destroy_plan(tca_plan_s* p) {
+  if (!p) return;
+  for (int k = 0; k < kMaxModes; ++k) {
+    free_op(p->mode[k].fwd);
+    free_op(p->mode[k].bwd);
+    free_op(p->mode[k].gram);
+    free_band(p->mode[k].lap);
+  }
+  cudaFree(p->ws[0]);
+  cudaFree(p->ws[1]);
+  cudaFree(p->ws64[0]);
+  cudaFree(p->ws64[1]);
+  cudaFree(p->rhs);
+  cudaFree(p->r);
+  cudaFree(p->p[0]);
+  cudaFree(p->p[1]);
+  cudaFree(p->q);
+  cudaFree(p->rhs64);
+  cudaFree(p->res64);
+  cudaFree(p->stage_x);
+  cudaFree(p->stage_b);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  for (cudaEvent_t& ev : p->sweep_ev)
+    if (ev) cudaEventDestroy(ev);
+  cudaFree(p->scal);
+  if (p->scal_host) cudaFreeHost(p->scal_host);
+  cudaFree(p->red.partials);
+  cudaFree(p->red.ticket);
+  delete p;
+}
+
+}  // namespace tca
+
+using namespace tca;
+
+extern "C" tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, const tca_factor* factors,
+                               const tca_reg* reg, tca_precision prec, cudaStream_t stream) {
+  if (!out || !n || !factors) return TCA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (order != 3 && order != 4) return TCA_ERR_INVALID_ARG;
+  if (prec != TCA_F64 && prec != TCA_F32 && prec != TCA_BF16_IR && prec != TCA_TF32_IR)
+    return TCA_ERR_INVALID_ARG;
+  for (int k = 0; k < order; ++k) {
+    const tca_factor& f = factors[k];
+    if (n[k] <= 0 || f.m <= 0 || f.n <= 0 || !f.values) return TCA_ERR_INVALID_ARG;
+    if (f.kind == TCA_FACTOR_ELL4 && !f.col0) return TCA_ERR_INVALID_ARG;
+    if (f.kind != TCA_FACTOR_ELL4 && f.kind != TCA_FACTOR_DENSE) return TCA_ERR_INVALID_ARG;
+    if (f.reserved != 0) return TCA_ERR_INVALID_ARG;
+    if (f.n != n[k]) return TCA_ERR_SHAPE;
+    if (f.n > (1 << 24) || f.m > (1 << 24)) return TCA_ERR_UNSUPPORTED;
+  }
+  const double lam = reg ? reg->lambda : 0.0;
+  if (!(lam >= 0.0) || !std::isfinite(lam)) return TCA_ERR_INVALID_ARG;
+  const uint32_t mask = reg ? reg->reg_mode_mask : 0u;
+
+  tca_plan_s* p = new tca_plan_s();
+  p->d = order;
+  p->prec = prec;
+  p->lambda = lam;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (p->num_sms <= 0) p->num_sms = 1;
+  p->N = 1;
+  p->M = 1;
+  for (int k = 0; k < order; ++k) {
+    p->n[k] = n[k];
+    p->m[k] = factors[k].m;
+    p->N *= n[k];
+    p->M *= factors[k].m;
+  }
+  tca_status st = TCA_OK;
+  for (int k = 0; k < order && st == TCA_OK; ++k) {
+    st = ingest_mode(p, k, factors[k], (mask >> k) & 1u, stream);
+    if (factors[k].kind != TCA_FACTOR_ELL4) p->all_band = false;
+  }
+  if (st != TCA_OK) {
+    destroy_plan(p);
+    return st;
+  }
+  // Mode order by cost (Sec. 2.1): shrinking factors first, expanding ones last,
+  // which keeps every intermediate as small as the chain allows.
+  for (int k = 0; k < order; ++k) p->order_fwd[k] = p->order_bwd[k] = k;
+  std::stable_sort(p->order_fwd, p->order_fwd + order, [&](int a, int b) {
+    return (double)p->m[a] / p->n[a] < (double)p->m[b] / p->n[b];
+  });
+  std::stable_sort(p->order_bwd, p->order_bwd + order, [&](int a, int b) {
+    return (double)p->n[a] / p->m[a] < (double)p->n[b] / p->m[b];
+  });
+  const int64_t peak_f = chain_peak(p->n, p->m, p->order_fwd, order);
+  const int64_t peak_b = chain_peak(p->m, p->n, p->order_bwd, order);
+  p->ws_elems = std::max<int64_t>({peak_f, peak_b, p->N, 1});
+  // The fused FP32 sweep covers banded operators whose fastest mode fits the tile.
+  // Order 3 runs as a 4D sweep with a unit fastest mode (no G_4, no L_4); an
+  // order-4 plan needs its own fastest mode to fill the tile (n4 = 4 or 8).
+  if (p->all_band && prec != TCA_F64) {
+    p->fused_ok = order == 3 || p->n[3] == 4 || p->n[3] == 8;
+  }
+  const size_t es = elem_size(p);
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&p->ws[0], es * (size_t)p->ws_elems);
+  if (e == cudaSuccess) e = cudaMalloc(&p->ws[1], es * (size_t)p->ws_elems);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->scal, sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->scal_host, sizeof(Scalars));
+  p->red.max_blocks = std::max(4096, p->num_sms * 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->red.partials, sizeof(double) * p->red.max_blocks);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->red.ticket, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->red.ticket, 0, 2 * sizeof(unsigned int), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(Scalars), stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    destroy_plan(p);
+    return TCA_ERR_ALLOC;
+  }
+  *out = p;
+  return TCA_OK;
+}
+
+extern "C" void tca_destroy(tca_plan_t plan) {
+  if (plan) cudaDeviceSynchronize();
+  destroy_plan(plan);
+}
+
+extern "C" const char* tca_status_string(tca_status s) {
+  switch (s) {
+    case TCA_OK: return "ok";
+    case TCA_ERR_INVALID_ARG: return "invalid argument";
+    case TCA_ERR_SHAPE: return "shape mismatch";
+    case TCA_ERR_UNSUPPORTED: return "unsupported";
+    case TCA_ERR_ALLOC: return "device allocation failed";
+    case TCA_ERR_CUDA: return "CUDA error";
+    case TCA_ERR_NOT_CONVERGED: return "not converged";
+    case TCA_ERR_BREAKDOWN: return "CG breakdown";
+    case TCA_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* tca_last_error_string(void) { return tca::g_last_error; }
+
+extern "C" uint64_t tca_kernel_launches(int reset) {
+  const uint64_t v = tca::g_launches;
+  if (reset) tca::g_launches = 0;
+  return v;
+}
+
+extern "C" int tca_version(void) { return (1 << 16) | 0; }

@@ -1,0 +1,263 @@
+// Internal declarations of the tca library: plan layout, error plumbing and
+// small device helpers shared by the kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/tca.h"
+
+namespace tca {
+
+constexpr int kMaxModes = 4;
+constexpr int kGramHalf = 3;  // G_k = A_k^T A_k of a 4-wide band is 7-banded
+constexpr int kLapHalf = 2;   // D2^T D2 is 5-banded
+constexpr int kMaxBandW = 16; // widest transposed ELL4 band accepted
+constexpr int kMaxProfiledIters = 64;  // iterations per graph replay when sweeps are timed
+
+// y[o] = sum_{e < W} w[o*W + e] * x[start[o] + e]; indices outside [0, n_in)
+// carry weight 0 in w and are skipped by the kernels.
+struct Band {
+  int64_t n_out = 0, n_in = 0;
+  int W = 0;
+  int32_t* start = nullptr;  // device, n_out
+  float* w32 = nullptr;      // device, n_out * W
+  double* w64 = nullptr;     // device, n_out * W
+};
+
+// Row-major n_out x n_in matrix.
+struct Dense {
+  int64_t n_out = 0, n_in = 0;
+  float* a32 = nullptr;
+  double* a64 = nullptr;
+};
+
+enum OpKind { OP_BAND = 0, OP_DENSE = 1 };
+
+struct ModeOp {
+  int kind = OP_BAND;
+  Band band;
+  Dense dense;
+  int64_t n_out() const { return kind == OP_BAND ? band.n_out : dense.n_out; }
+  int64_t n_in() const { return kind == OP_BAND ? band.n_in : dense.n_in; }
+};
+
+struct Mode {
+  int64_t n = 0, m = 0;
+  int factor_kind = TCA_FACTOR_DENSE;
+  ModeOp fwd;   // A_k   (m x n)
+  ModeOp bwd;   // A_k^T (n x m)
+  ModeOp gram;  // G_k = A_k^T A_k (n x n): 7-band (W=7, start=i-3) or dense
+  bool reg = false;
+  Band lap;     // lambda * D2^T D2 as a 5-band (W=5, start=i-2); zeros if !reg
+};
+
+// CG scalars, resident on the device (FP64, Fig. 2 names).
+struct Scalars {
+  double rho;       // <R, R>
+  double rho_new;   // rho1
+  double pq;        // <P, Q>
+  double alpha;
+  double beta;      // rho1 / rho for the next direction update
+  double bnorm;     // ||rhs||
+  double rtol;      // stopping threshold on sqrt(rho) / bnorm
+  double aux;       // spare reduction slot (true residual norm^2, dots)
+  int32_t converged;
+  int32_t breakdown;
+  int32_t iters;     // CG iterations completed on the device
+  int32_t max_iter;  // kernels of an iteration skip their work once iters reaches it
+};
+
+// True once the iteration loop must stop doing work (converged, broken down or
+// out of iterations); every CG kernel tests it on entry.
+__host__ __device__ inline bool cg_done(const Scalars* s) {
+  return s->converged | s->breakdown | (s->iters >= s->max_iter);
+}
+
+// Reduction scratch for the last-block-finishes pattern.
+struct Reduce {
+  double* partials = nullptr;  // one slot per block
+  unsigned int* ticket = nullptr;
+  int max_blocks = 0;
+};
+
+}  // namespace tca
+
+struct tca_plan_s {
+  int d = 0;
+  int prec = TCA_F32;
+  int64_t n[tca::kMaxModes] = {1, 1, 1, 1};
+  int64_t m[tca::kMaxModes] = {1, 1, 1, 1};
+  int64_t N = 0, M = 0;
+  double lambda = 0.0;
+  tca::Mode mode[tca::kMaxModes];
+  int order_fwd[tca::kMaxModes];  // mode order for apply (shrinking first, expanding last)
+  int order_bwd[tca::kMaxModes];  // mode order for apply_T
+  bool all_band = true;
+  bool fused_ok = false;          // fused normal-operator sweep applies to this shape
+
+  int64_t ws_elems = 0;           // capacity of each ping-pong buffer (elements)
+  void* ws[2] = {nullptr, nullptr};
+  double* ws64[2] = {nullptr, nullptr};  // FP64 ping-pong for the true residual
+  int64_t ws64_elems = 0;
+
+  // Solver vectors (element type of the plan), allocated on first solve.
+  void* rhs = nullptr;
+  void* r = nullptr;
+  void* p[2] = {nullptr, nullptr};
+  void* q = nullptr;
+  double* rhs64 = nullptr;
+  double* res64 = nullptr;
+  void* stage_x = nullptr;  // host-pointer staging (n-shaped)
+  void* stage_b = nullptr;  // host-pointer staging (m-shaped)
+
+  tca::Scalars* scal = nullptr;  // device
+  tca::Scalars* scal_host = nullptr;  // pinned mirror
+  tca::Reduce red;
+
+  // Cached CUDA graph of `graph_iters` CG iterations for one x buffer.
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_x = nullptr;
+  int graph_iters = 0;
+  bool graph_profiled = false;
+  uint64_t graph_launches = 0;  // kernels per graph replay
+  cudaEvent_t sweep_ev[2 * tca::kMaxProfiledIters] = {};  // start/end per iteration of a profiled graph
+
+  int num_sms = 0;
+};
+
+namespace tca {
+
+// ---- error plumbing -------------------------------------------------------
+void set_cuda_error(cudaError_t e);
+void note_launches(uint64_t count);
+
+#define TCA_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) {                                 \
+      ::tca::set_cuda_error(_e);                             \
+      return TCA_ERR_CUDA;                                   \
+    }                                                        \
+  } while (0)
+
+#define TCA_TRY(expr)                                        \
+  do {                                                       \
+    tca_status _s = (expr);                                  \
+    if (_s != TCA_OK) return _s;                             \
+  } while (0)
+
+#define TCA_LAUNCH_CHECK()                                   \
+  do {                                                       \
+    ::tca::note_launches(1);                                 \
+    cudaError_t _e = cudaGetLastError();                     \
+    if (_e != cudaSuccess) {                                 \
+      ::tca::set_cuda_error(_e);                             \
+      return TCA_ERR_CUDA;                                   \
+    }                                                        \
+  } while (0)
+
+inline size_t elem_size(const tca_plan_s* p) { return p->prec == TCA_F64 ? 8 : 4; }
+
+// ---- launchers implemented in the .cu files --------------------------------
+// Mode product y = x x_k op over a tensor viewed as (O, n_in, I) -> (O, n_out, I).
+template <typename Tin, typename Tout, typename Tc>
+tca_status launch_mode_op(const ModeOp& op, const Tin* x, Tout* y, int64_t O, int64_t I,
+                          cudaStream_t s);
+
+// y (+)= lambda * sum_k (x x_k L_k) over the 4D view dims[4]; accumulate adds into y.
+template <typename Tin, typename Tout>
+tca_status launch_reg_add(const tca_plan_s* p, const Tin* x, Tout* y, const int64_t* dims,
+                          cudaStream_t s);
+
+// Normal operator through the generic (unfused) sequence, element type T.
+template <typename T>
+tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s);
+
+// FP64 normal operator applied to a float or double x (true residual).
+template <typename Tin>
+tca_status normal_fp64(tca_plan_s* p, const Tin* x, double* y, cudaStream_t s);
+
+// Chained apply / apply_T with device pointers.
+template <typename Tin, typename Tout, typename Tc>
+tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, void* const* ws,
+                       int64_t ws_elems, cudaStream_t s);
+
+// Fused FP32 sweep (fused_ok): optionally p_new = r + beta p_old, q = K p_new,
+// <p_new, q> reduced to alpha.  Returns TCA_ERR_UNSUPPORTED if not applicable.
+tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, float* p_new,
+                            float* q, bool cg_mode, cudaStream_t s);
+
+// Blocks used by grid-stride vector kernels.
+int vector_grid(const tca_plan_s* p, int64_t n);
+
+bool is_device_ptr(const void* ptr);
+tca_status ensure_stage(tca_plan_s* p);
+tca_status ensure_ws64_public(tca_plan_s* p);
+
+}  // namespace tca
+
+// ---- device helpers --------------------------------------------------------
+namespace tca {
+namespace dev {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide FP64 sum; result valid in thread 0.  `sh` needs blockDim/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// Last-block-finishes grid reduction.  Every block calls it with its partial;
+// the block that arrives last sums all partials in a fixed order and returns
+// true in thread 0 with the total in *total.  Deterministic for a fixed grid.
+__device__ __forceinline__ bool grid_sum_last(double v, Reduce red, double* total, double* sh) {
+  __shared__ bool am_last;
+  const double bs = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    red.partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned int t = atomicAdd(red.ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += ((volatile double*)red.partials)[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *red.ticket = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<double>(double v) { return (float)v; }
+
+}  // namespace dev
+}  // namespace tca

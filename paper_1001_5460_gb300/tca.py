@@ -1,0 +1,239 @@
+"""ctypes binding of the tca C ABI (include/tca.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Importing this module loads ``libtca.so`` and raises ImportError when
+it is missing - there is no CPU fallback.
+
+Data arguments may be torch tensors (CUDA or CPU) or NumPy arrays; they are
+passed to the library as raw pointers, so they must be C-contiguous and of the
+plan's element type (float64 for a TCA_F64 plan, float32 otherwise).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtca.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"tca CUDA library not built ({LIB_PATH} missing); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# --- enums (tca.h) ---
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_SHAPE = 2
+ERR_UNSUPPORTED = 3
+ERR_ALLOC = 4
+ERR_CUDA = 5
+ERR_NOT_CONVERGED = 6
+ERR_BREAKDOWN = 7
+ERR_TIMEOUT = 8
+
+F64, F32, BF16_IR, TF32_IR = 0, 1, 2, 3
+FACTOR_DENSE, FACTOR_ELL4 = 0, 1
+OP_FACTOR, OP_FACTOR_T, OP_GRAM = 0, 1, 2
+
+PRECISIONS = {"f64": F64, "f32": F32, "bf16_ir": BF16_IR, "tf32_ir": TF32_IR}
+
+
+class tca_factor(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("values", ctypes.c_void_p), ("col0", ctypes.c_void_p)]
+
+
+class tca_reg(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("reg_mode_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class tca_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("x0_given", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
+
+
+class tca_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("refinements", ctypes.c_int32), ("rel_res_true", ctypes.c_double),
+                ("rel_res_recursive", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_lib.tca_plan.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64p, ctypes.POINTER(tca_factor),
+                          ctypes.POINTER(tca_reg), ctypes.c_int, _vp]
+_lib.tca_plan.restype = ctypes.c_int
+for _name in ("tca_apply", "tca_apply_T", "tca_apply_normal"):
+    getattr(_lib, _name).argtypes = [_vp, _vp, _vp, _vp]
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.tca_apply_mode.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _i64p, _vp, _vp, _vp]
+_lib.tca_apply_mode.restype = ctypes.c_int
+_lib.tca_solve.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info), _vp]
+_lib.tca_solve.restype = ctypes.c_int
+_lib.tca_destroy.argtypes = [_vp]
+_lib.tca_destroy.restype = None
+_lib.tca_status_string.argtypes = [ctypes.c_int]
+_lib.tca_status_string.restype = ctypes.c_char_p
+_lib.tca_last_error_string.argtypes = []
+_lib.tca_last_error_string.restype = ctypes.c_char_p
+_lib.tca_kernel_launches.argtypes = [ctypes.c_int]
+_lib.tca_kernel_launches.restype = ctypes.c_uint64
+_lib.tca_version.argtypes = []
+_lib.tca_version.restype = ctypes.c_int
+
+
+class TcaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = _lib.tca_status_string(status).decode()
+        if status == ERR_CUDA:
+            msg += f" ({_lib.tca_last_error_string().decode()})"
+        super().__init__(f"{what}: {msg}")
+        self.status = status
+
+
+def _check(status: int, what: str, ok=(OK,)) -> int:
+    if status not in ok:
+        raise TcaError(status, what)
+    return status
+
+
+def _ptr(a) -> int:
+    """Raw data pointer of a torch tensor or NumPy array (must be contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)!r}")
+
+
+def _stream(stream) -> int:
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    try:
+        import torch
+
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch missing
+        pass
+    return 0
+
+
+def version() -> int:
+    return _lib.tca_version()
+
+
+def kernel_launches(reset: bool = False) -> int:
+    return int(_lib.tca_kernel_launches(1 if reset else 0))
+
+
+def exported_symbols() -> list[str]:
+    return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
+            "tca_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
+
+
+class Factor:
+    """Host copy of one mode's factor in the layout tca_factor describes."""
+
+    def __init__(self, kind: int, m: int, n: int, values: np.ndarray, col0: np.ndarray | None = None):
+        self.kind = kind
+        self.m = int(m)
+        self.n = int(n)
+        self.values = np.ascontiguousarray(values, dtype=np.float64)
+        self.col0 = None if col0 is None else np.ascontiguousarray(col0, dtype=np.int32)
+
+    @classmethod
+    def from_synth(cls, f) -> "Factor":
+        if f.kind == "dense":
+            return cls(FACTOR_DENSE, f.m, f.n, np.asarray(f.a))
+        return cls(FACTOR_ELL4, f.m, f.n, np.asarray(f.w), np.asarray(f.col0))
+
+
+class Plan:
+    """A tca plan: ordered spaces, separable operator, regulariser and precision."""
+
+    def __init__(self, shape, factors, lam: float = 0.0, reg_mask: int | None = None, precision="f32",
+                 stream=None):
+        self.shape = tuple(int(s) for s in shape)
+        self.order = len(self.shape)
+        self.factors = [f if isinstance(f, Factor) else Factor.from_synth(f) for f in factors]
+        self.sample_shape = tuple(f.m for f in self.factors)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.dtype = np.float64 if self.precision == F64 else np.float32
+        arr = (tca_factor * self.order)()
+        for k, f in enumerate(self.factors):
+            arr[k].kind = f.kind
+            arr[k].reserved = 0
+            arr[k].m = f.m
+            arr[k].n = f.n
+            arr[k].values = f.values.ctypes.data
+            arr[k].col0 = f.col0.ctypes.data if f.col0 is not None else None
+        n = (ctypes.c_int64 * self.order)(*self.shape)
+        reg = tca_reg(float(lam), (1 << self.order) - 1 if reg_mask is None else int(reg_mask), 0)
+        h = _vp()
+        _check(_lib.tca_plan(ctypes.byref(h), self.order, n, arr, ctypes.byref(reg), self.precision,
+                             _stream(stream)), "tca_plan")
+        self._h = h
+        self.lam = float(lam)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.tca_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, y, stream=None):
+        _check(_lib.tca_apply(self._h, _ptr(x), _ptr(y), _stream(stream)), "tca_apply")
+        return y
+
+    def apply_T(self, y, x, stream=None):
+        _check(_lib.tca_apply_T(self._h, _ptr(y), _ptr(x), _stream(stream)), "tca_apply_T")
+        return x
+
+    def apply_normal(self, x, y, stream=None):
+        _check(_lib.tca_apply_normal(self._h, _ptr(x), _ptr(y), _stream(stream)), "tca_apply_normal")
+        return y
+
+    def apply_mode(self, mode: int, op: int, dims, x, y, stream=None):
+        d = (ctypes.c_int64 * self.order)(*[int(v) for v in dims])
+        _check(_lib.tca_apply_mode(self._h, int(mode), int(op), d, _ptr(x), _ptr(y), _stream(stream)),
+               "tca_apply_mode")
+        return y
+
+    def solve(self, b, x, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
+              check_every: int = 16, inner_rtol: float = 0.0, max_refine: int = 0, stream=None,
+              raise_on_error: bool = True, profile: bool = False):
+        """Solve (A^T A + lambda R) x = A^T b; returns (status, info dict)."""
+        opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, float(inner_rtol),
+                              int(max_refine), int(check_every), 1 if profile else 0)
+        info = tca_solve_info()
+        st = _lib.tca_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
+        if raise_on_error:
+            _check(st, "tca_solve", ok=(OK, ERR_NOT_CONVERGED))
+        return st, {"iters": info.iters, "refinements": info.refinements, "rel_res_true": info.rel_res_true,
+                    "rel_res_recursive": info.rel_res_recursive, "seconds": info.seconds,
+                    "sweep_ms": info.sweep_ms, "sweep_launches": info.sweep_launches}
+
+
+def plan_from_instance(inst, precision="f32", reg_mask=None, stream=None) -> Plan:
+    """Plan for a synthetic ``synth.Instance``."""
+    return Plan(inst.shape, inst.factors, lam=inst.lam, reg_mask=reg_mask, precision=precision, stream=stream)

@@ -1,0 +1,86 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares (no GPU needed).
+
+Also exercises the argument checks that return before any device work.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tca():
+    from paper_1001_5460_gb300 import build
+
+    build.build()
+    from paper_1001_5460_gb300 import tca as t
+
+    return t
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names |= set(re.findall(r"^TCA_API\s+[\w\s\*]+?\b(tca_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_solve", "tca_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(tca):
+    lib = ctypes.CDLL(tca.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(tca):
+    assert tca._lib.tca_status_string(0) == b"ok"
+    assert tca._lib.tca_status_string(tca.ERR_SHAPE) == b"shape mismatch"
+    assert tca._lib.tca_status_string(99) == b"unknown status"
+    assert tca.version() >> 16 == 1
+
+
+def test_plan_rejects_bad_arguments_before_device_work(tca):
+    fac = (tca.tca_factor * 3)()
+    vals = np.ones((4, 3))
+    for k in range(3):
+        fac[k].kind = tca.FACTOR_DENSE
+        fac[k].m, fac[k].n = 4, 3
+        fac[k].values = vals.ctypes.data
+    n = (ctypes.c_int64 * 3)(3, 3, 3)
+    h = ctypes.c_void_p()
+    reg = tca.tca_reg(0.1, 7, 0)
+    # order must be 3 or 4
+    assert tca._lib.tca_plan(ctypes.byref(h), 2, n, fac, ctypes.byref(reg), tca.F32, None) == tca.ERR_INVALID_ARG
+    # factor n must match the space size
+    n_bad = (ctypes.c_int64 * 3)(3, 5, 3)
+    assert tca._lib.tca_plan(ctypes.byref(h), 3, n_bad, fac, ctypes.byref(reg), tca.F32, None) == tca.ERR_SHAPE
+    # unknown precision, negative lambda, null pointers
+    assert tca._lib.tca_plan(ctypes.byref(h), 3, n, fac, ctypes.byref(reg), 9, None) == tca.ERR_INVALID_ARG
+    reg_neg = tca.tca_reg(-1.0, 7, 0)
+    assert tca._lib.tca_plan(ctypes.byref(h), 3, n, fac, ctypes.byref(reg_neg), tca.F32, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_plan(None, 3, n, fac, ctypes.byref(reg), tca.F32, None) == tca.ERR_INVALID_ARG
+    fac[1].reserved = 1
+    assert tca._lib.tca_plan(ctypes.byref(h), 3, n, fac, ctypes.byref(reg), tca.F32, None) == tca.ERR_INVALID_ARG
+    # entry points reject a null plan
+    assert tca._lib.tca_apply(None, None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_solve(None, None, None, None, None, None) == tca.ERR_INVALID_ARG
+    tca._lib.tca_destroy(None)  # NULL is ignored
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The binding imports nothing from the oracle and the library sources name no oracle."""
+    pkg = os.path.join(ROOT, "paper_1001_5460_gb300")
+    for path in glob.glob(os.path.join(pkg, "*.py")) + glob.glob(os.path.join(pkg, "csrc", "*")):
+        text = open(path).read()
+        assert "import oracle" not in text and "from oracle" not in text, path

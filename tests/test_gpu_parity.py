@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Sizes span several tiles of every kernel and leave ragged tails; each case uses
+the same seeded inputs on both sides.  Tolerances: relative L2 error <= 1e-12
+for FP64 plans and <= 2e-5 for FP32 plans (derivation in the design notes).
+"""
+import numpy as np
+import pytest
+
+from oracle import tca_oracle as O
+from paper_1001_5460_gb300 import synth
+from tests.gpu_common import TOL_F32, TOL_F64, empty_dev, lib, need_cuda, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _bspline(shape, seed, lam=1e-3):
+    return synth.instance_bspline(shape, seed=seed, lam=lam, with_truth=False)
+
+
+def _dense(shape, seed, lam=1e-2):
+    rng = np.random.default_rng(seed)
+    facs = []
+    for n in shape:
+        m = int(np.ceil(1.5 * n))
+        facs.append(synth.Factor("dense", m, n, a=synth.dense_gaussian_factor(m, n, rng)))
+    return synth.Instance(tuple(shape), facs, None, None, lam, seed)
+
+
+CASES = [
+    ("bspline", (40, 37, 29, 8), "f32"),     # fused sweep, n4 = 8, ragged tiles
+    ("bspline", (23, 50, 45, 4), "f32"),     # fused sweep, n4 = 4
+    ("bspline", (33, 41, 70), "f32"),        # order 3: fused sweep with n4 = 1
+    ("bspline", (12, 13, 11, 16), "f32"),    # n4 = 16: generic sweeps
+    ("bspline", (9, 10, 7, 5), "f32"),       # n4 = 5: generic sweeps
+    ("bspline", (17, 14, 19, 3), "f64"),
+    ("dense", (13, 11, 9, 4), "f32"),
+    ("dense", (16, 16, 16), "f64"),
+    ("dense", (20, 7, 33), "f32"),
+]
+
+
+def _inst(kind, shape, seed):
+    return _bspline(shape, seed) if kind == "bspline" else _dense(shape, seed)
+
+
+@pytest.mark.parametrize("kind,shape,prec", CASES)
+def test_apply_and_apply_T(kind, shape, prec):
+    tca = lib()
+    inst = _inst(kind, shape, 100 + len(shape))
+    mats = [f.dense() for f in inst.factors]
+    plan = tca.plan_from_instance(inst, precision=prec)
+    dt = plan.dtype
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(inst.shape).astype(dt)
+    y = rng.standard_normal(inst.sample_shape).astype(dt)
+    ax = empty_dev(inst.sample_shape, dt)
+    aty = empty_dev(inst.shape, dt)
+    plan.apply(to_dev(x, dt), ax)
+    plan.apply_T(to_dev(y, dt), aty)
+    tol = TOL_F64 if prec == "f64" else TOL_F32
+    assert rel_l2(ax.cpu().numpy(), O.apply(x, mats)) < tol
+    assert rel_l2(aty.cpu().numpy(), O.apply_T(y, mats)) < tol
+
+
+@pytest.mark.parametrize("kind,shape,prec", CASES)
+def test_normal_operator(kind, shape, prec):
+    tca = lib()
+    inst = _inst(kind, shape, 200 + len(shape))
+    inst.lam = 0.05
+    mats = [f.dense() for f in inst.factors]
+    plan = tca.plan_from_instance(inst, precision=prec)
+    dt = plan.dtype
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(inst.shape).astype(dt)
+    kx = empty_dev(inst.shape, dt)
+    plan.apply_normal(to_dev(x, dt), kx)
+    ref = O.normal_apply(x, mats, inst.lam)
+    tol = TOL_F64 if prec == "f64" else TOL_F32
+    got = kx.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) < tol
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_single_mode_products(mode, op):
+    tca = lib()
+    inst = _bspline((21, 18, 35, 8), 300)
+    mats = [f.dense() for f in inst.factors]
+    plan = tca.plan_from_instance(inst, precision="f32")
+    dims = list(inst.shape)
+    if op == tca.OP_FACTOR_T:
+        dims[mode] = inst.factors[mode].m
+    a = mats[mode]
+    mat = a if op == tca.OP_FACTOR else a.T if op == tca.OP_FACTOR_T else a.T @ a
+    out_dims = list(dims)
+    out_dims[mode] = mat.shape[0]
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(dims).astype(np.float32)
+    y = empty_dev(out_dims, np.float32)
+    plan.apply_mode(mode, op, dims, to_dev(x, np.float32), y)
+    assert rel_l2(y.cpu().numpy(), O.mode_product(x, mat, mode)) < TOL_F32
+
+
+def test_ragged_and_degenerate_shapes():
+    """Modes of size 1 and 2 (no regulariser), single-sample factors, prime sizes."""
+    tca = lib()
+    rng = np.random.default_rng(10)
+    for shape in [(1, 5, 7), (2, 3, 1, 4), (7, 1, 13, 8), (3, 17, 2)]:
+        facs = []
+        for n in shape:
+            m = max(1, int(round(1.5 * n)))
+            col0, w, _ = synth.bspline_factor_ell4(n, m, rng)
+            facs.append(synth.Factor("ell4", m, n, col0=col0, w=w))
+        inst = synth.Instance(shape, facs, None, None, 0.1, 0)
+        mats = [f.dense() for f in facs]
+        for prec in ("f32", "f64"):
+            plan = tca.plan_from_instance(inst, precision=prec)
+            dt = plan.dtype
+            x = rng.standard_normal(shape).astype(dt)
+            kx = empty_dev(shape, dt)
+            plan.apply_normal(to_dev(x, dt), kx)
+            tol = TOL_F64 if prec == "f64" else TOL_F32
+            assert rel_l2(kx.cpu().numpy(), O.normal_apply(x, mats, 0.1)) < tol, (shape, prec)
+
+
+def test_solve_dense_3d_fp64_matches_cholesky():
+    """Dense 16^3 problem, FP64, CG to 1e-10 vs the Cholesky solve of the reshaped system."""
+    tca = lib()
+    inst = synth.instance_dense_3d(seed=0)
+    mats = [f.dense() for f in inst.factors]
+    b = O.apply(inst.x_true, mats) + inst.noise
+    plan = tca.plan_from_instance(inst, precision="f64")
+    x = empty_dev(inst.shape, np.float64)
+    st, info = plan.solve(to_dev(b, np.float64), x, rtol=1e-10)
+    assert st == tca.OK
+    x_direct = O.direct_solve(b, mats, inst.lam, inst.shape)
+    assert rel_l2(x.cpu().numpy(), x_direct) < 1e-8
+    assert info["rel_res_true"] <= 1e-10
+    assert O.rel_residual(x.cpu().numpy(), b, mats, inst.lam) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [(32, 28, 24, 8), (30, 26, 40), (16, 18, 14, 16), (20, 22, 18, 4)])
+def test_solve_bspline_fp32(shape):
+    """FP32 CG to a true relative residual of 1e-6; solution matches the FP64 oracle's."""
+    tca = lib()
+    inst = synth.instance_bspline(shape, seed=400 + len(shape), dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-6)
+    assert st == tca.OK, info
+    got = x.cpu().numpy()
+    # The oracle's own verdict on the GPU solution (FP64, long way).
+    assert O.rel_residual(got, b.astype(np.float64), mats, inst.lam) <= 1.5e-6
+    ref = O.solve(b.astype(np.float64), mats, inst.lam, rtol=1e-12).x
+    assert rel_l2(got, ref) < 5e-5
+    assert info["rel_res_true"] <= 1e-6
+    assert abs(info["rel_res_true"] - O.rel_residual(got, b.astype(np.float64), mats, inst.lam)) < 1e-7
+
+
+def test_solve_host_buffers_match_device():
+    tca = lib()
+    torch = need_cuda()
+    inst = synth.instance_bspline((24, 20, 22, 8), seed=500, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    xd = empty_dev(inst.shape, np.float32)
+    plan.solve(to_dev(b, np.float32), xd, rtol=1e-6)
+    xh = np.zeros(inst.shape, np.float32)
+    st, info = plan.solve(np.ascontiguousarray(b), xh, rtol=1e-6)
+    assert st == tca.OK
+    np.testing.assert_array_equal(xh, xd.cpu().numpy())
+    pinned = torch.from_numpy(b).pin_memory()
+    xp = torch.zeros(inst.shape, dtype=torch.float32).pin_memory()
+    plan.solve(pinned, xp, rtol=1e-6)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(xp.numpy(), xd.cpu().numpy())
+
+
+def test_solve_with_initial_guess_and_max_iter():
+    tca = lib()
+    inst = synth.instance_bspline((20, 18, 16, 4), seed=600, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-6)
+    full_iters = info["iters"]
+    # Warm start from the solution: converges at once.
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-5, x0_given=True)
+    assert st == tca.OK and info["iters"] <= 2
+    # max_iter cap reports NOT_CONVERGED with x still filled.
+    x2 = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x2, rtol=1e-9, max_iter=5, raise_on_error=False)
+    assert st == tca.ERR_NOT_CONVERGED and info["iters"] == 5
+    assert np.all(np.isfinite(x2.cpu().numpy()))
+    assert full_iters > 5
+
+
+def test_zero_rhs():
+    tca = lib()
+    inst = synth.instance_bspline((10, 9, 8, 4), seed=700, with_truth=False)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    b = np.zeros(inst.sample_shape, np.float32)
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x)
+    assert st == tca.OK and info["iters"] == 0
+    assert np.all(x.cpu().numpy() == 0)
+
+
+@pytest.mark.slow
+def test_full_size_normal_operator_sampled():
+    """160x160x160x8 with 240^3x12 B-spline factors (the timed workload): K x on sampled points."""
+    tca = lib()
+    inst = synth.instance_bspline((160, 160, 160, 8), seed=2, with_truth=False)
+    mats = [f.dense() for f in inst.factors]
+    plan = tca.plan_from_instance(inst, precision="f32")
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(inst.shape, dtype=np.float32)
+    kx = empty_dev(inst.shape, np.float32)
+    plan.apply_normal(to_dev(x, np.float32), kx)
+    got = kx.cpu().numpy()
+    pts = [tuple(int(rng.integers(0, n)) for n in inst.shape) for _ in range(40)]
+    pts += [(0, 0, 0, 0), (159, 159, 159, 7), (0, 159, 3, 7), (80, 0, 159, 0)]
+    for pt in pts:
+        ref = O.normal_apply_at(x, mats, inst.lam, pt)
+        assert abs(got[pt] - ref) <= 1e-5 * (abs(ref) + 1.0), (pt, got[pt], ref)

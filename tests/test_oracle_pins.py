@@ -325,3 +325,24 @@ def test_pin_catches_wrong_cg_sign():
         q = kop(p); alpha = rho / O.inner(p, q); c = c + alpha * p; r = r + alpha * q
         rho1 = O.inner(r, r); p = r + (rho1 / rho) * p; rho = rho1
     assert not np.allclose(c, ref, rtol=1e-4)
+
+
+def test_sampled_oracle_matches_full():
+    """Point-wise (A x)[s] and (K x)[i] agree with the full oracle evaluations."""
+    inst = synth.instance_bspline((9, 8, 10, 4), seed=21, lam=0.2, with_truth=False)
+    mats = [f.dense() for f in inst.factors]
+    rng = np.random.default_rng(22)
+    x = rng.standard_normal(inst.shape)
+    ax = O.apply(x, mats)
+    kx = O.normal_apply(x, mats, 0.2)
+    for _ in range(12):
+        s = tuple(int(rng.integers(0, m)) for m in inst.sample_shape)
+        i = tuple(int(rng.integers(0, n)) for n in inst.shape)
+        assert O.apply_at(x, mats, s) == pytest.approx(ax[s], rel=1e-12, abs=1e-12)
+        assert O.normal_apply_at(x, mats, 0.2, i) == pytest.approx(kx[i], rel=1e-12, abs=1e-12)
+    # dense factors too
+    mats = [rng.standard_normal((5, 4)), rng.standard_normal((6, 3)), rng.standard_normal((4, 5))]
+    x = rng.standard_normal((4, 3, 5))
+    kx = O.normal_apply(x, mats, 0.3)
+    for i in [(0, 0, 0), (3, 2, 4), (1, 1, 2)]:
+        assert O.normal_apply_at(x, mats, 0.3, i) == pytest.approx(kx[i], rel=1e-12)
