@@ -44,7 +44,43 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation"],
+                    help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
+
+
+def run_case(args, local):
+    """One kernel alone on the full-size tensors: small device footprint for profilers."""
+    import torch
+
+    from paper_1001_5460_gb300 import synth, tca
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, with_truth=False)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    x = torch.randn(SHAPE, dtype=torch.float32, device=device)
+    N = x.numel()
+    if args.case == "normal":
+        y = torch.empty_like(x)
+        fn, nbytes = (lambda: plan.apply_normal(x, y)), 2 * N * 4
+    elif args.case == "gram":
+        y = torch.empty_like(x)
+        fn, nbytes = (lambda: plan.apply_mode(0, tca.OP_GRAM, SHAPE, x, y)), 2 * N * 4
+    else:
+        y = torch.empty((inst.factors[0].m,) + SHAPE[1:], dtype=torch.float32, device=device)
+        fn, nbytes = (lambda: plan.apply_mode(0, tca.OP_FACTOR, SHAPE, x, y)), (N + y.numel()) * 4
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"case": args.case, "ms": round(ms, 5), "gbs": round(nbytes / ms / 1e6, 1)}), flush=True)
 
 
 def dist_setup(n_gpus):
@@ -338,7 +374,9 @@ def run_tca(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
-    if args.impl == "reference":
+    if args.case:
+        run_case(args, local)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_tca(args, rank, world, local)

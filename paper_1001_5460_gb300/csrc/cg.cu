@@ -204,7 +204,7 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, const T* pold, T* pnew,
   T* q = (T*)p->q;
   const int grid = std::min(vector_grid(p, N), first_reduce(p).max_blocks);
   const bool fused = sizeof(T) == 4 && p->fused_ok;
-  if (ev_begin) TCA_CUDA_TRY(cudaEventRecord(ev_begin, s));
+  if (ev_begin) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_begin, s, cudaEventRecordExternal));
   if constexpr (sizeof(T) == 4) {
     if (fused) TCA_TRY(normal_fused_f32(p, r, pold, pnew, q, true, s));
   }
@@ -215,7 +215,7 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, const T* pold, T* pnew,
     cg_alpha_kernel<T><<<grid, kVecThreads, 0, s>>>(pnew, q, N, p->scal, first_reduce(p));
     TCA_LAUNCH_CHECK();
   }
-  if (ev_end) TCA_CUDA_TRY(cudaEventRecord(ev_end, s));
+  if (ev_end) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_end, s, cudaEventRecordExternal));
   cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p));
   TCA_LAUNCH_CHECK();
   return TCA_OK;
