@@ -181,6 +181,25 @@ typedef struct {
 TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
                      tca_solve_info* info, cudaStream_t stream);
 
+/* Relative residual ||rhs - kx||_2 / ||rhs||_2 of two FP64 device vectors of
+ * length n, written to *out (device memory, one double).  If ||rhs|| is zero
+ * the absolute norm ||rhs - kx|| is written instead (0 for n = 0).
+ *
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory when they check a solution - code with a fixed
+ * memory budget after start-up, device memory owned by another allocator, or
+ * a hook that runs while the caller's allocator is locked.  It allocates
+ * nothing: its reduction scratch is a fixed 256 KiB device array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's address (set-up),
+ * so make that first call before any stream capture.  n may not exceed
+ * 134,217,728 (TCA_ERR_UNSUPPORTED, message in tca_last_error_string()).
+ * Every call shares the scratch, which keeps the last call's contents; calls
+ * that overlap on the GPU (unordered streams) race and give undefined
+ * results.  Asynchronous on the stream. */
+TCA_API tca_status tca_rel_residual_noalloc(const double* rhs, const double* kx, int64_t n, double* out,
+                                            cudaStream_t stream);
+
 /* Free a plan and its device memory (NULL is ignored). */
 TCA_API void tca_destroy(tca_plan_t plan);
 

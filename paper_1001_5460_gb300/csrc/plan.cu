@@ -17,6 +17,7 @@ static thread_local uint64_t g_launches = 0;
 void set_cuda_error(cudaError_t e) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
+void set_error_message(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 void note_launches(uint64_t count) { g_launches += count; }
 
 int vector_grid(const tca_plan_s* p, int64_t n) {

@@ -132,6 +132,7 @@ namespace tca {
 
 // ---- error plumbing -------------------------------------------------------
 void set_cuda_error(cudaError_t e);
+void set_error_message(const char* msg);
 void note_launches(uint64_t count);
 
 #define TCA_CUDA_TRY(expr)                                   \

@@ -76,6 +76,8 @@ _lib.tca_apply_mode.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _i64p, _vp, _vp
 _lib.tca_apply_mode.restype = ctypes.c_int
 _lib.tca_solve.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info), _vp]
 _lib.tca_solve.restype = ctypes.c_int
+_lib.tca_rel_residual_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+_lib.tca_rel_residual_noalloc.restype = ctypes.c_int
 _lib.tca_destroy.argtypes = [_vp]
 _lib.tca_destroy.restype = None
 _lib.tca_status_string.argtypes = [ctypes.c_int]
@@ -135,6 +137,17 @@ def version() -> int:
 
 def kernel_launches(reset: bool = False) -> int:
     return int(_lib.tca_kernel_launches(1 if reset else 0))
+
+
+def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
+    """||rhs - kx|| / ||rhs|| of two FP64 device vectors into out (one FP64 device value).
+
+    For callers that must not allocate device memory at this point: the library
+    keeps the reduction scratch in a fixed device array of its own.
+    """
+    n = int(rhs.numel() if hasattr(rhs, "numel") else np.asarray(rhs).size)
+    return _check(_lib.tca_rel_residual_noalloc(_ptr(rhs), _ptr(kx), n, _ptr(out), _stream(stream)),
+                  "tca_rel_residual_noalloc")
 
 
 def exported_symbols() -> list[str]:
