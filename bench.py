@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
-    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation"],
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -61,6 +61,14 @@ def run_case(args, local):
     plan = tca.plan_from_instance(inst, precision="f32")
     x = torch.randn(SHAPE, dtype=torch.float32, device=device)
     N = x.numel()
+    if args.case == "cgsweep":
+        # A few CG iterations on random data: the CG-mode fused sweep in its solve context.
+        b = torch.randn(inst.sample_shape, dtype=torch.float32, device=device)
+        for _ in range(args.warmup + args.steps):
+            st, info = plan.solve(b, x, rtol=1e-30, max_iter=4, raise_on_error=False, profile=True)
+        ms = info["sweep_ms"] / max(info["sweep_launches"], 1)
+        print(json.dumps({"case": args.case, "ms": round(ms, 5), "gbs": round(4 * N * 4 / ms / 1e6, 1)}), flush=True)
+        return
     if args.case == "normal":
         y = torch.empty_like(x)
         fn, nbytes = (lambda: plan.apply_normal(x, y)), 2 * N * 4

@@ -19,8 +19,18 @@
 // In CG mode the kernel also forms the new direction p = r + beta p_old on the
 // fly (halo included), stores it, and reduces <p, q> to alpha = rho / <p, q>
 // (last block; Fig. 2, alpha := rho/(P+*Q)).
+//
+// Shared-memory layout is chosen for conflict-free access: every row pitch holds
+// an odd number of 16-byte chunks and stage A maps consecutive lanes to
+// consecutive rows, so eight lanes of a 128-bit access phase hit eight distinct
+// bank quads; the per-stage buffers are double-buffered so that a plane costs
+// two block barriers (three in CG mode).  Products are issued as packed FP32
+// pairs (fma.rn.f32x2) wherever both operands pair up naturally, and the
+// accumulator ring along mode 1 is indexed by compile-time slots (a switch on
+// j mod 7) so it never moves between registers.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "tca_internal.cuh"
 
@@ -58,32 +68,48 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// d = a * b + c on a pair of FP32 lanes (one packed FMA instruction).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
 template <int N4, int T2, int T3, int T3P, int NT, int STAGES, bool CG>
 struct Cfg {
   static constexpr int H2 = T2 + 6, H3 = T3 + 6;
-  static constexpr int TILE = H2 * H3 * N4;   // halo tile, floats
-  static constexpr int CORE = T2 * T3 * N4;
-  static constexpr int S1N = H2 * T3 * N4;
-  static constexpr int NIN = CG ? 2 : 1;      // loaded tensors per plane
-  static constexpr int RB = NT / (N4 * T3);   // row blocks in stage B
-  static constexpr int P = T2 / RB;           // rows per thread in stage B
-  static constexpr int PENC = H2 * (T3 / T3P);
+  // Row pitches (floats) with an odd number of 16-byte chunks (odd word count
+  // for N4 = 1): eight lanes on eight consecutive rows then hit eight distinct
+  // bank quads.
+  static constexpr int pitch(int cols) {
+    return N4 == 1 ? (cols | 1) : (cols * N4 + (((cols * N4 / 4) % 2 == 0) ? 4 : 0));
+  }
+  static constexpr int ROW = pitch(H3);            // floats per halo-tile row
+  static constexpr int TILE = ((H2 * ROW + 31) / 32) * 32;
+  static constexpr int ROW1 = pitch(T3);           // floats per S1 / SL row
+  static constexpr int S1N = ((H2 * ROW1 + 31) / 32) * 32;
+  static constexpr int SLN = ((T2 * ROW1 + 31) / 32) * 32;
+  static constexpr int CORE = T2 * T3 * N4;        // thread-private ring slots
+  static constexpr int NIN = CG ? 2 : 1;
+  static constexpr int RB = NT / (N4 * T3);        // row blocks in stage B
+  static constexpr int P = T2 / RB;                // rows per thread in stage B
+  static constexpr int NBQ = T3 / T3P;             // pencils per halo row
+  static constexpr int RPB = ((H2 + 7) / 8) * 8;   // pencil slots per column block
   static_assert(NT % (N4 * T3) == 0, "stage-B mapping");
-  static_assert(T2 % RB == 0, "stage-B rows");
+  static_assert(T2 % RB == 0 && P % 4 == 0, "stage-B rows come in pairs of pairs");
   static_assert(T3 % T3P == 0, "stage-A pencils");
+  static_assert(N4 == 1 || N4 % 4 == 0, "fastest mode 1, 4 or 8");
+  static constexpr int NB = CG ? 2 : 1;            // double-buffered p tile in CG mode
   // shared memory carve-up (floats)
   static constexpr int OFF_IN = 0;
   static constexpr int OFF_P = OFF_IN + STAGES * NIN * TILE;
-  static constexpr int OFF_S1 = OFF_P + (CG ? TILE : 0);
-  static constexpr int OFF_SL = OFF_S1 + S1N;
-  static constexpr int OFF_RING = OFF_SL + CORE;
-  static constexpr int OFF_G2 = OFF_RING + (CG ? 4 * CORE : 0);
-  static constexpr int OFF_L2 = OFF_G2 + T2 * 7;
-  static constexpr int OFF_G3 = OFF_L2 + T2 * 5;
-  static constexpr int OFF_L3 = OFF_G3 + T3 * 7;
-  static constexpr int OFF_G4 = OFF_L3 + T3 * 5;
-  static constexpr int OFF_L4 = OFF_G4 + N4 * 7;
-  static constexpr int OFF_RED = ((OFF_L4 + N4 * 5 + 1) / 2) * 2;  // doubles, 8B aligned
+  static constexpr int OFF_S1 = OFF_P + (CG ? NB * TILE : 0);
+  static constexpr int OFF_SL = OFF_S1 + 2 * S1N;
+  static constexpr int OFF_RING = OFF_SL + 2 * SLN;
+  static constexpr int OFF_G3 = OFF_RING + (CG ? 4 * CORE : 0);   // [T3][8]
+  static constexpr int OFF_L3 = OFF_G3 + T3 * 8;                  // [T3][8]
+  static constexpr int OFF_G4 = OFF_L3 + T3 * 8;                  // [7][N4]  (offset-major)
+  static constexpr int OFF_L4 = OFF_G4 + 7 * N4;                  // [5][N4]
+  static constexpr int OFF_G2 = ((OFF_L4 + 5 * N4 + 3) / 4) * 4;  // [7][T2]  (offset-major)
+  static constexpr int OFF_L2 = OFF_G2 + 7 * T2;                  // [5][T2]
+  static constexpr int OFF_RED = ((OFF_L2 + 5 * T2 + 3) / 4) * 4; // doubles
   static constexpr int FLOATS = OFF_RED + 2 * (NT / 32);
   static constexpr size_t BYTES = sizeof(float) * FLOATS;
 };
@@ -91,7 +117,7 @@ struct Cfg {
 template <int N4, int T2, int T3, int T3P, int NT, int STAGES, bool CG>
 __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
   using C = Cfg<N4, T2, T3, T3P, NT, STAGES, CG>;
-  constexpr int H3 = C::H3, P = C::P;
+  constexpr int H2 = C::H2, ROW = C::ROW, ROW1 = C::ROW1, P = C::P;
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
 
@@ -112,262 +138,407 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
   const int je = min(n1, c1 + kGramHalf);
 
   float* s_in = sm + C::OFF_IN;
-  float* s_p = CG ? sm + C::OFF_P : nullptr;
-  float* s_s1 = sm + C::OFF_S1;
-  float* s_sl = sm + C::OFF_SL;
   float* s_ring = sm + C::OFF_RING;
-  float* g2s = sm + C::OFF_G2;
-  float* l2s = sm + C::OFF_L2;
   float* g3s = sm + C::OFF_G3;
   float* l3s = sm + C::OFF_L3;
   float* g4s = sm + C::OFF_G4;
   float* l4s = sm + C::OFF_L4;
+  float* g2s = sm + C::OFF_G2;
+  float* l2s = sm + C::OFF_L2;
   double* s_red = reinterpret_cast<double*>(sm + C::OFF_RED);
 
-  // Tile coefficient tables (rows outside the domain are zero).
-  for (int t = tid; t < T2 * 7; t += NT) {
-    const int r = t / 7, i2 = i2_0 + r;
-    g2s[t] = i2 < n2 ? a.g[1][(int64_t)i2 * 7 + t % 7] : 0.f;
+  // Tile coefficient tables (entries outside the domain are zero).
+  for (int t = tid; t < T3 * 8; t += NT) {
+    const int r = t >> 3, e = t & 7, i3 = i3_0 + r;
+    g3s[t] = (i3 < n3 && e < 7) ? a.g[2][(int64_t)i3 * 7 + e] : 0.f;
+    l3s[t] = (i3 < n3 && e < 5) ? a.l[2][(int64_t)i3 * 5 + e] : 0.f;
   }
-  for (int t = tid; t < T2 * 5; t += NT) {
-    const int r = t / 5, i2 = i2_0 + r;
-    l2s[t] = i2 < n2 ? a.l[1][(int64_t)i2 * 5 + t % 5] : 0.f;
-  }
-  for (int t = tid; t < T3 * 7; t += NT) {
-    const int r = t / 7, i3 = i3_0 + r;
-    g3s[t] = i3 < n3 ? a.g[2][(int64_t)i3 * 7 + t % 7] : 0.f;
-  }
-  for (int t = tid; t < T3 * 5; t += NT) {
-    const int r = t / 5, i3 = i3_0 + r;
-    l3s[t] = i3 < n3 ? a.l[2][(int64_t)i3 * 5 + t % 5] : 0.f;
+  for (int t = tid; t < 7 * T2; t += NT) {
+    const int e = t / T2, r = t % T2, i2 = i2_0 + r;
+    g2s[t] = i2 < n2 ? a.g[1][(int64_t)i2 * 7 + e] : 0.f;
+    if (e < 5) l2s[t] = i2 < n2 ? a.l[1][(int64_t)i2 * 5 + e] : 0.f;
   }
   if constexpr (N4 > 1) {
-    for (int t = tid; t < N4 * 7; t += NT) g4s[t] = a.g[3][t];
-    for (int t = tid; t < N4 * 5; t += NT) l4s[t] = a.l[3][t];
+    for (int t = tid; t < 7 * N4; t += NT) {
+      const int e = t / N4, i4 = t % N4;
+      g4s[t] = a.g[3][i4 * 7 + e];
+      if (e < 5) l4s[t] = a.l[3][i4 * 5 + e];
+    }
   }
 
   const int64_t plane = (int64_t)n2 * n3 * N4;
 
-  // Issue the asynchronous copies of plane jj (halo tile) into stage buffer buf.
+  // Asynchronous copies of plane jj (halo tile) into stage buffer buf.
+  // Each thread's share of the halo-tile copy is the same for every plane:
+  // its shared-memory offsets and in-plane source offsets (-1: outside the
+  // domain, zero fill) are computed once.
+  constexpr int CW = (N4 % 4 == 0) ? 4 : 1;             // floats per copy
+  constexpr int ELEMS = H2 * C::H3 * (N4 / CW);         // copies per tensor and plane
+  constexpr int NCP = (ELEMS + NT - 1) / NT;
+  int cp_dst[NCP], cp_src[NCP];
+#pragma unroll
+  for (int i = 0; i < NCP; ++i) {
+    const int t = tid + i * NT;
+    cp_dst[i] = -1;
+    cp_src[i] = -1;
+    if (t < ELEMS) {
+      const int v = t % (N4 / CW), rc = t / (N4 / CW);
+      const int cc = rc % C::H3, rr = rc / C::H3;
+      const int i2 = i2_0 - 3 + rr, i3 = i3_0 - 3 + cc;
+      const bool ok = (unsigned)i2 < (unsigned)n2 && (unsigned)i3 < (unsigned)n3;
+      cp_dst[i] = rr * ROW + cc * N4 + CW * v;
+      cp_src[i] = ok ? (i2 * n3 + i3) * N4 + CW * v : -1;
+    }
+  }
   auto issue = [&](int jj, int buf) {
-#pragma unroll 1
+#pragma unroll
     for (int src_i = 0; src_i < C::NIN; ++src_i) {
       const float* g = (CG && src_i == 0) ? a.r : a.pold;
       float* dst = s_in + (buf * C::NIN + src_i) * C::TILE;
       const float* gp = g + (int64_t)jj * plane;
-      if constexpr (N4 % 4 == 0) {
-        constexpr int V = N4 / 4;  // float4 per (row, col)
-        for (int t = tid; t < C::H2 * H3 * V; t += NT) {
-          const int v = t % V, rc = t / V;
-          const int cc = rc % H3, rr = rc / H3;
-          const int i2 = i2_0 - 3 + rr, i3 = i3_0 - 3 + cc;
-          const bool ok = (unsigned)i2 < (unsigned)n2 && (unsigned)i3 < (unsigned)n3;
-          const float* src = ok ? gp + ((int64_t)i2 * n3 + i3) * N4 + 4 * v : g;
-          cp_async16(dst + (rr * H3 + cc) * N4 + 4 * v, src, ok);
-        }
-      } else {
-        for (int t = tid; t < C::H2 * H3 * N4; t += NT) {
-          const int i4 = t % N4, rc = t / N4;
-          const int cc = rc % H3, rr = rc / H3;
-          const int i2 = i2_0 - 3 + rr, i3 = i3_0 - 3 + cc;
-          const bool ok = (unsigned)i2 < (unsigned)n2 && (unsigned)i3 < (unsigned)n3;
-          const float* src = ok ? gp + ((int64_t)i2 * n3 + i3) * N4 + i4 : g;
-          cp_async4(dst + t, src, ok);
-        }
+#pragma unroll
+      for (int i = 0; i < NCP; ++i) {
+        if (cp_dst[i] < 0) continue;
+        const bool ok = cp_src[i] >= 0;
+        if constexpr (CW == 4) cp_async16(dst + cp_dst[i], ok ? gp + cp_src[i] : g, ok);
+        else cp_async4(dst + cp_dst[i], ok ? gp + cp_src[i] : g, ok);
       }
     }
   };
 
-  // Stage-B thread mapping.
+  // Stage-B thread mapping: one column (bcol, i4b), P consecutive core rows.
   const int i4b = tid % N4;
   const int bcol = (tid / N4) % T3;
   const int a0 = (tid / (N4 * T3)) * P;
   const bool col_ok = (i3_0 + bcol) < n3;
+  // In-plane offset of the thread's first row and a bit per row inside the domain.
+  const int64_t out_base = ((int64_t)(i2_0 + a0) * n3 + i3_0 + bcol) * N4 + i4b;
+  const int64_t row_step = (int64_t)n3 * N4;
+  unsigned row_ok = 0;
+#pragma unroll
+  for (int k = 0; k < P; ++k) row_ok |= (col_ok && (i2_0 + a0 + k) < n2) ? (1u << k) : 0u;
 
-  float acc[P][7];
+  float2 acc[P / 2][7];
 #pragma unroll
-  for (int k = 0; k < P; ++k)
+  for (int k = 0; k < P / 2; ++k)
 #pragma unroll
-    for (int e = 0; e < 7; ++e) acc[k][e] = 0.f;
+    for (int e = 0; e < 7; ++e) acc[k][e] = make_float2(0.f, 0.f);
   double dot = 0.0;
+  // Per-plane stage-B results (pairs of rows) consumed by the ring update.
+  float2 w2[P / 2], lin2[P / 2], pc2[P / 2];
+  float g1r[7], l1r[5];
+#pragma unroll
+  for (int k2 = 0; k2 < P / 2; ++k2) w2[k2] = lin2[k2] = pc2[k2] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int e = 0; e < 7; ++e) g1r[e] = 0.f;
+#pragma unroll
+  for (int e = 0; e < 5; ++e) l1r[e] = 0.f;
 
-  // Prologue: planes jb .. jb+STAGES-2.
 #pragma unroll 1
   for (int s = 0; s < STAGES - 1; ++s) {
     if (jb + s < je) issue(jb + s, s);
     cp_async_commit();
   }
-  __syncthreads();  // coefficient tables visible
 
 #pragma unroll 1
   for (int j = jb; j < c1 + kGramHalf; ++j) {
     const int it = j - jb;
     const bool have = j < je;
-    {
-      const int jn = j + STAGES - 1;
-      if (jn < je) issue(jn, (it + STAGES - 1) % STAGES);
-      cp_async_commit();
-    }
+    const int par = it & 1;
     if (have) {
-      cp_async_wait<STAGES - 1>();
+      cp_async_wait<STAGES - 2>();
+      // Plane j landed for every thread; every thread is also done with plane
+      // j-1, whose stage buffer the next copy reuses.  (On the first pass this
+      // barrier also publishes the coefficient tables.)
       __syncthreads();
+      {
+        const int jn = j + STAGES - 1;
+        if (jn < je) issue(jn, (it + STAGES - 1) % STAGES);
+        cp_async_commit();
+      }
       const int buf = it % STAGES;
       const float* src;
       if constexpr (CG) {
         const float4* rr = reinterpret_cast<const float4*>(s_in + (buf * 2 + 0) * C::TILE);
         const float4* pp = reinterpret_cast<const float4*>(s_in + (buf * 2 + 1) * C::TILE);
-        float4* out = reinterpret_cast<float4*>(s_p);
-        static_assert(C::TILE % 4 == 0, "tile must hold whole float4");
+        float* pdst = sm + C::OFF_P + par * C::TILE;
+        float4* out = reinterpret_cast<float4*>(pdst);
         for (int t = tid; t < C::TILE / 4; t += NT) {
           const float4 x = rr[t], y = pp[t];
           out[t] = make_float4(fmaf(beta, y.x, x.x), fmaf(beta, y.y, x.y), fmaf(beta, y.z, x.z),
                                fmaf(beta, y.w, x.w));
         }
         __syncthreads();
-        src = s_p;
+        src = pdst;
       } else {
         src = s_in + buf * C::TILE;
       }
+      float* s_s1 = sm + C::OFF_S1 + par * C::S1N;
+      float* s_sl = sm + C::OFF_SL + par * C::SLN;
 
-      // ---- stage A: G_3 then G_4 along the rows of the halo tile ----
+      // ---- stage A: G_3 then G_4 along rows of the halo tile; L_3 + L_4 on core rows ----
 #pragma unroll 1
-      for (int pc = tid; pc < C::PENC; pc += NT) {
-        const int ar = pc / (T3 / T3P);
-        const int b0 = (pc % (T3 / T3P)) * T3P;
-        float v[T3P + 6][N4];
+      for (int slot = tid; slot < C::RPB * C::NBQ; slot += NT) {
+        const int ar = slot % C::RPB;
+        const int bq = slot / C::RPB;
+        if (ar >= H2) continue;
+        const int b0 = bq * T3P;
+        constexpr int NV = (N4 + 1) / 2;  // pairs per column (N4 = 1 keeps one lane in .x)
+        float2 v[T3P + 6][NV];
+        const float* rowp = src + ar * ROW + b0 * N4;
+        if constexpr (N4 == 8) {
 #pragma unroll
-        for (int t = 0; t < T3P + 6; ++t) {
-          const float* row = src + (ar * H3 + b0 + t) * N4;
-          if constexpr (N4 % 4 == 0) {
-#pragma unroll
-            for (int q4 = 0; q4 < N4 / 4; ++q4) {
-              const float4 f = reinterpret_cast<const float4*>(row)[q4];
-              v[t][4 * q4 + 0] = f.x; v[t][4 * q4 + 1] = f.y; v[t][4 * q4 + 2] = f.z; v[t][4 * q4 + 3] = f.w;
-            }
-          } else {
-#pragma unroll
-            for (int i4 = 0; i4 < N4; ++i4) v[t][i4] = row[i4];
+          for (int t = 0; t < T3P + 6; ++t) {
+            const float4 lo = reinterpret_cast<const float4*>(rowp + t * N4)[0];
+            const float4 hi = reinterpret_cast<const float4*>(rowp + t * N4)[1];
+            v[t][0] = make_float2(lo.x, lo.y); v[t][1] = make_float2(lo.z, lo.w);
+            v[t][2] = make_float2(hi.x, hi.y); v[t][3] = make_float2(hi.z, hi.w);
           }
+        } else if constexpr (N4 == 4) {
+#pragma unroll
+          for (int t = 0; t < T3P + 6; ++t) {
+            const float4 f = *reinterpret_cast<const float4*>(rowp + t * N4);
+            v[t][0] = make_float2(f.x, f.y); v[t][1] = make_float2(f.z, f.w);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < T3P + 6; ++t) v[t][0] = make_float2(rowp[t], 0.f);
         }
-        float u[T3P][N4];
+        // G_3 along the row, pairs over the fastest mode.
+        float2 u[T3P][NV];
 #pragma unroll
         for (int t = 0; t < T3P; ++t) {
-          float gc[7];
+          const float4 ga = *reinterpret_cast<const float4*>(g3s + (b0 + t) * 8);
+          const float4 gb = *reinterpret_cast<const float4*>(g3s + (b0 + t) * 8 + 4);
+          const float gc[7] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z};
 #pragma unroll
-          for (int e = 0; e < 7; ++e) gc[e] = g3s[(b0 + t) * 7 + e];
+          for (int m = 0; m < NV; ++m) {
+            float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int i4 = 0; i4 < N4; ++i4) {
-            float s = 0.f;
-#pragma unroll
-            for (int e = 0; e < 7; ++e) s = fmaf(gc[e], v[t + e][i4], s);
-            u[t][i4] = s;
+            for (int e = 0; e < 7; ++e) s2 = ffma2(bc2(gc[e]), v[t + e][m], s2);
+            u[t][m] = s2;
           }
         }
-#pragma unroll
-        for (int t = 0; t < T3P; ++t) {
-          float o[N4];
-          if constexpr (N4 > 1) {
-#pragma unroll
-            for (int i4 = 0; i4 < N4; ++i4) {
-              float s = 0.f;
-#pragma unroll
-              for (int e = 0; e < 7; ++e) {
-                const int c = i4 - 3 + e;
-                if (c >= 0 && c < N4) s = fmaf(g4s[i4 * 7 + e], u[t][c], s);
-              }
-              o[i4] = s;
-            }
-          } else {
-            o[0] = u[t][0];
-          }
-          float* dst = s_s1 + (ar * T3 + b0 + t) * N4;
-#pragma unroll
-          for (int i4 = 0; i4 < N4; ++i4) dst[i4] = o[i4];
-        }
-        if (ar >= 3 && ar < 3 + T2) {
+        // G_4 along the fastest mode: output pair (2m, 2m+1) at offset d reads
+        // (u[2m+d], u[2m+d+1]) - an aligned pair for even d, an odd pair otherwise.
+        float2 o[T3P][NV];
+        if constexpr (N4 > 1) {
+          float2 od[T3P][NV + 1];  // od[t][k] = (u[t][2k-1], u[t][2k]), zero outside
 #pragma unroll
           for (int t = 0; t < T3P; ++t) {
-            float lc[5];
+            od[t][0] = make_float2(0.f, u[t][0].x);
 #pragma unroll
-            for (int e = 0; e < 5; ++e) lc[e] = l3s[(b0 + t) * 5 + e];
-            float* dst = s_sl + ((ar - 3) * T3 + b0 + t) * N4;
+            for (int k = 1; k < NV; ++k) od[t][k] = make_float2(u[t][k - 1].y, u[t][k].x);
+            od[t][NV] = make_float2(u[t][NV - 1].y, 0.f);
 #pragma unroll
-            for (int i4 = 0; i4 < N4; ++i4) {
-              float s = 0.f;
+            for (int m = 0; m < NV; ++m) o[t][m] = make_float2(0.f, 0.f);
+          }
+          // One 128-bit coefficient load serves output pairs 2mm and 2mm+1 of every row t.
 #pragma unroll
-              for (int e = 0; e < 5; ++e) s = fmaf(lc[e], v[t + 1 + e][i4], s);
-              if constexpr (N4 > 1) {
+          for (int mm = 0; mm < NV / 2; ++mm) {
 #pragma unroll
-                for (int e = 0; e < 5; ++e) {
-                  const int c = i4 - 2 + e;
-                  if (c >= 0 && c < N4) s = fmaf(l4s[i4 * 5 + e], v[t + 3][c], s);
+            for (int e = 0; e < 7; ++e) {
+              const int d = e - 3;
+              const float4 c4 = *reinterpret_cast<const float4*>(g4s + e * N4 + 4 * mm);
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                const int m = 2 * mm + hh;
+                const float2 cf = hh ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+#pragma unroll
+                for (int t = 0; t < T3P; ++t) {
+                  if ((d & 1) == 0) {
+                    const int pi = m + d / 2;
+                    if (pi >= 0 && pi < NV) o[t][m] = ffma2(cf, u[t][pi], o[t][m]);
+                  } else {
+                    const int pi = m + (d + 1) / 2;
+                    if (pi >= 0 && pi <= NV) o[t][m] = ffma2(cf, od[t][pi], o[t][m]);
+                  }
                 }
               }
-              dst[i4] = s;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) o[t][0] = u[t][0];
+        }
+#pragma unroll
+        for (int t = 0; t < T3P; ++t) {
+          float* dst = s_s1 + ar * ROW1 + (b0 + t) * N4;
+          if constexpr (N4 == 8) {
+            reinterpret_cast<float4*>(dst)[0] = make_float4(o[t][0].x, o[t][0].y, o[t][1].x, o[t][1].y);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(o[t][2].x, o[t][2].y, o[t][3].x, o[t][3].y);
+          } else if constexpr (N4 == 4) {
+            *reinterpret_cast<float4*>(dst) = make_float4(o[t][0].x, o[t][0].y, o[t][1].x, o[t][1].y);
+          } else {
+            dst[0] = o[t][0].x;
+          }
+        }
+        if (ar >= 3 && ar < 3 + T2) {
+          float2 lin[T3P][NV];
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) {
+            const float4 la = *reinterpret_cast<const float4*>(l3s + (b0 + t) * 8);
+            const float lc[5] = {la.x, la.y, la.z, la.w, l3s[(b0 + t) * 8 + 4]};
+#pragma unroll
+            for (int m = 0; m < NV; ++m) {
+              float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int e = 0; e < 5; ++e) s2 = ffma2(bc2(lc[e]), v[t + 1 + e][m], s2);
+              lin[t][m] = s2;
+            }
+          }
+          if constexpr (N4 > 1) {
+            float2 od[T3P][NV + 1];  // odd pairs of the centre column v[t + 3]
+#pragma unroll
+            for (int t = 0; t < T3P; ++t) {
+              od[t][0] = make_float2(0.f, v[t + 3][0].x);
+#pragma unroll
+              for (int k = 1; k < NV; ++k) od[t][k] = make_float2(v[t + 3][k - 1].y, v[t + 3][k].x);
+              od[t][NV] = make_float2(v[t + 3][NV - 1].y, 0.f);
+            }
+#pragma unroll
+            for (int mm = 0; mm < NV / 2; ++mm) {
+#pragma unroll
+              for (int e = 0; e < 5; ++e) {
+                const int d = e - 2;
+                const float4 c4 = *reinterpret_cast<const float4*>(l4s + e * N4 + 4 * mm);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                  const int m = 2 * mm + hh;
+                  const float2 cf = hh ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+#pragma unroll
+                  for (int t = 0; t < T3P; ++t) {
+                    if ((d & 1) == 0) {
+                      const int pi = m + d / 2;
+                      if (pi >= 0 && pi < NV) lin[t][m] = ffma2(cf, v[t + 3][pi], lin[t][m]);
+                    } else {
+                      const int pi = m + (d + 1) / 2;
+                      if (pi >= 0 && pi <= NV) lin[t][m] = ffma2(cf, od[t][pi], lin[t][m]);
+                    }
+                  }
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) {
+            float* dst = s_sl + (ar - 3) * ROW1 + (b0 + t) * N4;
+            if constexpr (N4 == 8) {
+              reinterpret_cast<float4*>(dst)[0] = make_float4(lin[t][0].x, lin[t][0].y, lin[t][1].x, lin[t][1].y);
+              reinterpret_cast<float4*>(dst)[1] = make_float4(lin[t][2].x, lin[t][2].y, lin[t][3].x, lin[t][3].y);
+            } else if constexpr (N4 == 4) {
+              *reinterpret_cast<float4*>(dst) = make_float4(lin[t][0].x, lin[t][0].y, lin[t][1].x, lin[t][1].y);
+            } else {
+              dst[0] = lin[t][0].x;
             }
           }
         }
       }
       __syncthreads();
 
-      // ---- stage B: G_2 down columns, L_2, scatter along mode 1 ----
+      // ---- stage B: G_2 down columns and L_2; per-row results for the scatter ----
       {
         float s1c[P + 6];
 #pragma unroll
-        for (int k = 0; k < P + 6; ++k) s1c[k] = s_s1[((a0 + k) * T3 + bcol) * N4 + i4b];
+        for (int k = 0; k < P + 6; ++k) s1c[k] = s_s1[(a0 + k) * ROW1 + bcol * N4 + i4b];
         float s0c[P + 4];
 #pragma unroll
-        for (int k = 0; k < P + 4; ++k) s0c[k] = src[((a0 + 1 + k) * H3 + bcol + 3) * N4 + i4b];
-        float g1r[7], l1r[5];
+        for (int k = 0; k < P + 4; ++k) s0c[k] = src[(a0 + 1 + k) * ROW + (bcol + 3) * N4 + i4b];
 #pragma unroll
         for (int e = 0; e < 7; ++e) g1r[e] = __ldg(a.g[0] + (int64_t)j * 7 + e);
 #pragma unroll
         for (int e = 0; e < 5; ++e) l1r[e] = __ldg(a.l[0] + (int64_t)j * 5 + e);
         const bool own_plane = (j >= c0) && (j < c1);
+        float* pn = CG ? a.pnew + (int64_t)j * plane + out_base : nullptr;
 #pragma unroll
-        for (int k = 0; k < P; ++k) {
-          float w = 0.f;
+        for (int h = 0; h < P / 4; ++h) {
+          // Coefficients of rows a0+4h .. a0+4h+3, one 128-bit load per offset.
+          float4 g2f[7], l2f[5];
 #pragma unroll
-          for (int e = 0; e < 7; ++e) w = fmaf(g2s[(a0 + k) * 7 + e], s1c[k + e], w);
-          float lin = s_sl[((a0 + k) * T3 + bcol) * N4 + i4b];
+          for (int e = 0; e < 7; ++e) g2f[e] = *reinterpret_cast<const float4*>(g2s + e * T2 + a0 + 4 * h);
 #pragma unroll
-          for (int e = 0; e < 5; ++e) lin = fmaf(l2s[(a0 + k) * 5 + e], s0c[k + e], lin);
-          const float pcv = s0c[k + 2];
+          for (int e = 0; e < 5; ++e) l2f[e] = *reinterpret_cast<const float4*>(l2s + e * T2 + a0 + 4 * h);
 #pragma unroll
-          for (int e = 0; e < 7; ++e) acc[k][e] = fmaf(g1r[e], w, acc[k][e]);
+          for (int hh = 0; hh < 2; ++hh) {
+            const int k2 = 2 * h + hh;
+            const int k = 2 * k2;
+            float2 w = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int e = 0; e < 5; ++e) acc[k][e + 1] = fmaf(l1r[e], pcv, acc[k][e + 1]);
-          acc[k][3] += lin;
-          if constexpr (CG) {
-            s_ring[(j & 3) * C::CORE + ((a0 + k) * T3 + bcol) * N4 + i4b] = pcv;
-            const int i2 = i2_0 + a0 + k;
-            if (own_plane && col_ok && i2 < n2)
-              a.pnew[(int64_t)j * plane + ((int64_t)i2 * n3 + i3_0 + bcol) * N4 + i4b] = pcv;
+            for (int e = 0; e < 7; ++e) {
+              const float2 cf = hh ? make_float2(g2f[e].z, g2f[e].w) : make_float2(g2f[e].x, g2f[e].y);
+              w = ffma2(cf, make_float2(s1c[k + e], s1c[k + 1 + e]), w);
+            }
+            float2 lin = make_float2(s_sl[(a0 + k) * ROW1 + bcol * N4 + i4b],
+                                     s_sl[(a0 + k + 1) * ROW1 + bcol * N4 + i4b]);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+              const float2 cf = hh ? make_float2(l2f[e].z, l2f[e].w) : make_float2(l2f[e].x, l2f[e].y);
+              lin = ffma2(cf, make_float2(s0c[k + e], s0c[k + 1 + e]), lin);
+            }
+            const float2 pcv = make_float2(s0c[k + 2], s0c[k + 3]);
+            w2[k2] = w;
+            lin2[k2] = lin;
+            pc2[k2] = pcv;
+            if constexpr (CG) {
+              float* ring = s_ring + (j & 3) * C::CORE;
+              ring[(k) * NT + tid] = pcv.x;
+              ring[(k + 1) * NT + tid] = pcv.y;
+              if (own_plane && ((row_ok >> k) & 1u)) pn[k * row_step] = pcv.x;
+              if (own_plane && ((row_ok >> (k + 1)) & 1u)) pn[(k + 1) * row_step] = pcv.y;
+            }
           }
         }
       }
-      __syncthreads();
     }
-    // ---- emit plane j-3 and rotate the accumulator ring ----
+    // ---- scatter plane j into the ring along mode 1, emit plane j-3 ----
+    // acc[.][s] accumulates plane c with s = c mod 7; the switch makes every
+    // slot index a compile-time constant so the ring stays in registers.
     const int c = j - kGramHalf;
-    if (c >= c0) {
-      float part = 0.f;
+    auto step = [&](auto tag) {
+      constexpr int S = decltype(tag)::value;  // j mod 7
+      if (have) {
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int i2 = i2_0 + a0 + k;
-        if (col_ok && i2 < n2) {
-          const float qv = acc[k][0];
-          a.q[(int64_t)c * plane + ((int64_t)i2 * n3 + i3_0 + bcol) * N4 + i4b] = qv;
-          if constexpr (CG) part = fmaf(qv, s_ring[(c & 3) * C::CORE + ((a0 + k) * T3 + bcol) * N4 + i4b], part);
+        for (int k2 = 0; k2 < P / 2; ++k2) {
+#pragma unroll
+          for (int d = -3; d <= 3; ++d)
+            acc[k2][(S + d + 7) % 7] = ffma2(bc2(g1r[3 + d]), w2[k2], acc[k2][(S + d + 7) % 7]);
+#pragma unroll
+          for (int d = -2; d <= 2; ++d)
+            acc[k2][(S + d + 7) % 7] = ffma2(bc2(l1r[2 + d]), pc2[k2], acc[k2][(S + d + 7) % 7]);
+          acc[k2][S].x += lin2[k2].x;
+          acc[k2][S].y += lin2[k2].y;
         }
       }
-      dot += (double)part;
-    }
+      constexpr int E = (S + 4) % 7;  // slot of plane j-3
+      if (c >= c0) {
+        float part = 0.f;
+        float* qo = a.q + (int64_t)c * plane + out_base;
+        const float* ring = s_ring + (c & 3) * C::CORE + tid;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
+        for (int k2 = 0; k2 < P / 2; ++k2) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc[k][e] = acc[k][e + 1];
-      acc[k][6] = 0.f;
+          for (int h = 0; h < 2; ++h) {
+            const int k = 2 * k2 + h;
+            if ((row_ok >> k) & 1u) {
+              const float qv = h ? acc[k2][E].y : acc[k2][E].x;
+              qo[k * row_step] = qv;
+              if constexpr (CG) part = fmaf(qv, ring[k * NT], part);
+            }
+          }
+        }
+        dot += (double)part;
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < P / 2; ++k2) acc[k2][E] = make_float2(0.f, 0.f);
+    };
+    switch (j % 7) {
+      case 0: step(std::integral_constant<int, 0>{}); break;
+      case 1: step(std::integral_constant<int, 1>{}); break;
+      case 2: step(std::integral_constant<int, 2>{}); break;
+      case 3: step(std::integral_constant<int, 3>{}); break;
+      case 4: step(std::integral_constant<int, 4>{}); break;
+      case 5: step(std::integral_constant<int, 5>{}); break;
+      default: step(std::integral_constant<int, 6>{}); break;
     }
   }
   cp_async_wait<0>();
@@ -391,6 +562,7 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
 template <int N4, int T2, int T3, int T3P, int NT, int STAGES, bool CG>
 tca_status launch_fused(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   using C = Cfg<N4, T2, T3, T3P, NT, STAGES, CG>;
+  static_assert(C::BYTES <= 227 * 1024, "shared memory budget");
   auto kfn = fused_normal_kernel<N4, T2, T3, T3P, NT, STAGES, CG>;
   static bool attr_done = false;
   if (!attr_done) {
