@@ -295,9 +295,16 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
 }
 
 // FP64 true relative residual of x into p->scal->aux; optionally r = residual.
+// FP32 plans use double-float arithmetic on the FP32 pipes (residual_ff.cu);
+// FP64 plans use native FP64.
 template <typename T>
 static tca_status true_residual(tca_plan_s* p, const T* x, bool write_r, cudaStream_t s) {
-  const double* rhs64 = sizeof(T) == 8 ? (const double*)p->rhs : p->rhs64;
+  if constexpr (sizeof(T) == 4) {
+    return residual_ff(p, (const float*)x, reinterpret_cast<const float2*>(p->rhs64),
+                       reinterpret_cast<float2*>(p->res64), write_r ? (float*)p->r : nullptr, first_reduce(p),
+                       second_reduce(p), s);
+  }
+  const double* rhs64 = (const double*)p->rhs;
   TCA_TRY(normal_fp64<T>(p, x, p->res64, s));
   const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks - 1);
   true_residual_kernel<T><<<grid, kVecThreads, 0, s>>>(rhs64, p->res64, write_r ? (T*)p->r : nullptr, p->N, p->scal,
@@ -323,12 +330,15 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   double sweep_ms = 0.0;
   int sweep_n = 0;
 
-  // rhs = A^T b (FP32 for the iteration; FP64 for the true residual).
-  TCA_TRY((apply_chain<T, T, T>(p, true, (const T*)b_in, (T*)p->rhs, p->ws, p->ws_elems, s)));
+  // rhs = A^T b.  FP32 plans: one double-float chain gives the accurate rhs
+  // (kept as (hi, lo) pairs for the true residual) and its FP32 rounding for
+  // the iteration.  FP64 plans: native FP64.
   if constexpr (sizeof(T) == 4) {
     TCA_TRY(ensure_ws64_public(p));
-    TCA_TRY((apply_chain<float, double, double>(p, true, (const float*)b_in, p->rhs64, (void* const*)p->ws64,
-                                                 p->ws64_elems, s)));
+    TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
+                     reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
+  } else {
+    TCA_TRY((apply_chain<T, T, T>(p, true, (const T*)b_in, (T*)p->rhs, p->ws, p->ws_elems, s)));
   }
   cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, rtol, max_iter);
   TCA_LAUNCH_CHECK();

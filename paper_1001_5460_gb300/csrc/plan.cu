@@ -123,12 +123,30 @@ static void free_band(Band& b) {
   cudaFree(b.start);
   cudaFree(b.w32);
   cudaFree(b.w64);
+  cudaFree(b.wff);
   b = Band();
 }
 static void free_dense(Dense& d) {
   cudaFree(d.a32);
   cudaFree(d.a64);
+  cudaFree(d.aff);
+  cudaFree(d.zero_start);
   d = Dense();
+}
+
+// Double-float copies of the FP64 coefficients (used by the FP64-accurate residual).
+static tca_status add_ff_band(Band& b, cudaStream_t s) {
+  const int64_t n = b.n_out * b.W;
+  TCA_TRY(dmalloc(&b.wff, n));
+  return split_ff(b.w64, b.wff, n, s);
+}
+static tca_status add_ff_op(ModeOp& op, cudaStream_t s) {
+  if (op.kind == OP_BAND) return add_ff_band(op.band, s);
+  Dense& d = op.dense;
+  TCA_TRY(dmalloc(&d.aff, d.n_out * d.n_in));
+  TCA_TRY(dmalloc(&d.zero_start, d.n_out));
+  TCA_CUDA_TRY(cudaMemsetAsync(d.zero_start, 0, sizeof(int32_t) * d.n_out, s));
+  return split_ff(d.a64, d.aff, d.n_out * d.n_in, s);
 }
 static void free_op(ModeOp& o) {
   free_band(o.band);
@@ -259,6 +277,10 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
   TCA_TRY(dmalloc(&lb.w32, n * 5));
   lap_band_kernel<<<nblk(n * 5), 256, 0, s>>>(n, md.reg ? p->lambda : 0.0, lb.w64, lb.w32, lb.start);
   TCA_LAUNCH_CHECK();
+  TCA_TRY(add_ff_op(md.fwd, s));
+  TCA_TRY(add_ff_op(md.bwd, s));
+  TCA_TRY(add_ff_op(md.gram, s));
+  TCA_TRY(add_ff_band(lb, s));
   return TCA_OK;
 }
 

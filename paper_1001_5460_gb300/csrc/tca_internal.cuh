@@ -25,6 +25,7 @@ struct Band {
   int32_t* start = nullptr;  // device, n_out
   float* w32 = nullptr;      // device, n_out * W
   double* w64 = nullptr;     // device, n_out * W
+  float2* wff = nullptr;     // device, n_out * W: w64 split into (hi, lo) floats
 };
 
 // Row-major n_out x n_in matrix.
@@ -32,6 +33,8 @@ struct Dense {
   int64_t n_out = 0, n_in = 0;
   float* a32 = nullptr;
   double* a64 = nullptr;
+  float2* aff = nullptr;          // a64 split into (hi, lo) floats
+  int32_t* zero_start = nullptr;  // n_out zeros: the matrix viewed as a full-width band
 };
 
 enum OpKind { OP_BAND = 0, OP_DENSE = 1 };
@@ -193,6 +196,13 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
 
 // Blocks used by grid-stride vector kernels.
 int vector_grid(const tca_plan_s* p, int64_t n);
+
+// Double-float (FP32 pair) arithmetic for FP64-accurate products (residual_ff.cu).
+tca_status split_ff(const double* a, float2* b, int64_t n, cudaStream_t s);
+tca_status chain_ff(tca_plan_s* p, bool transpose, bool gram, const float* x, float2* y, float* y32,
+                    float2* const* ws, int64_t ws_elems, cudaStream_t s);
+tca_status residual_ff(tca_plan_s* p, const float* x, const float2* rhs_ff, float2* kx_ff, float* r_out,
+                       Reduce red, Reduce red2, cudaStream_t s);
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);
