@@ -210,6 +210,13 @@ tca_status launch_mode_op(const ModeOp& op, const Tin* x, Tout* y, int64_t O, in
   const int n_in = (int)op.n_in(), n_out = (int)op.n_out();
   if (O <= 0 || I <= 0) return TCA_OK;
   const bool dense = op.kind == OP_DENSE;
+  if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4 && sizeof(Tc) == 4) {
+    // FP32 bands: TMA-staged row tiles or register fibres when the shape allows.
+    if (!dense) {
+      const tca_status st = launch_band_fast(op.band, (const float*)x, (float*)y, O, I, s);
+      if (st != TCA_ERR_UNSUPPORTED) return st;
+    }
+  }
   const Tc* w = dense ? asel<Tc>(op.dense) : wsel<Tc>(op.band);
   if (I >= 32) {
     const int64_t i_chunks_v = (I + 255) / 256;

@@ -175,6 +175,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     fb.n_out = m;
     fb.n_in = n;
     fb.W = 4;
+    fb.rows32 = rows_per_chunk(c0.data(), m, 4);
     TCA_TRY(dmalloc(&fb.start, m));
     TCA_TRY(dmalloc(&fb.w64, m * 4));
     TCA_TRY(dmalloc(&fb.w32, m * 4));
@@ -211,6 +212,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     bb.n_out = n;
     bb.n_in = m;
     bb.W = W;
+    bb.rows32 = rows_per_chunk(ts.data(), n, W);
     TCA_TRY(dmalloc(&bb.start, n));
     TCA_TRY(dmalloc(&bb.w64, n * W));
     TCA_TRY(dmalloc(&bb.w32, n * W));
@@ -228,6 +230,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     gb.n_out = n;
     gb.n_in = n;
     gb.W = 2 * kGramHalf + 1;
+    gb.rows32 = (int)std::min<int64_t>(n, 32) - 1 + gb.W;
     TCA_TRY(dmalloc(&gb.start, n));
     TCA_TRY(dmalloc(&gb.w64, n * 7));
     TCA_TRY(dmalloc(&gb.w32, n * 7));
@@ -272,6 +275,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
   lb.n_out = n;
   lb.n_in = n;
   lb.W = 2 * kLapHalf + 1;
+  lb.rows32 = (int)std::min<int64_t>(n, 32) - 1 + lb.W;
   TCA_TRY(dmalloc(&lb.start, n));
   TCA_TRY(dmalloc(&lb.w64, n * 5));
   TCA_TRY(dmalloc(&lb.w32, n * 5));

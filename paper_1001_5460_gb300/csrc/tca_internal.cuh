@@ -26,6 +26,7 @@ struct Band {
   float* w32 = nullptr;      // device, n_out * W
   double* w64 = nullptr;     // device, n_out * W
   float2* wff = nullptr;     // device, n_out * W: w64 split into (hi, lo) floats
+  int rows32 = 0;            // input rows spanned by any 32 consecutive outputs (TMA tile height)
 };
 
 // Row-major n_out x n_in matrix.
@@ -203,6 +204,12 @@ tca_status chain_ff(tca_plan_s* p, bool transpose, bool gram, const float* x, fl
                     float2* const* ws, int64_t ws_elems, cudaStream_t s);
 tca_status residual_ff(tca_plan_s* p, const float* x, const float2* rhs_ff, float2* kx_ff, float* r_out,
                        Reduce red, Reduce red2, cudaStream_t s);
+
+// TMA-staged / register-fibre banded mode products (mode_tma.cu); UNSUPPORTED
+// when the shape or alignment does not fit, so callers fall back.
+tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t O, int64_t I, cudaStream_t s);
+int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W);
+tca_status read_wait_timeout(int* flag, bool reset);
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);
