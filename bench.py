@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
-    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep"],
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -57,6 +57,31 @@ def run_case(args, local):
 
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
+    if args.case == "dense":
+        # Dense 96x96 Gram factor on mode 1 of a 96x96x96x24 tensor: tensor-core mode product.
+        shape = (96, 96, 96, 24)
+        rng = np.random.default_rng(SEED)
+        facs = [synth.Factor("dense", int(1.5 * n), n, a=synth.dense_gaussian_factor(int(1.5 * n), n, rng))
+                for n in shape]
+        dplan = tca.Plan(shape, facs, lam=LAM, precision="f32")
+        x = torch.randn(shape, dtype=torch.float32, device=device)
+        y = torch.empty_like(x)
+        fn = lambda: dplan.apply_mode(0, tca.OP_GRAM, shape, x, y)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        n = x.numel()
+        print(json.dumps({"case": "dense", "ms": round(ms, 5), "gbs": round(2 * n * 4 / ms / 1e6, 1),
+                          "useful_tflops": round(2 * n * 96 / ms / 1e9, 2),
+                          "issued_tflops_3xtf32": round(3 * 2 * n * 96 / ms / 1e9, 2)}), flush=True)
+        return
     inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, with_truth=False)
     plan = tca.plan_from_instance(inst, precision="f32")
     x = torch.randn(SHAPE, dtype=torch.float32, device=device)

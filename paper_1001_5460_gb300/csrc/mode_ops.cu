@@ -215,6 +215,9 @@ tca_status launch_mode_op(const ModeOp& op, const Tin* x, Tout* y, int64_t O, in
     if (!dense) {
       const tca_status st = launch_band_fast(op.band, (const float*)x, (float*)y, O, I, s);
       if (st != TCA_ERR_UNSUPPORTED) return st;
+    } else if (op.tc_split > 0) {
+      const tca_status st = launch_dense_tc(op.dense, (const float*)x, (float*)y, O, I, op.tc_split, s);
+      if (st != TCA_ERR_UNSUPPORTED) return st;
     }
   }
   const Tc* w = dense ? asel<Tc>(op.dense) : wsel<Tc>(op.band);

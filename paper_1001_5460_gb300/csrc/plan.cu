@@ -266,6 +266,10 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     TCA_TRY(dmalloc(&gd.a32, n * n));
     gram_dense_kernel<<<nblk(n * n), 256, 0, s>>>(fd.a64, m, n, gd.a64, gd.a32);
     TCA_LAUNCH_CHECK();
+    // FP32 plans run dense products on the tensor cores with the 3xTF32 split
+    // (about FP32 accuracy); reduced-precision plans use plain TF32.
+    const int split = p->prec == TCA_F32 ? 2 : (p->prec == TCA_F64 ? 0 : 1);
+    md.fwd.tc_split = md.bwd.tc_split = md.gram.tc_split = split;
   } else {
     return TCA_ERR_INVALID_ARG;
   }

@@ -229,3 +229,23 @@ def test_full_size_normal_operator_sampled():
     for pt in pts:
         ref = O.normal_apply_at(x, mats, inst.lam, pt)
         assert abs(got[pt] - ref) <= 1e-5 * (abs(ref) + 1.0), (pt, got[pt], ref)
+
+
+@pytest.mark.parametrize("shape", [(40, 30, 50, 8), (17, 96, 33), (64, 5, 9, 4)])
+def test_dense_products_on_tensor_cores(shape):
+    """Dense mode products run on tcgen05: a TF32 plan shows TF32 rounding (1e-5 .. 5e-3 relative),
+    the FP32 plan's 3xTF32 split stays at FP32 level; several 128-row tiles, padded K and N."""
+    tca = lib()
+    inst = _dense(shape, 800 + len(shape))
+    mats = [f.dense() for f in inst.factors]
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(inst.shape).astype(np.float32)
+    ref = O.apply(x, mats)
+    errs = {}
+    for prec in ("f32", "tf32_ir"):
+        plan = tca.plan_from_instance(inst, precision=prec)
+        ax = empty_dev(inst.sample_shape, np.float32)
+        plan.apply(to_dev(x, np.float32), ax)
+        errs[prec] = rel_l2(ax.cpu().numpy(), ref)
+    assert errs["f32"] < TOL_F32, errs
+    assert 1e-5 < errs["tf32_ir"] < 5e-3, errs
