@@ -313,6 +313,126 @@ static tca_status true_residual(tca_plan_s* p, const T* x, bool write_r, cudaStr
   return TCA_OK;
 }
 
+// Replay the cached CG graph until the recursive residual meets rtol, CG
+// breaks down or the device iteration count reaches max_iter.  The scalar
+// record is left in p->scal_host.
+static tca_status cg_iterate(tca_plan_s* p, double rtol, int max_iter, int every, bool profile, double* sweep_ms,
+                             int* sweep_n, cudaStream_t s) {
+  Scalars* hs = p->scal_host;
+  // Start-of-iteration stop test (a zero right-hand side or an exact x0).
+  TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  bool conv = hs->bnorm == 0.0 || std::sqrt(hs->rho) <= rtol * hs->bnorm;
+  while (!conv && !hs->breakdown && hs->iters < max_iter) {
+    const int it_before = hs->iters;
+    TCA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, s));
+    note_launches(p->graph_launches);
+    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    conv = hs->converged != 0;
+    if (profile) {
+      // Iterations of this replay that did work; the rest returned at entry.
+      const int ran = std::min(every, hs->iters - it_before + (hs->breakdown ? 1 : 0));
+      for (int i = 0; i < ran; ++i) {
+        float ms = 0.f;
+        TCA_CUDA_TRY(cudaEventElapsedTime(&ms, p->sweep_ev[2 * i], p->sweep_ev[2 * i + 1]));
+        *sweep_ms += ms;
+        ++*sweep_n;
+      }
+    }
+  }
+  return TCA_OK;
+}
+
+__global__ void axpy_f32_kernel(float* __restrict__ x, const float* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
+// Mixed precision with iterative refinement (the _IR plans): an outer loop in
+// FP64-accurate arithmetic (double-float residual r = A^T b - K x), an inner
+// CG on K d = r run to inner_rtol with the plan's reduced-precision operator
+// (plain TF32 tensor-core products for dense factors), and x += d, until the
+// true relative residual meets rtol.
+static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_solve_opts* o, tca_solve_info* info,
+                           cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  TCA_TRY(ensure_solver_buffers<float>(p));
+  TCA_TRY(ensure_ws64_public(p));
+  if (!p->dbuf) {
+    cudaError_t e = cudaMalloc((void**)&p->dbuf, sizeof(float) * (size_t)p->N);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return TCA_ERR_ALLOC;
+    }
+  }
+  const int64_t N = p->N;
+  const double rtol = o ? o->rtol : 1e-6;
+  const double inner = (o && o->inner_rtol > 0.0) ? o->inner_rtol : 1e-3;
+  const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
+  const int max_refine = (o && o->max_refine > 0) ? o->max_refine : 30;
+  int every = (o && o->check_every > 0) ? o->check_every : 16;
+  every = std::max(2, (every + 1) / 2 * 2);
+  const bool profile = o && o->profile;
+  if (profile) every = std::min(every, kMaxProfiledIters);
+  if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
+  double sweep_ms = 0.0;
+  int sweep_n = 0;
+  float* d = p->dbuf;
+  TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
+                   reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
+  if (!(o && o->x0_given)) TCA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * N, s));
+  TCA_TRY(get_graph<float>(p, d, every, profile, s));
+  const int vgrid = std::min(vector_grid(p, N), second_reduce(p).max_blocks - 1);
+  Scalars* hs = p->scal_host;
+  tca_status status = TCA_OK;
+  int total = 0, outer = 0;
+  double rec = 0.0;
+  for (;;) {
+    // Outer residual in double-float: p->rhs <- r (FP32), scal->aux <- ||r|| / ||A^T b||.
+    TCA_TRY(residual_ff(p, x, reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
+                        (float*)p->rhs, first_reduce(p), second_reduce(p), s));
+    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    const double rel = hs->aux;
+    if (!(rel > rtol)) break;  // converged (or a zero right-hand side)
+    if (total >= max_iter || outer >= max_refine) {
+      status = TCA_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++outer;
+    // Inner CG from d = 0 on K d = r, to inner_rtol relative to ||r||.
+    cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, inner, max_iter - total);
+    TCA_LAUNCH_CHECK();
+    TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(float) * N, s));
+    TCA_CUDA_TRY(cudaMemsetAsync(p->p[1], 0, sizeof(float) * N, s));
+    TCA_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(float) * N, s));
+    cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, nullptr, (float*)p->r, N, p->scal,
+                                                          first_reduce(p), 1, second_reduce(p));
+    TCA_LAUNCH_CHECK();
+    TCA_TRY(cg_iterate(p, inner, max_iter - total, every, profile, &sweep_ms, &sweep_n, s));
+    total += hs->iters;
+    rec = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho, 0.0)) / hs->bnorm : 0.0;
+    if (hs->breakdown) {
+      status = TCA_ERR_BREAKDOWN;
+      break;
+    }
+    axpy_f32_kernel<<<vgrid, kVecThreads, 0, s>>>(x, d, N);
+    TCA_LAUNCH_CHECK();
+  }
+  if (info) {
+    info->iters = total;
+    info->refinements = outer;
+    info->rel_res_true = hs->aux;
+    info->rel_res_recursive = rec;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->sweep_ms = sweep_ms;
+    info->sweep_launches = sweep_n;
+    info->reserved = 0;
+  }
+  return status;
+}
+
 template <typename T>
 static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_solve_opts* o, tca_solve_info* info,
                              cudaStream_t s) {
@@ -366,28 +486,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   int restarts = 0;
   Scalars* hs = p->scal_host;
   for (;;) {
-    // Start-of-iteration stop test (a zero right-hand side or an exact x0).
-    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-    TCA_CUDA_TRY(cudaStreamSynchronize(s));
-    bool conv = hs->bnorm == 0.0 || std::sqrt(hs->rho) <= rtol * hs->bnorm;
-    while (!conv && !hs->breakdown && hs->iters < max_iter) {
-      const int it_before = hs->iters;
-      TCA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, s));
-      note_launches(p->graph_launches);
-      TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-      TCA_CUDA_TRY(cudaStreamSynchronize(s));
-      conv = hs->converged != 0;
-      if (profile) {
-        // Iterations of this replay that did work; the rest returned at entry.
-        const int ran = std::min(every, hs->iters - it_before + (hs->breakdown ? 1 : 0));
-        for (int i = 0; i < ran; ++i) {
-          float ms = 0.f;
-          TCA_CUDA_TRY(cudaEventElapsedTime(&ms, p->sweep_ev[2 * i], p->sweep_ev[2 * i + 1]));
-          sweep_ms += ms;
-          ++sweep_n;
-        }
-      }
-    }
+    TCA_TRY(cg_iterate(p, rtol, max_iter, every, profile, &sweep_ms, &sweep_n, s));
     if (hs->breakdown) {
       status = TCA_ERR_BREAKDOWN;
       break;
@@ -432,7 +531,6 @@ extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const t
                                 tca_solve_info* info, cudaStream_t stream) {
   if (!plan || !b || !x) return TCA_ERR_INVALID_ARG;
   tca_plan_s* p = plan;
-  if (p->prec == TCA_BF16_IR || p->prec == TCA_TF32_IR) return TCA_ERR_UNSUPPORTED;
   const size_t es = elem_size(p);
   // Host buffers, and device buffers the vector kernels cannot address with
   // 16-byte accesses, go through the plan's staging buffers.
@@ -450,8 +548,10 @@ extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const t
       TCA_CUDA_TRY(cudaMemcpyAsync(p->stage_x, x, es * (size_t)p->N, cudaMemcpyDefault, stream));
     dx = p->stage_x;
   }
-  tca_status st = p->prec == TCA_F64 ? solve_impl<double>(p, db, (double*)dx, opts, info, stream)
-                                     : solve_impl<float>(p, db, (float*)dx, opts, info, stream);
+  tca_status st;
+  if (p->prec == TCA_F64) st = solve_impl<double>(p, db, (double*)dx, opts, info, stream);
+  else if (p->prec == TCA_F32) st = solve_impl<float>(p, db, (float*)dx, opts, info, stream);
+  else st = solve_ir(p, db, (float*)dx, opts, info, stream);
   if (!x_dev && (st == TCA_OK || st == TCA_ERR_NOT_CONVERGED || st == TCA_ERR_BREAKDOWN)) {
     TCA_CUDA_TRY(cudaMemcpyAsync(x, p->stage_x, es * (size_t)p->N, cudaMemcpyDefault, stream));
     TCA_CUDA_TRY(cudaStreamSynchronize(stream));

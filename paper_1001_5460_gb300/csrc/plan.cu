@@ -325,6 +325,7 @@ static void destroy_plan(tca_plan_s* p) {
   cudaFree(p->q);
   cudaFree(p->rhs64);
   cudaFree(p->res64);
+  cudaFree(p->dbuf);
   cudaFree(p->stage_x);
   cudaFree(p->stage_b);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);

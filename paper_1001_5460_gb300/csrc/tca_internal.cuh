@@ -115,6 +115,7 @@ struct tca_plan_s {
   void* q = nullptr;
   double* rhs64 = nullptr;
   double* res64 = nullptr;
+  float* dbuf = nullptr;    // refinement correction d (mixed-precision plans)
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
 

@@ -249,3 +249,32 @@ def test_dense_products_on_tensor_cores(shape):
         errs[prec] = rel_l2(ax.cpu().numpy(), ref)
     assert errs["f32"] < TOL_F32, errs
     assert 1e-5 < errs["tf32_ir"] < 5e-3, errs
+
+
+@pytest.mark.parametrize("kind,shape,prec", [("dense", (20, 18, 16, 4), "tf32_ir"),
+                                             ("dense", (24, 30, 20), "bf16_ir"),
+                                             ("bspline", (24, 20, 22, 8), "bf16_ir"),
+                                             ("bspline", (20, 22, 18, 4), "tf32_ir")])
+def test_solve_mixed_precision_refinement(kind, shape, prec):
+    """Reduced-precision inner CG + FP64-accurate refinement reaches the FP64 oracle's solution."""
+    tca = lib()
+    if kind == "dense":
+        inst = _dense(shape, 900 + len(shape), lam=1e-2)
+        rng = np.random.default_rng(5)
+        inst.x_true = synth.smooth_random_field(shape, 3.0, rng, dtype=np.float64)
+        inst.noise = 0.01 * rng.standard_normal(inst.sample_shape)
+    else:
+        inst = synth.instance_bspline(shape, seed=910 + len(shape), dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision=prec)
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-6, inner_rtol=1e-2)
+    assert st == tca.OK, info
+    assert info["refinements"] >= 1
+    got = x.cpu().numpy()
+    rel = O.rel_residual(got, b.astype(np.float64), mats, inst.lam)
+    assert rel <= 1.5e-6, (rel, info)
+    assert abs(info["rel_res_true"] - rel) < 1e-7
+    ref = O.solve(b.astype(np.float64), mats, inst.lam, rtol=1e-12).x
+    assert rel_l2(got, ref) < 1e-4
