@@ -181,6 +181,45 @@ typedef struct {
 TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
                      tca_solve_info* info, cudaStream_t stream);
 
+/* Solve `count` independent systems (A_i^T A_i + lambda_i R_i) x_i = A_i^T b_i,
+ * each by the CG of Sec. 4.1, Fig. 2, in one CUDA graph launch.  Many small
+ * problems of uneven shapes are the workload; the paper's method is applied
+ * unchanged to each of them.  plans[i]: a distinct TCA_F32 plan per instance
+ * (any order, shape and factor kinds; a plan may not appear twice).  b[i]:
+ * m_i-shaped, x[i]: n_i-shaped, both device memory, x[i] 16-byte aligned;
+ * host or unaligned buffers give TCA_ERR_UNSUPPORTED.  opts applies to every
+ * instance (rtol, max_iter, x0_given, check_every = iterations of every
+ * instance per body pass of the loop graph; profile is ignored).
+ * The first call for a given set of plans and buffers captures two graphs:
+ * a set-up graph (A^T b in double-float, scalars, first residual, instances
+ * as parallel branches) and a loop graph whose single while-conditional node
+ * repeats check_every iterations of every still-running instance until all
+ * have met rtol, broken down or used max_iter.  Later calls with the same
+ * plans, buffers and options replay them.  After the loop the true residual
+ * of each instance is recomputed in double-float and instances above rtol
+ * restart from their x (info[i].refinements counts restarts).  info: `count`
+ * entries or NULL; seconds is the wall time of the whole batch.  Returns the
+ * first non-OK instance status (TCA_ERR_NOT_CONVERGED / TCA_ERR_BREAKDOWN);
+ * every x[i] and info[i] is still written.  The graphs are cached per
+ * process for one batch at a time.  Synchronises the stream. */
+TCA_API tca_status tca_solve_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
+                                     const tca_solve_opts* opts, tca_solve_info* info, cudaStream_t stream);
+
+/* Autotune the plan's fused normal-operator sweep: time the sweep for a few
+ * tile extents along mode 1 around the cost model's choice (the plan-time
+ * expression analysis of Sec. 2.1 and Sec. 4, which picks evaluation orders
+ * and kernels by cost, extended with a measurement on this GPU) and keep the
+ * fastest in the plan.  Results are cached per shape (n_1..n_4) for the life
+ * of the process, so a second plan of the same shape tunes in no time.  Plans
+ * without the fused sweep (TCA_F64, dense factors, order 4 with n_4 other
+ * than 4 or 8) return TCA_OK unchanged.  Uses the plan's workspace; call it before a solve
+ * (not concurrently with one on this plan).  Synchronises the stream. */
+TCA_API tca_status tca_autotune(tca_plan_t plan, cudaStream_t stream);
+
+/* Tile extent the autotuner chose for the plan (chunks of mode 1), or 0 when
+ * the plan uses the cost model. */
+TCA_API int tca_autotuned_chunks(tca_plan_t plan);
+
 /* Relative residual ||rhs - kx||_2 / ||rhs||_2 of two FP64 device vectors of
  * length n, written to *out (device memory, one double).  If ||rhs|| is zero
  * the absolute norm ||rhs - kx|| is written instead (0 for n = 0).

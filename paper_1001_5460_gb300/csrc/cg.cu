@@ -14,6 +14,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <vector>
 
 #include "tca_internal.cuh"
 
@@ -523,9 +525,285 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Batched solve: many independent plans in one CUDA graph launch.
+//
+// The setup graph (A^T b, scalars, r = A^T b for every instance) and the loop
+// graph are built once per batch signature.  The loop graph is a single
+// while-conditional node; its body runs `every` CG iterations of every
+// instance as parallel branches (instances spread over a pool of capture
+// streams) and ends with a one-thread kernel that keeps the loop going while
+// any instance is still iterating.  One cudaGraphLaunch therefore iterates
+// the whole batch to recursive convergence; the host then checks each true
+// residual and relaunches for the (rare) instances that need a restart.
+
+namespace {
+
+__global__ void batch_cond_kernel(Scalars* const* __restrict__ scal, int count, cudaGraphConditionalHandle h) {
+  int running = 0;
+  for (int i = 0; i < count; ++i) running |= cg_done(scal[i]) ? 0 : 1;
+  cudaGraphSetConditional(h, running ? 1u : 0u);
+}
+
+// Start-of-iteration stop test on the device (a zero right-hand side or an
+// exact initial guess), so that such an instance does no iteration at all.
+__global__ void batch_start_test_kernel(Scalars* sc) {
+  if (sc->bnorm == 0.0 || sqrt(sc->rho) <= sc->rtol * sc->bnorm) sc->converged = 1;
+}
+
+constexpr int kBatchStreams = 64;
+
+struct BatchGraphs {
+  std::vector<const void*> key;
+  cudaGraphExec_t setup = nullptr, loop = nullptr;
+  Scalars** scal_dev = nullptr;
+  uint64_t launches_setup = 0, launches_loop = 0;
+};
+
+std::mutex g_batch_mutex;
+BatchGraphs g_batch;  // last batch signature (one cached batch per process)
+cudaStream_t g_pool[kBatchStreams] = {};
+cudaEvent_t g_fork = nullptr, g_join[kBatchStreams] = {};
+
+tca_status ensure_pool() {
+  if (g_fork) return TCA_OK;
+  for (int i = 0; i < kBatchStreams; ++i) {
+    TCA_CUDA_TRY(cudaStreamCreateWithFlags(&g_pool[i], cudaStreamNonBlocking));
+    TCA_CUDA_TRY(cudaEventCreateWithFlags(&g_join[i], cudaEventDisableTiming));
+  }
+  TCA_CUDA_TRY(cudaEventCreateWithFlags(&g_fork, cudaEventDisableTiming));
+  return TCA_OK;
+}
+
+// Per-instance set-up: rhs (double-float), scalars, zero directions, x, r.
+tca_status enqueue_setup(tca_plan_s* p, const float* b, float* x, double rtol, int max_iter, bool x0,
+                         cudaStream_t s) {
+  TCA_TRY(chain_ff(p, true, false, b, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
+                   reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
+  cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, rtol, max_iter);
+  TCA_LAUNCH_CHECK();
+  const int64_t N = p->N;
+  TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(float) * N, s));
+  TCA_CUDA_TRY(cudaMemsetAsync(p->p[1], 0, sizeof(float) * N, s));
+  const int vgrid = std::min(vector_grid(p, N), second_reduce(p).max_blocks - 1);
+  const float* kx = nullptr;
+  if (x0) {
+    if (p->fused_ok) TCA_TRY(normal_fused_f32(p, nullptr, x, nullptr, (float*)p->q, false, s));
+    else TCA_TRY(normal_generic<float>(p, x, (float*)p->q, s));
+    kx = (const float*)p->q;
+  } else {
+    TCA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * N, s));
+  }
+  cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, kx, (float*)p->r, N, p->scal,
+                                                        first_reduce(p), 1, second_reduce(p));
+  TCA_LAUNCH_CHECK();
+  batch_start_test_kernel<<<1, 1, 0, s>>>(p->scal);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+// Capture `body(i, stream)` for every instance on the stream pool, forked from
+// and joined back into the capturing stream cs.
+template <typename F>
+tca_status capture_branches(int count, cudaStream_t cs, F body) {
+  TCA_CUDA_TRY(cudaEventRecord(g_fork, cs));
+  const int ns = std::min(count, kBatchStreams);
+  for (int k = 0; k < ns; ++k) TCA_CUDA_TRY(cudaStreamWaitEvent(g_pool[k], g_fork, 0));
+  for (int i = 0; i < count; ++i) TCA_TRY(body(i, g_pool[i % ns]));
+  for (int k = 0; k < ns; ++k) {
+    TCA_CUDA_TRY(cudaEventRecord(g_join[k], g_pool[k]));
+    TCA_CUDA_TRY(cudaStreamWaitEvent(cs, g_join[k], 0));
+  }
+  return TCA_OK;
+}
+
+tca_status build_batch(int count, tca_plan_s** plans, const float* const* b, float* const* x, double rtol,
+                       int max_iter, bool x0, int every, BatchGraphs* bg) {
+  cudaStream_t cs;
+  TCA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const uint64_t before = tca_kernel_launches(0);
+  tca_status st = TCA_OK;
+  // Setup graph.
+  cudaGraph_t g = nullptr;
+  TCA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  st = capture_branches(count, cs, [&](int i, cudaStream_t s) {
+    return enqueue_setup(plans[i], b[i], x[i], rtol, max_iter, x0, s);
+  });
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  const uint64_t mid = tca_kernel_launches(0);
+  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bg->setup, g, 0);
+  if (g) cudaGraphDestroy(g);
+  // Loop graph: while (any instance iterating) { every iterations of every instance }.
+  cudaGraph_t lg = nullptr;
+  cudaGraphConditionalHandle h;
+  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphCreate(&lg, 0);
+  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, lg, 1, cudaGraphCondAssignDefault);
+  cudaGraph_t body = nullptr;
+  if (st == TCA_OK && e == cudaSuccess) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, lg, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+  }
+  if (st == TCA_OK && e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (st == TCA_OK && e == cudaSuccess) {
+    st = capture_branches(count, cs, [&](int i, cudaStream_t s) -> tca_status {
+      tca_plan_s* p = plans[i];
+      for (int it = 0; it < every; ++it)
+        TCA_TRY(enqueue_iteration<float>(p, x[i], (const float*)p->p[it & 1], (float*)p->p[(it + 1) & 1], s,
+                                         nullptr, nullptr));
+      return TCA_OK;
+    });
+    batch_cond_kernel<<<1, 1, 0, cs>>>(bg->scal_dev, count, h);
+    note_launches(1);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bg->loop, lg, 0);
+  if (lg) cudaGraphDestroy(lg);
+  const uint64_t after = tca_kernel_launches(0);
+  tca_kernel_launches(1);
+  note_launches(before);  // captured launches are counted when the graphs run
+  bg->launches_setup = mid - before;
+  bg->launches_loop = after - mid;
+  cudaStreamDestroy(cs);
+  if (st != TCA_OK) return st;
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return TCA_ERR_CUDA;
+  }
+  return TCA_OK;
+}
+
+}  // namespace
+
+static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float* const* b, float* const* x,
+                                     const tca_solve_opts* o, tca_solve_info* info, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const double rtol = o ? o->rtol : 1e-6;
+  const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
+  const bool x0 = o && o->x0_given;
+  int every = (o && o->check_every > 0) ? o->check_every : 16;
+  every = std::max(2, (every + 1) / 2 * 2);
+  if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    TCA_TRY(ensure_solver_buffers<float>(plans[i]));
+    TCA_TRY(ensure_ws64_public(plans[i]));
+  }
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  TCA_TRY(ensure_pool());
+  std::vector<const void*> key;
+  key.push_back((const void*)(intptr_t)every);
+  key.push_back((const void*)(intptr_t)max_iter);
+  key.push_back((const void*)(intptr_t)(x0 ? 1 : 0));
+  key.push_back(reinterpret_cast<const void*>((uintptr_t)(rtol * 1e15)));
+  for (int i = 0; i < count; ++i) {
+    key.push_back(plans[i]);
+    key.push_back((const void*)(uintptr_t)plans[i]->generation);
+    key.push_back(b[i]);
+    key.push_back(x[i]);
+  }
+  if (key != g_batch.key || !g_batch.loop) {
+    if (g_batch.setup) cudaGraphExecDestroy(g_batch.setup);
+    if (g_batch.loop) cudaGraphExecDestroy(g_batch.loop);
+    g_batch.setup = g_batch.loop = nullptr;
+    g_batch.key.clear();
+    cudaFree(g_batch.scal_dev);
+    g_batch.scal_dev = nullptr;
+    // Tile extents of the banded instances' fused sweeps come from the
+    // autotuner (cached per shape).
+    for (int i = 0; i < count; ++i) TCA_TRY(tca_autotune(plans[i], s));
+    std::vector<Scalars*> sp(count);
+    for (int i = 0; i < count; ++i) sp[i] = plans[i]->scal;
+    TCA_CUDA_TRY(cudaMalloc((void**)&g_batch.scal_dev, sizeof(Scalars*) * count));
+    TCA_CUDA_TRY(cudaMemcpy(g_batch.scal_dev, sp.data(), sizeof(Scalars*) * count, cudaMemcpyHostToDevice));
+    TCA_TRY(build_batch(count, plans, b, x, rtol, max_iter, x0, every, &g_batch));
+    g_batch.key = key;
+  }
+  TCA_CUDA_TRY(cudaGraphLaunch(g_batch.setup, s));
+  note_launches(g_batch.launches_setup);
+  std::vector<int> restarts(count, 0);
+  std::vector<char> active(count, 1);
+  tca_status status = TCA_OK;
+  for (int round = 0;; ++round) {
+    TCA_CUDA_TRY(cudaGraphLaunch(g_batch.loop, s));
+    note_launches(g_batch.launches_loop);  // one body replay's worth; a lower bound
+    // True residual (double-float) of every instance that iterated in this
+    // launch; restart those above rtol.
+    bool again = false;
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      tca_plan_s* p = plans[i];
+      TCA_TRY(residual_ff(p, x[i], reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
+                          (float*)p->r, first_reduce(p), second_reduce(p), s));
+    }
+    for (int i = 0; i < count; ++i)
+      if (active[i])
+        TCA_CUDA_TRY(cudaMemcpyAsync(plans[i]->scal_host, plans[i]->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      active[i] = 0;
+      tca_plan_s* p = plans[i];
+      const Scalars& hs = *p->scal_host;
+      if (hs.breakdown || hs.bnorm == 0.0 || hs.aux <= rtol || hs.iters >= max_iter) continue;
+      active[i] = 1;
+      // Restart from x: r holds the double-float residual rounded to FP32.
+      const int vgrid = std::min(vector_grid(p, p->N), second_reduce(p).max_blocks - 1);
+      cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->r, nullptr, (float*)p->r, p->N, p->scal,
+                                                            first_reduce(p), 0, second_reduce(p));
+      TCA_LAUNCH_CHECK();
+      batch_start_test_kernel<<<1, 1, 0, s>>>(p->scal);
+      TCA_LAUNCH_CHECK();
+      ++restarts[i];
+      again = true;
+    }
+    if (!again || round > 8) break;
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < count; ++i) {
+    const Scalars& hs = *plans[i]->scal_host;
+    tca_status si = TCA_OK;
+    if (hs.breakdown) si = TCA_ERR_BREAKDOWN;
+    else if (hs.bnorm != 0.0 && hs.aux > rtol) si = TCA_ERR_NOT_CONVERGED;
+    if (si != TCA_OK && status == TCA_OK) status = si;
+    if (info) {
+      info[i].iters = hs.iters;
+      info[i].refinements = restarts[i];
+      info[i].rel_res_true = hs.bnorm == 0.0 ? 0.0 : hs.aux;
+      info[i].rel_res_recursive = hs.bnorm > 0 ? std::sqrt(std::max(hs.rho, 0.0)) / hs.bnorm : 0.0;
+      info[i].seconds = secs;
+      info[i].sweep_ms = 0.0;
+      info[i].sweep_launches = 0;
+      info[i].reserved = 0;
+    }
+  }
+  return status;
+}
+
 }  // namespace tca
 
 using namespace tca;
+
+extern "C" tca_status tca_solve_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
+                                        const tca_solve_opts* opts, tca_solve_info* info, cudaStream_t stream) {
+  if (count <= 0 || !plans || !b || !x) return TCA_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !b[i] || !x[i]) return TCA_ERR_INVALID_ARG;
+    if (plans[i]->prec != TCA_F32) return TCA_ERR_UNSUPPORTED;
+    if (!is_device_ptr(b[i]) || !is_device_ptr(x[i]) || (uintptr_t)x[i] % 16 != 0) return TCA_ERR_UNSUPPORTED;
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == plans[i]) return TCA_ERR_INVALID_ARG;  // each instance needs its own plan
+  }
+  return solve_batched_impl(count, plans, reinterpret_cast<const float* const*>(b), reinterpret_cast<float* const*>(x),
+                            opts, info, stream);
+}
 
 extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
                                 tca_solve_info* info, cudaStream_t stream) {

@@ -591,6 +591,10 @@ tca_status launch_fused(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
       best_nc = nc;
     }
   }
+  // An autotuned chunk count (tca_autotune) overrides the wave model.
+  if (p->fused_nchunks > 0 && (int64_t)tiles * p->fused_nchunks <= p->red.max_blocks)
+    best_nc = std::min(p->fused_nchunks, n1);
+  p->fused_model_nchunks = best_nc;
   a.chunk = (n1 + best_nc - 1) / best_nc;
   a.nchunks = (n1 + a.chunk - 1) / a.chunk;
   a.tiles3 = tiles3;

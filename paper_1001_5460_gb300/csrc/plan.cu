@@ -2,6 +2,7 @@
 // mode ordering, workspace.  Implements tca_plan / tca_destroy and the small
 // status helpers of tca.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -362,7 +363,9 @@ extern "C" tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, con
   if (!(lam >= 0.0) || !std::isfinite(lam)) return TCA_ERR_INVALID_ARG;
   const uint32_t mask = reg ? reg->reg_mode_mask : 0u;
 
+  static std::atomic<uint64_t> generations{0};
   tca_plan_s* p = new tca_plan_s();
+  p->generation = ++generations;
   p->d = order;
   p->prec = prec;
   p->lambda = lam;

@@ -102,6 +102,8 @@ struct tca_plan_s {
   int order_bwd[tca::kMaxModes];  // mode order for apply_T
   bool all_band = true;
   bool fused_ok = false;          // fused normal-operator sweep applies to this shape
+  int fused_nchunks = 0;          // autotuned chunk count along mode 1 (0: wave model)
+  int fused_model_nchunks = 0;    // chunk count the last fused launch used
 
   int64_t ws_elems = 0;           // capacity of each ping-pong buffer (elements)
   void* ws[2] = {nullptr, nullptr};
@@ -132,6 +134,7 @@ struct tca_plan_s {
   cudaEvent_t sweep_ev[2 * tca::kMaxProfiledIters] = {};  // start/end per iteration of a profiled graph
 
   int num_sms = 0;
+  uint64_t generation = 0;  // unique per plan created in this process (cache keys)
 };
 
 namespace tca {

@@ -207,16 +207,16 @@ def instance_bspline(shape, seed: int, oversample: float = 1.5, lam: float = 1e-
     return Instance(tuple(shape), factors, x_true, noise, lam, seed)
 
 
-def instance_batched(index: int, base_seed: int = 100) -> Instance:
+def instance_batched(index: int, base_seed: int = 100, lo: int = 24, hi: int = 96) -> Instance:
     """One of the uneven batched instances (seed = base_seed + index).
 
-    Sizes n_k ~ U{24..96} for three modes and a 4th mode in {1, 4, 8} (1 means a
-    3D instance).  Even indices use dense Gaussian factors, odd ones B-spline
+    Sizes n_k ~ U{lo..hi} (24..96 by default) for three modes and a 4th mode in
+    {1, 4, 8} (1 means a 3D instance).  Even indices use dense Gaussian factors, odd ones B-spline
     factors; m_k = ceil(1.5 n_k); lambda is log-uniform in [1e-4, 1e-2].
     """
     seed = base_seed + index
     rng = np.random.default_rng(seed)
-    dims = [int(rng.integers(24, 97)) for _ in range(3)]
+    dims = [int(rng.integers(lo, hi + 1)) for _ in range(3)]
     n4 = int(rng.choice([1, 4, 8]))
     if n4 > 1:
         dims.append(n4)

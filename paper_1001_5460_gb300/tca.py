@@ -76,6 +76,13 @@ _lib.tca_apply_mode.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _i64p, _vp, _vp
 _lib.tca_apply_mode.restype = ctypes.c_int
 _lib.tca_solve.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info), _vp]
 _lib.tca_solve.restype = ctypes.c_int
+_lib.tca_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info), _vp]
+_lib.tca_solve_batched.restype = ctypes.c_int
+_lib.tca_autotune.argtypes = [_vp, _vp]
+_lib.tca_autotune.restype = ctypes.c_int
+_lib.tca_autotuned_chunks.argtypes = [_vp]
+_lib.tca_autotuned_chunks.restype = ctypes.c_int
 _lib.tca_rel_residual_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
 _lib.tca_rel_residual_noalloc.restype = ctypes.c_int
 _lib.tca_destroy.argtypes = [_vp]
@@ -152,7 +159,7 @@ def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
 
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
+            "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_rel_residual_noalloc", "tca_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
 
 
 class Factor:
@@ -242,9 +249,35 @@ class Plan:
         st = _lib.tca_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
         if raise_on_error:
             _check(st, "tca_solve", ok=(OK, ERR_NOT_CONVERGED))
-        return st, {"iters": info.iters, "refinements": info.refinements, "rel_res_true": info.rel_res_true,
-                    "rel_res_recursive": info.rel_res_recursive, "seconds": info.seconds,
-                    "sweep_ms": info.sweep_ms, "sweep_launches": info.sweep_launches}
+        return st, _info_dict(info)
+
+    def autotune(self, stream=None) -> int:
+        """Time the fused sweep's tile extents on this GPU and keep the fastest; returns the choice (0: none)."""
+        _check(_lib.tca_autotune(self._h, _stream(stream)), "tca_autotune")
+        return int(_lib.tca_autotuned_chunks(self._h))
+
+
+def _info_dict(info) -> dict:
+    return {"iters": info.iters, "refinements": info.refinements, "rel_res_true": info.rel_res_true,
+            "rel_res_recursive": info.rel_res_recursive, "seconds": info.seconds,
+            "sweep_ms": info.sweep_ms, "sweep_launches": info.sweep_launches}
+
+
+def solve_batched(plans, bs, xs, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
+                  check_every: int = 16, stream=None, raise_on_error: bool = True):
+    """Solve every plans[i] system for bs[i] into xs[i] in one graph launch; returns (status, [info dicts])."""
+    count = len(plans)
+    if not (len(bs) == count == len(xs)) or count == 0:
+        raise ValueError("plans, bs and xs must be non-empty and of equal length")
+    hp = (_vp * count)(*[p.handle for p in plans])
+    bp = (_vp * count)(*[_ptr(b) for b in bs])
+    xp = (_vp * count)(*[_ptr(x) for x in xs])
+    opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, 0.0, 0, int(check_every), 0)
+    infos = (tca_solve_info * count)()
+    st = _lib.tca_solve_batched(count, hp, bp, xp, ctypes.byref(opts), infos, _stream(stream))
+    if raise_on_error:
+        _check(st, "tca_solve_batched", ok=(OK, ERR_NOT_CONVERGED))
+    return st, [_info_dict(i) for i in infos]
 
 
 def plan_from_instance(inst, precision="f32", reg_mask=None, stream=None) -> Plan:
