@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
-    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense"],
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense", "batched"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -82,6 +82,9 @@ def run_case(args, local):
                           "useful_tflops": round(2 * n * 96 / ms / 1e9, 2),
                           "issued_tflops_3xtf32": round(3 * 2 * n * 96 / ms / 1e9, 2)}), flush=True)
         return
+    if args.case == "batched":
+        run_batched(args, device)
+        return
     inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, with_truth=False)
     plan = tca.plan_from_instance(inst, precision="f32")
     x = torch.randn(SHAPE, dtype=torch.float32, device=device)
@@ -114,6 +117,74 @@ def run_case(args, local):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     print(json.dumps({"case": args.case, "ms": round(ms, 5), "gbs": round(nbytes / ms / 1e6, 1)}), flush=True)
+
+
+BATCH = 64
+
+
+def run_batched(args, device):
+    """64 uneven instances (3D/4D, n_k ~ U[24,96], n_4 in {1,4,8}, half dense, half B-spline,
+    lambda log-uniform in [1e-4,1e-2]) solved to 1e-6 in one graph launch, against the same
+    instances solved one after another with tca_solve."""
+    import torch
+
+    from paper_1001_5460_gb300 import synth, tca
+
+    insts = [synth.instance_batched(i) for i in range(BATCH)]
+    plans = [tca.plan_from_instance(inst, precision="f32") for inst in insts]
+    bs, xs = [], []
+    for inst, plan in zip(insts, plans):
+        xt = torch.from_numpy(inst.x_true).to(device)
+        b = torch.from_numpy(np.ascontiguousarray(inst.noise, dtype=np.float32)).to(device)
+        ax = torch.empty_like(b)
+        plan.apply(xt, ax)
+        bs.append(ax + b)
+        xs.append(torch.empty(inst.shape, dtype=torch.float32, device=device))
+    torch.cuda.synchronize()
+    unknowns = sum(int(np.prod(i.shape)) for i in insts)
+    t0 = time.perf_counter()
+    st, infos = tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0  # graph capture + autotune + solve
+    for _ in range(max(args.warmup - 1, 0)):
+        tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = tca.kernel_launches()
+    e0.record()
+    for _ in range(args.steps):
+        st, infos = tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
+    e1.record()
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    launches = (tca.kernel_launches() - launches0) // max(args.steps, 1)
+    # The same instances, one tca_solve each (each plan's own cached iteration graph).
+    for plan, b, x in zip(plans, bs, xs):
+        plan.solve(b, x, rtol=RTOL, max_iter=20000)
+    torch.cuda.synchronize()
+    e0.record()
+    seq_infos = []
+    for _ in range(args.steps):
+        seq_infos = [plan.solve(b, x, rtol=RTOL, max_iter=20000)[1] for plan, b, x in zip(plans, bs, xs)]
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    iters = [i["iters"] for i in infos]
+    slowest = sorted(range(BATCH), key=lambda k: -seq_infos[k]["seconds"])[:4]
+    print(json.dumps({
+        "case": "batched", "instances": BATCH, "unknowns": unknowns, "status": int(st),
+        "batched_ms": round(batched_ms, 3), "sequential_ms": round(seq_ms, 3),
+        "speedup": round(seq_ms / batched_ms, 3), "first_call_s": round(first_s, 3),
+        "iters_min": min(iters), "iters_median": int(statistics.median(iters)), "iters_max": max(iters),
+        "iters_total": int(sum(iters)), "restarts": int(sum(i["refinements"] for i in infos)),
+        "rel_res_true_max": max(i["rel_res_true"] for i in infos),
+        "seq_iters_total": int(sum(i["iters"] for i in seq_infos)),
+        "gpu_launches_lower_bound": int(launches),
+        "autotuned_chunks": [p.autotune() for p, i in zip(plans, insts) if i.factors[0].kind == "ell4"],
+        "slowest_alone": [{"shape": list(insts[k].shape), "kind": insts[k].factors[0].kind,
+                           "iters": seq_infos[k]["iters"], "ms": round(1e3 * seq_infos[k]["seconds"], 2)}
+                          for k in slowest],
+    }), flush=True)
 
 
 def dist_setup(n_gpus):

@@ -188,19 +188,22 @@ TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_
  * (any order, shape and factor kinds; a plan may not appear twice).  b[i]:
  * m_i-shaped, x[i]: n_i-shaped, both device memory, x[i] 16-byte aligned;
  * host or unaligned buffers give TCA_ERR_UNSUPPORTED.  opts applies to every
- * instance (rtol, max_iter, x0_given, check_every = iterations of every
- * instance per body pass of the loop graph; profile is ignored).
- * The first call for a given set of plans and buffers captures two graphs:
- * a set-up graph (A^T b in double-float, scalars, first residual, instances
- * as parallel branches) and a loop graph whose single while-conditional node
- * repeats check_every iterations of every still-running instance until all
- * have met rtol, broken down or used max_iter.  Later calls with the same
- * plans, buffers and options replay them.  After the loop the true residual
- * of each instance is recomputed in double-float and instances above rtol
- * restart from their x (info[i].refinements counts restarts).  info: `count`
+ * instance (rtol, max_iter, x0_given, check_every = CG iterations per pass
+ * of an instance's inner loop; profile is ignored).
+ * The first call for a given set of plans, buffers and options autotunes
+ * the banded plans (tca_autotune) and captures one graph in which every
+ * instance is an independent branch: set-up (A^T b in double-float, scalars,
+ * first residual), then a while-conditional loop of restarts whose body runs
+ * a nested while-conditional loop of check_every CG iterations until the
+ * recursive residual meets rtol, recomputes the true residual in
+ * double-float and, while it misses rtol and iterations remain, restarts CG
+ * from x.  An instance that finishes leaves its loops while the others keep
+ * iterating.  Later calls with the same signature replay the graph: one
+ * graph launch per call, no host round trip until every instance is done
+ * (info[i].refinements counts the restarts, at most 16).  info: `count`
  * entries or NULL; seconds is the wall time of the whole batch.  Returns the
  * first non-OK instance status (TCA_ERR_NOT_CONVERGED / TCA_ERR_BREAKDOWN);
- * every x[i] and info[i] is still written.  The graphs are cached per
+ * every x[i] and info[i] is still written.  The graph is cached per
  * process for one batch at a time.  Synchronises the stream. */
 TCA_API tca_status tca_solve_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
                                      const tca_solve_opts* opts, tca_solve_info* info, cudaStream_t stream);

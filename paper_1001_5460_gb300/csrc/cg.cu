@@ -528,40 +528,68 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
 // ---------------------------------------------------------------------------
 // Batched solve: many independent plans in one CUDA graph launch.
 //
-// The setup graph (A^T b, scalars, r = A^T b for every instance) and the loop
-// graph are built once per batch signature.  The loop graph is a single
-// while-conditional node; its body runs `every` CG iterations of every
-// instance as parallel branches (instances spread over a pool of capture
-// streams) and ends with a one-thread kernel that keeps the loop going while
-// any instance is still iterating.  One cudaGraphLaunch therefore iterates
-// the whole batch to recursive convergence; the host then checks each true
-// residual and relaunches for the (rare) instances that need a restart.
+// One graph holds every instance as an independent branch:
+//   set-up: A^T b in double-float, scalars, r = A^T b, start test
+//   WHILE (instance not finished) {                      restarts
+//     inner = !done
+//     WHILE (inner) { check_every CG iterations; inner = !done }
+//     true residual in double-float; restart from x if it misses rtol
+//     outer = !done
+//   }
+// The branches share nothing, so an instance that converges early leaves its
+// loop while the others keep iterating, and the GPU runs the kernels of all
+// running instances concurrently.  The host launches the graph once and reads
+// every instance's scalars afterwards.
 
 namespace {
 
-__global__ void batch_cond_kernel(Scalars* const* __restrict__ scal, int count, cudaGraphConditionalHandle h) {
-  int running = 0;
-  for (int i = 0; i < count; ++i) running |= cg_done(scal[i]) ? 0 : 1;
-  cudaGraphSetConditional(h, running ? 1u : 0u);
+constexpr int kMaxRestarts = 16;
+
+// Loop condition: one thread sets the handle from the instance's stop flags.
+__global__ void cond_running_kernel(const Scalars* sc, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, cg_done(sc) ? 0u : 1u);
 }
 
 // Start-of-iteration stop test on the device (a zero right-hand side or an
 // exact initial guess), so that such an instance does no iteration at all.
 __global__ void batch_start_test_kernel(Scalars* sc) {
+  sc->restarts = 0;
   if (sc->bnorm == 0.0 || sqrt(sc->rho) <= sc->rtol * sc->bnorm) sc->converged = 1;
+}
+
+// After the true residual (sc->aux = ||A^T b - K x|| / ||A^T b||, r = that
+// residual rounded to FP32): when it misses rtol and iterations remain, start
+// a fresh direction from r (rho = <r, r>, beta = 0).  Every block takes the
+// same decision from the scalars, which only the last block changes.
+__global__ void __launch_bounds__(kVecThreads) batch_restart_kernel(const float* __restrict__ r, int64_t n,
+                                                                    Scalars* sc, Reduce red) {
+  __shared__ double sh[kVecThreads / 32];
+  if (sc->breakdown || sc->bnorm == 0.0 || !(sc->aux > sc->rtol) || sc->iters >= sc->max_iter ||
+      sc->restarts >= kMaxRestarts)
+    return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)r[i] * (double)r[i];
+  double t;
+  if (dev::grid_sum_last(acc, red, &t, sh)) {
+    sc->rho = t;
+    sc->beta = 0.0;
+    sc->restarts += 1;
+    sc->converged = sqrt(t) <= sc->rtol * sc->bnorm ? 1 : 0;
+  }
 }
 
 constexpr int kBatchStreams = 64;
 
-struct BatchGraphs {
+struct BatchGraph {
   std::vector<const void*> key;
-  cudaGraphExec_t setup = nullptr, loop = nullptr;
-  Scalars** scal_dev = nullptr;
-  uint64_t launches_setup = 0, launches_loop = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> l_setup, l_iter, l_check;  // launches per set-up / iteration / restart check
+  int every = 0;
 };
 
 std::mutex g_batch_mutex;
-BatchGraphs g_batch;  // last batch signature (one cached batch per process)
+BatchGraph g_batch;  // last batch signature (one cached batch per process)
 cudaStream_t g_pool[kBatchStreams] = {};
 cudaEvent_t g_fork = nullptr, g_join[kBatchStreams] = {};
 
@@ -602,76 +630,124 @@ tca_status enqueue_setup(tca_plan_s* p, const float* b, float* x, double rtol, i
   return TCA_OK;
 }
 
-// Capture `body(i, stream)` for every instance on the stream pool, forked from
-// and joined back into the capturing stream cs.
-template <typename F>
-tca_status capture_branches(int count, cudaStream_t cs, F body) {
-  TCA_CUDA_TRY(cudaEventRecord(g_fork, cs));
-  const int ns = std::min(count, kBatchStreams);
-  for (int k = 0; k < ns; ++k) TCA_CUDA_TRY(cudaStreamWaitEvent(g_pool[k], g_fork, 0));
-  for (int i = 0; i < count; ++i) TCA_TRY(body(i, g_pool[i % ns]));
-  for (int k = 0; k < ns; ++k) {
-    TCA_CUDA_TRY(cudaEventRecord(g_join[k], g_pool[k]));
-    TCA_CUDA_TRY(cudaStreamWaitEvent(cs, g_join[k], 0));
+// Conditional handle owned by the graph that stream s is capturing into.
+tca_status capture_handle(cudaStream_t s, unsigned default_value, bool assign_default, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  TCA_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive || !g) {
+    set_error_message("stream is not capturing");
+    return TCA_ERR_CUDA;
   }
+  TCA_CUDA_TRY(cudaGraphConditionalHandleCreate(h, g, default_value, assign_default ? cudaGraphCondAssignDefault : 0));
+  return TCA_OK;
+}
+
+// Append a WHILE node on handle h to the capture sequence of s; returns its body graph.
+tca_status capture_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  TCA_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edges, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  TCA_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  TCA_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return TCA_OK;
+}
+
+// Capture `fill(stream)` into the (empty) graph g.
+template <typename F>
+tca_status capture_into(cudaGraph_t g, cudaStream_t cs, F fill) {
+  TCA_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const tca_status st = fill(cs);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (st != TCA_OK) return st;
+  TCA_CUDA_TRY(e);
   return TCA_OK;
 }
 
 tca_status build_batch(int count, tca_plan_s** plans, const float* const* b, float* const* x, double rtol,
-                       int max_iter, bool x0, int every, BatchGraphs* bg) {
+                       int max_iter, bool x0, int every, BatchGraph* bg) {
   cudaStream_t cs;
   TCA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  const uint64_t before = tca_kernel_launches(0);
+  const uint64_t saved = tca_kernel_launches(1);
+  bg->l_setup.assign(count, 0);
+  bg->l_iter.assign(count, 0);
+  bg->l_check.assign(count, 0);
+  bg->every = every;
+  std::vector<cudaGraph_t> outer(count, nullptr);
+  std::vector<cudaGraphConditionalHandle> ho(count);
   tca_status st = TCA_OK;
-  // Setup graph.
-  cudaGraph_t g = nullptr;
-  TCA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  st = capture_branches(count, cs, [&](int i, cudaStream_t s) {
-    return enqueue_setup(plans[i], b[i], x[i], rtol, max_iter, x0, s);
-  });
-  cudaError_t e = cudaStreamEndCapture(cs, &g);
-  const uint64_t mid = tca_kernel_launches(0);
-  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bg->setup, g, 0);
-  if (g) cudaGraphDestroy(g);
-  // Loop graph: while (any instance iterating) { every iterations of every instance }.
-  cudaGraph_t lg = nullptr;
-  cudaGraphConditionalHandle h;
-  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphCreate(&lg, 0);
-  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, lg, 1, cudaGraphCondAssignDefault);
-  cudaGraph_t body = nullptr;
-  if (st == TCA_OK && e == cudaSuccess) {
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, lg, nullptr, nullptr, 0, &cp);
-    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+  // Top level: per instance, set-up then the restart loop, as parallel branches.
+  cudaGraph_t top = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = [&]() -> tca_status {
+      TCA_CUDA_TRY(cudaEventRecord(g_fork, cs));
+      const int ns = std::min(count, kBatchStreams);
+      for (int k = 0; k < ns; ++k) TCA_CUDA_TRY(cudaStreamWaitEvent(g_pool[k], g_fork, 0));
+      for (int i = 0; i < count; ++i) {
+        cudaStream_t s = g_pool[i % ns];
+        const uint64_t l0 = tca_kernel_launches(0);
+        TCA_TRY(enqueue_setup(plans[i], b[i], x[i], rtol, max_iter, x0, s));
+        bg->l_setup[i] = tca_kernel_launches(0) - l0;
+        TCA_TRY(capture_handle(s, 1, true, &ho[i]));
+        TCA_TRY(capture_while(s, ho[i], &outer[i]));
+      }
+      for (int k = 0; k < ns; ++k) {
+        TCA_CUDA_TRY(cudaEventRecord(g_join[k], g_pool[k]));
+        TCA_CUDA_TRY(cudaStreamWaitEvent(cs, g_join[k], 0));
+      }
+      return TCA_OK;
+    }();
+    e = cudaStreamEndCapture(cs, &top);
   }
-  if (st == TCA_OK && e == cudaSuccess)
-    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (st == TCA_OK && e == cudaSuccess) {
-    st = capture_branches(count, cs, [&](int i, cudaStream_t s) -> tca_status {
-      tca_plan_s* p = plans[i];
+  // Restart loop body and inner iteration loop of every instance.
+  for (int i = 0; i < count && st == TCA_OK && e == cudaSuccess; ++i) {
+    tca_plan_s* p = plans[i];
+    cudaGraph_t inner = nullptr;
+    cudaGraphConditionalHandle hi;
+    st = capture_into(outer[i], cs, [&](cudaStream_t s) -> tca_status {
+      TCA_TRY(capture_handle(s, 0, false, &hi));
+      cond_running_kernel<<<1, 1, 0, s>>>(p->scal, hi);
+      TCA_LAUNCH_CHECK();
+      TCA_TRY(capture_while(s, hi, &inner));
+      const uint64_t l0 = tca_kernel_launches(0);
+      TCA_TRY(residual_ff(p, x[i], reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
+                          (float*)p->r, first_reduce(p), second_reduce(p), s));
+      const int vgrid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
+      batch_restart_kernel<<<vgrid, kVecThreads, 0, s>>>((const float*)p->r, p->N, p->scal, first_reduce(p));
+      TCA_LAUNCH_CHECK();
+      cond_running_kernel<<<1, 1, 0, s>>>(p->scal, ho[i]);
+      TCA_LAUNCH_CHECK();
+      bg->l_check[i] = tca_kernel_launches(0) - l0 + 2;  // + the inner gate
+      return TCA_OK;
+    });
+    if (st != TCA_OK) break;
+    st = capture_into(inner, cs, [&](cudaStream_t s) -> tca_status {
+      const uint64_t l0 = tca_kernel_launches(0);
       for (int it = 0; it < every; ++it)
         TCA_TRY(enqueue_iteration<float>(p, x[i], (const float*)p->p[it & 1], (float*)p->p[(it + 1) & 1], s,
                                          nullptr, nullptr));
+      bg->l_iter[i] = (tca_kernel_launches(0) - l0) / every;
+      cond_running_kernel<<<1, 1, 0, s>>>(p->scal, hi);
+      TCA_LAUNCH_CHECK();
       return TCA_OK;
     });
-    batch_cond_kernel<<<1, 1, 0, cs>>>(bg->scal_dev, count, h);
-    note_launches(1);
-    cudaGraph_t out = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &out);
-    if (e == cudaSuccess) e = e2;
   }
-  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bg->loop, lg, 0);
-  if (lg) cudaGraphDestroy(lg);
-  const uint64_t after = tca_kernel_launches(0);
+  if (st == TCA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bg->exec, top, 0);
+  if (top) cudaGraphDestroy(top);
   tca_kernel_launches(1);
-  note_launches(before);  // captured launches are counted when the graphs run
-  bg->launches_setup = mid - before;
-  bg->launches_loop = after - mid;
+  note_launches(saved);  // captured launches are counted when the graph runs
   cudaStreamDestroy(cs);
   if (st != TCA_OK) return st;
   if (e != cudaSuccess) {
@@ -709,73 +785,37 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
     key.push_back(b[i]);
     key.push_back(x[i]);
   }
-  if (key != g_batch.key || !g_batch.loop) {
-    if (g_batch.setup) cudaGraphExecDestroy(g_batch.setup);
-    if (g_batch.loop) cudaGraphExecDestroy(g_batch.loop);
-    g_batch.setup = g_batch.loop = nullptr;
+  if (key != g_batch.key || !g_batch.exec) {
+    if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+    g_batch.exec = nullptr;
     g_batch.key.clear();
-    cudaFree(g_batch.scal_dev);
-    g_batch.scal_dev = nullptr;
     // Tile extents of the banded instances' fused sweeps come from the
     // autotuner (cached per shape).
     for (int i = 0; i < count; ++i) TCA_TRY(tca_autotune(plans[i], s));
-    std::vector<Scalars*> sp(count);
-    for (int i = 0; i < count; ++i) sp[i] = plans[i]->scal;
-    TCA_CUDA_TRY(cudaMalloc((void**)&g_batch.scal_dev, sizeof(Scalars*) * count));
-    TCA_CUDA_TRY(cudaMemcpy(g_batch.scal_dev, sp.data(), sizeof(Scalars*) * count, cudaMemcpyHostToDevice));
     TCA_TRY(build_batch(count, plans, b, x, rtol, max_iter, x0, every, &g_batch));
     g_batch.key = key;
   }
-  TCA_CUDA_TRY(cudaGraphLaunch(g_batch.setup, s));
-  note_launches(g_batch.launches_setup);
-  std::vector<int> restarts(count, 0);
-  std::vector<char> active(count, 1);
-  tca_status status = TCA_OK;
-  for (int round = 0;; ++round) {
-    TCA_CUDA_TRY(cudaGraphLaunch(g_batch.loop, s));
-    note_launches(g_batch.launches_loop);  // one body replay's worth; a lower bound
-    // True residual (double-float) of every instance that iterated in this
-    // launch; restart those above rtol.
-    bool again = false;
-    for (int i = 0; i < count; ++i) {
-      if (!active[i]) continue;
-      tca_plan_s* p = plans[i];
-      TCA_TRY(residual_ff(p, x[i], reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
-                          (float*)p->r, first_reduce(p), second_reduce(p), s));
-    }
-    for (int i = 0; i < count; ++i)
-      if (active[i])
-        TCA_CUDA_TRY(cudaMemcpyAsync(plans[i]->scal_host, plans[i]->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-    TCA_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int i = 0; i < count; ++i) {
-      if (!active[i]) continue;
-      active[i] = 0;
-      tca_plan_s* p = plans[i];
-      const Scalars& hs = *p->scal_host;
-      if (hs.breakdown || hs.bnorm == 0.0 || hs.aux <= rtol || hs.iters >= max_iter) continue;
-      active[i] = 1;
-      // Restart from x: r holds the double-float residual rounded to FP32.
-      const int vgrid = std::min(vector_grid(p, p->N), second_reduce(p).max_blocks - 1);
-      cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->r, nullptr, (float*)p->r, p->N, p->scal,
-                                                            first_reduce(p), 0, second_reduce(p));
-      TCA_LAUNCH_CHECK();
-      batch_start_test_kernel<<<1, 1, 0, s>>>(p->scal);
-      TCA_LAUNCH_CHECK();
-      ++restarts[i];
-      again = true;
-    }
-    if (!again || round > 8) break;
-  }
+  TCA_CUDA_TRY(cudaGraphLaunch(g_batch.exec, s));
+  for (int i = 0; i < count; ++i)
+    TCA_CUDA_TRY(cudaMemcpyAsync(plans[i]->scal_host, plans[i]->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  tca_status status = TCA_OK;
   for (int i = 0; i < count; ++i) {
     const Scalars& hs = *plans[i]->scal_host;
+    // Launch count of this instance's branch: set-up, one restart check per
+    // pass of the outer loop, and the inner passes (iterations that find the
+    // instance finished still launch and return at entry).
+    const uint64_t passes = (uint64_t)(hs.iters + every - 1) / every;  // a lower bound
+    note_launches(g_batch.l_setup[i] + (uint64_t)(hs.restarts + 1) * g_batch.l_check[i] +
+                  passes * ((uint64_t)every * g_batch.l_iter[i] + 1));
     tca_status si = TCA_OK;
     if (hs.breakdown) si = TCA_ERR_BREAKDOWN;
-    else if (hs.bnorm != 0.0 && hs.aux > rtol) si = TCA_ERR_NOT_CONVERGED;
+    else if (hs.bnorm != 0.0 && !(hs.aux <= rtol)) si = TCA_ERR_NOT_CONVERGED;
     if (si != TCA_OK && status == TCA_OK) status = si;
     if (info) {
       info[i].iters = hs.iters;
-      info[i].refinements = restarts[i];
+      info[i].refinements = hs.restarts;
       info[i].rel_res_true = hs.bnorm == 0.0 ? 0.0 : hs.aux;
       info[i].rel_res_recursive = hs.bnorm > 0 ? std::sqrt(std::max(hs.rho, 0.0)) / hs.bnorm : 0.0;
       info[i].seconds = secs;

@@ -73,6 +73,8 @@ struct Scalars {
   int32_t breakdown;
   int32_t iters;     // CG iterations completed on the device
   int32_t max_iter;  // kernels of an iteration skip their work once iters reaches it
+  int32_t restarts;  // device-side restarts from the true residual (batched solve)
+  int32_t pad;
 };
 
 // True once the iteration loop must stop doing work (converged, broken down or
