@@ -1,0 +1,740 @@
+// Learned initial guess / preconditioner: a 4-layer 3D convolutional network
+// over modes 1..3 of a tensor (mode 4 is a batch index), trained on the GPU by
+// the kernels in this file (forward, backpropagation, Adam).
+//
+//   h1 = relu(conv(u, W1) + b1)      1 -> 32 channels
+//   h2 = relu(conv(h1, W2) + b2)     32 -> 32
+//   h3 = relu(conv(h2, W3) + b3)     32 -> 32
+//   y  = conv(h3, W4) + b4           32 -> 1
+//
+// conv is the 'same' 3x3x3 cross-correlation with zero padding; tap
+// t = 9a + 3b + e (a, b, e in 0..2) reads the neighbour at offset
+// (a-1, b-1, e-1) in modes 1..3.  Weights and the activations h1..h3 (and
+// their gradients) are stored in bfloat16; every sum accumulates in FP32.
+//
+// Layouts.  A tensor of shape (D, H, W, B) is a C-order array, voxel
+// v = ((z H + y) W + x) B + n.  A 32-channel activation is [V][32] bfloat16
+// (64 bytes per voxel, channels fastest).  The master parameters are FP32 in
+// the packed order of the public API: per layer W[c_out][c_in][3][3][3], b.
+// After every update a preparation kernel writes the bfloat16-rounded copies
+// in the layouts the convolution kernels read (forward and flipped/transposed
+// for the input gradients: the adjoint of a correlation with W[o][c][t] is
+// the correlation with W[o][c][26 - t] with the channel roles swapped).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "tca_internal.cuh"
+#include "../../include/tca_net.h"
+
+namespace tca {
+namespace net {
+
+constexpr int C = 32;
+constexpr int T = 27;
+// Packed parameter offsets (floats).
+constexpr int64_t kW1 = 0, kB1 = kW1 + C * T;
+constexpr int64_t kW2 = kB1 + C, kB2 = kW2 + C * C * T;
+constexpr int64_t kW3 = kB2 + C, kB3 = kW3 + C * C * T;
+constexpr int64_t kW4 = kB3 + C, kB4 = kW4 + C * T;
+constexpr int64_t kParams = kB4 + 1;
+
+// Derived (bfloat16-rounded) weight layouts, FP32 or bf16 as noted.
+struct Derived {
+  __align__(16) float w1f[T * C];  // [t][co]                      layer 1 forward
+  __align__(16) float w4b[T * C];  // [t][ci] = W4[0][ci][26 - t]  layer 4 input gradient (1 -> 32)
+  __align__(16) float w4f[T * C];  // [t][ci]                      layer 4 forward (32 -> 1)
+  __align__(16) float b1[C];
+  __align__(16) float b2[C];
+  __align__(16) float b3[C];
+  __align__(16) float b4[4];
+  __align__(16) __nv_bfloat16 w2f[T * C * C];  // [t][i][o] = W2[o][i][t]
+  __align__(16) __nv_bfloat16 w3f[T * C * C];
+  __align__(16) __nv_bfloat16 w2b[T * C * C];  // [t][o][i] = W2[o][i][26 - t]: input gradient of layer 2
+  __align__(16) __nv_bfloat16 w3b[T * C * C];
+};
+
+// Address of a member of the device-resident Derived block.
+#define DW(n, field) \
+  (reinterpret_cast<const std::remove_reference_t<decltype(Derived::field[0])>*>( \
+      reinterpret_cast<const char*>((n)->dw) + offsetof(Derived, field)))
+
+struct Dims {
+  int D, H, W, B;
+  int64_t V;
+};
+
+__device__ __forceinline__ int64_t tap_offset(int t, const Dims& d) {
+  const int a = t / 9 - 1, b = (t / 3) % 3 - 1, e = t % 3 - 1;
+  return (((int64_t)a * d.H + b) * d.W + e) * d.B;
+}
+
+// Validity mask of the 27 taps for voxel (z, y, x): bit t set when the
+// neighbour lies inside the volume.
+__device__ __forceinline__ unsigned tap_mask(int z, int y, int x, const Dims& d) {
+  unsigned m = 0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int zz = z + t / 9 - 1, yy = y + (t / 3) % 3 - 1, xx = x + t % 3 - 1;
+    if (zz >= 0 && zz < d.D && yy >= 0 && yy < d.H && xx >= 0 && xx < d.W) m |= 1u << t;
+  }
+  return m;
+}
+
+__device__ __forceinline__ void decode(int64_t v, const Dims& d, int& z, int& y, int& x) {
+  int64_t r = v / d.B;
+  x = (int)(r % d.W);
+  r /= d.W;
+  y = (int)(r % d.H);
+  z = (int)(r / d.H);
+}
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 h) { return __bfloat162float(h); }
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float round_bf(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+
+// Store 32 FP32 values as 32 bfloat16 (64 bytes) at dst.
+__device__ __forceinline__ void store32(__nv_bfloat16* dst, const float* acc) {
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 w;
+    w.x = pack2(acc[8 * q + 0], acc[8 * q + 1]);
+    w.y = pack2(acc[8 * q + 2], acc[8 * q + 3]);
+    w.z = pack2(acc[8 * q + 4], acc[8 * q + 5]);
+    w.w = pack2(acc[8 * q + 6], acc[8 * q + 7]);
+    d4[q] = w;
+  }
+}
+__device__ __forceinline__ void load32(const __nv_bfloat16* src, float* out) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 w = __ldg(s4 + q);
+    out[8 * q + 0] = bf_lo(w.x); out[8 * q + 1] = bf_hi(w.x);
+    out[8 * q + 2] = bf_lo(w.y); out[8 * q + 3] = bf_hi(w.y);
+    out[8 * q + 4] = bf_lo(w.z); out[8 * q + 5] = bf_hi(w.z);
+    out[8 * q + 6] = bf_lo(w.w); out[8 * q + 7] = bf_hi(w.w);
+  }
+}
+
+constexpr int kThreads = 128;
+
+// ---- 1 -> 32 channels ------------------------------------------------------
+// Forward (layer 1): out = relu(sum_t w[t][co] * in[v + off t] * in_scale + b).
+// Input gradient of layer 4 (MASK): out = (sum_t w4b[t][ci] g[v + off t]) * (h3 > 0).
+template <bool MASK>
+__global__ void __launch_bounds__(kThreads) conv1to32_kernel(const float* __restrict__ in,
+                                                             const float* __restrict__ scale_dev,
+                                                             const float* __restrict__ w, const float* __restrict__ bias,
+                                                             const __nv_bfloat16* __restrict__ mask_src,
+                                                             __nv_bfloat16* __restrict__ out, Dims d) {
+  __shared__ float sw[T * C];
+  __shared__ float sb[C];
+  for (int i = threadIdx.x; i < T * C; i += blockDim.x) sw[i] = w[i];
+  if (threadIdx.x < C) sb[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+  __syncthreads();
+  const float inv = scale_dev ? 1.f / *scale_dev : 1.f;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += (int64_t)gridDim.x * blockDim.x) {
+    int z, y, x;
+    decode(v, d, z, y, x);
+    const unsigned m = tap_mask(z, y, x, d);
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = sb[c];
+    for (int t = 0; t < T; ++t) {
+      if (!(m >> t & 1u)) continue;
+      const float val = __ldg(in + v + tap_offset(t, d)) * inv;
+      const float4* w4 = reinterpret_cast<const float4*>(sw + t * C);
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q) {
+        const float4 ww = w4[q];
+        acc[4 * q + 0] = fmaf(ww.x, val, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(ww.y, val, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(ww.z, val, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(ww.w, val, acc[4 * q + 3]);
+      }
+    }
+    if constexpr (MASK) {
+      float h[C];
+      load32(mask_src + v * C, h);
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = h[c] > 0.f ? acc[c] : 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaxf(acc[c], 0.f);
+    }
+    store32(out + v * C, acc);
+  }
+}
+
+// ---- 32 -> 1 channel (layer 4 forward) ---------------------------------------
+// y = (sum_t sum_ci w4f[t][ci] h3[v + off t][ci] + b4) * out_scale
+__global__ void __launch_bounds__(kThreads) conv32to1_kernel(const __nv_bfloat16* __restrict__ h,
+                                                             const float* __restrict__ w, const float* __restrict__ bias,
+                                                             const float* __restrict__ scale_dev,
+                                                             float* __restrict__ out, Dims d) {
+  __shared__ float sw[T * C];
+  for (int i = threadIdx.x; i < T * C; i += blockDim.x) sw[i] = w[i];
+  __syncthreads();
+  const float s = scale_dev ? *scale_dev : 1.f;
+  const float b = bias[0];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += (int64_t)gridDim.x * blockDim.x) {
+    int z, y, x;
+    decode(v, d, z, y, x);
+    const unsigned m = tap_mask(z, y, x, d);
+    float acc = b;
+    for (int t = 0; t < T; ++t) {
+      if (!(m >> t & 1u)) continue;
+      float hv[C];
+      load32(h + (v + tap_offset(t, d)) * C, hv);
+      const float* wt = sw + t * C;
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc = fmaf(wt[c], hv[c], acc);
+    }
+    out[v] = acc * s;
+  }
+}
+
+// ---- 32 -> 32 channels (layers 2, 3 and their input gradients) -----------------
+// out[v][o] = act(sum_t sum_i w[t][i][o] in[v + off t][i] + b[o]); act = relu
+// (forward) or the mask (h > 0) of the layer below (input gradient).
+template <bool MASK>
+__global__ void __launch_bounds__(kThreads) conv32to32_kernel(const __nv_bfloat16* __restrict__ in,
+                                                              const __nv_bfloat16* __restrict__ w,
+                                                              const float* __restrict__ bias,
+                                                              const __nv_bfloat16* __restrict__ mask_src,
+                                                              __nv_bfloat16* __restrict__ out, Dims d) {
+  extern __shared__ __align__(16) unsigned char net_smem[];
+  uint32_t* sw = reinterpret_cast<uint32_t*>(net_smem);  // [t][i][o/2] bf16 pairs
+  for (int i = threadIdx.x; i < T * C * C / 8; i += blockDim.x)
+    reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(w)[i];
+  __shared__ float sb[C];
+  if (threadIdx.x < C) sb[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+  __syncthreads();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += (int64_t)gridDim.x * blockDim.x) {
+    int z, y, x;
+    decode(v, d, z, y, x);
+    const unsigned m = tap_mask(z, y, x, d);
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = sb[c];
+    for (int t = 0; t < T; ++t) {
+      if (!(m >> t & 1u)) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(in + (v + tap_offset(t, d)) * C);
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const uint4 iw = __ldg(src + q);
+        const float xi[8] = {bf_lo(iw.x), bf_hi(iw.x), bf_lo(iw.y), bf_hi(iw.y),
+                             bf_lo(iw.z), bf_hi(iw.z), bf_lo(iw.w), bf_hi(iw.w)};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint4* wr = reinterpret_cast<const uint4*>(sw + ((t * C + 8 * q + k) * C) / 2);
+#pragma unroll
+          for (int o8 = 0; o8 < 4; ++o8) {
+            const uint4 ww = wr[o8];
+            acc[8 * o8 + 0] = fmaf(bf_lo(ww.x), xi[k], acc[8 * o8 + 0]);
+            acc[8 * o8 + 1] = fmaf(bf_hi(ww.x), xi[k], acc[8 * o8 + 1]);
+            acc[8 * o8 + 2] = fmaf(bf_lo(ww.y), xi[k], acc[8 * o8 + 2]);
+            acc[8 * o8 + 3] = fmaf(bf_hi(ww.y), xi[k], acc[8 * o8 + 3]);
+            acc[8 * o8 + 4] = fmaf(bf_lo(ww.z), xi[k], acc[8 * o8 + 4]);
+            acc[8 * o8 + 5] = fmaf(bf_hi(ww.z), xi[k], acc[8 * o8 + 5]);
+            acc[8 * o8 + 6] = fmaf(bf_lo(ww.w), xi[k], acc[8 * o8 + 6]);
+            acc[8 * o8 + 7] = fmaf(bf_hi(ww.w), xi[k], acc[8 * o8 + 7]);
+          }
+        }
+      }
+    }
+    if constexpr (MASK) {
+      float h[C];
+      load32(mask_src + v * C, h);
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = h[c] > 0.f ? acc[c] : 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaxf(acc[c], 0.f);
+    }
+    store32(out + v * C, acc);
+  }
+}
+
+// ---- loss ----------------------------------------------------------------------
+// g = bf16(2 (y - t) / V);  loss += sum (y - t)^2 / V  (last block adds to *loss).
+__global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                                                   float* __restrict__ g, Dims d, double* loss, Reduce red) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  const float inv = 2.f / (float)d.V;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += (int64_t)gridDim.x * blockDim.x) {
+    const float diff = y[v] - t[v];
+    g[v] = round_bf(inv * diff);
+    acc += (double)diff * (double)diff;
+  }
+  double tot;
+  if (dev::grid_sum_last(acc, red, &tot, sh)) *loss += tot / (double)d.V;
+}
+
+// ---- weight gradients ------------------------------------------------------------
+// dW[t][o][i] = sum_v G[v][o] X[v + off t][i] over one chunk of rows (z, y) of the
+// volume, written as per-chunk partial sums.  CG / CX: channels of G / X (32 or 1);
+// G and X are bfloat16 [V][32] when 32 channels, FP32 [V] when 1.  A thread owns a
+// 4 (o) x 4 (i) block of one tap (1 x 4 / 4 x 1 for single-channel operands).
+template <int CG, int CX>
+__global__ void __launch_bounds__(192) wgrad_kernel(const void* __restrict__ Gp, const void* __restrict__ Xp,
+                                                    float* __restrict__ partial, Dims d, int rows_per_chunk) {
+  constexpr int NO = CG == 1 ? 1 : 4, NI = CX == 1 ? 1 : 4;
+  constexpr int GO = CG / NO, GI = CX / NI;     // groups of o and i
+  constexpr int COMBOS = T * GO * GI;
+  const int combo = blockIdx.x * blockDim.x + threadIdx.x;
+  if (combo >= COMBOS) return;
+  const int t = combo / (GO * GI);
+  const int og = (combo / GI) % GO, ig = combo % GI;
+  const int a = t / 9 - 1, b = (t / 3) % 3 - 1, e = t % 3 - 1;
+  const int64_t off = tap_offset(t, d);
+  float acc[NO * NI];
+#pragma unroll
+  for (int k = 0; k < NO * NI; ++k) acc[k] = 0.f;
+  const int rows = d.D * d.H;
+  const int r0 = blockIdx.y * rows_per_chunk, r1 = min(rows, r0 + rows_per_chunk);
+  const int x0 = max(0, -e), x1 = min(d.W, d.W - e);
+  for (int r = r0; r < r1; ++r) {
+    const int z = r / d.H, y = r % d.H;
+    if (z + a < 0 || z + a >= d.D || y + b < 0 || y + b >= d.H) continue;
+    const int64_t vb = ((int64_t)r * d.W) * d.B;
+    for (int64_t v = vb + (int64_t)x0 * d.B; v < vb + (int64_t)x1 * d.B; ++v) {
+      float gv[NO], xv[NI];
+      if constexpr (CG == 1) {
+        gv[0] = __ldg(reinterpret_cast<const float*>(Gp) + v);
+      } else {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(Gp) + v * C + og * 4));
+        gv[0] = bf_lo(w.x); gv[1] = bf_hi(w.x); gv[2] = bf_lo(w.y); gv[3] = bf_hi(w.y);
+      }
+      if constexpr (CX == 1) {
+        xv[0] = __ldg(reinterpret_cast<const float*>(Xp) + v + off);
+      } else {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(Xp) + (v + off) * C + ig * 4));
+        xv[0] = bf_lo(w.x); xv[1] = bf_hi(w.x); xv[2] = bf_lo(w.y); xv[3] = bf_hi(w.y);
+      }
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+#pragma unroll
+        for (int i = 0; i < NI; ++i) acc[o * NI + i] = fmaf(gv[o], xv[i], acc[o * NI + i]);
+    }
+  }
+  // partial[chunk][t][o][i] over the full CG x CX block.
+  float* dst = partial + (int64_t)blockIdx.y * T * CG * CX + (int64_t)t * CG * CX;
+#pragma unroll
+  for (int o = 0; o < NO; ++o)
+#pragma unroll
+    for (int i = 0; i < NI; ++i) dst[(og * NO + o) * CX + ig * NI + i] = acc[o * NI + i];
+}
+
+// Bias gradient partials: db[o] = sum_v G[v][o] per chunk of rows.
+template <int CG>
+__global__ void __launch_bounds__(256) bgrad_kernel(const void* __restrict__ Gp, float* __restrict__ partial, Dims d,
+                                                    int rows_per_chunk) {
+  __shared__ float sh[256];
+  const int rows = d.D * d.H;
+  const int r0 = blockIdx.x * rows_per_chunk, r1 = min(rows, r0 + rows_per_chunk);
+  const int64_t v0 = (int64_t)r0 * d.W * d.B, v1 = (int64_t)r1 * d.W * d.B;
+  // thread -> (channel, lane): CG == 32: 32 channels x 8 lanes; CG == 1: 256 lanes.
+  const int ch = CG == 1 ? 0 : threadIdx.x % 32;
+  const int lane = CG == 1 ? threadIdx.x : threadIdx.x / 32;
+  const int lanes = CG == 1 ? 256 : 8;
+  float acc = 0.f;
+  for (int64_t v = v0 + lane; v < v1; v += lanes) {
+    if constexpr (CG == 1) acc += __ldg(reinterpret_cast<const float*>(Gp) + v);
+    else acc += bf(reinterpret_cast<const __nv_bfloat16*>(Gp)[v * C + ch]);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < (CG == 1 ? 1 : 32)) {
+    float s = 0.f;
+    for (int l = 0; l < lanes; ++l) s += sh[CG == 1 ? l : l * 32 + ch];
+    partial[(int64_t)blockIdx.x * CG + ch] = s;
+  }
+}
+
+// Sum the chunk partials (fixed order) and add into the packed gradient:
+// weights from partial[chunk][t][o][i] to grad[w_off + (o CIN + i) 27 + t],
+// biases from bpartial[chunk][o] to grad[b_off + o].
+__global__ void reduce_grads_kernel(const float* __restrict__ partial, const float* __restrict__ bpartial,
+                                    int chunks, int co, int ci, float* __restrict__ grad, int64_t w_off,
+                                    int64_t b_off) {
+  const int nw = T * co * ci;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nw) {
+    float s = 0.f;
+    for (int c = 0; c < chunks; ++c) s += partial[(int64_t)c * nw + k];
+    const int t = k / (co * ci), o = (k / ci) % co, i = k % ci;
+    grad[w_off + ((int64_t)o * ci + i) * T + t] += s;
+  } else if (k < nw + co) {
+    const int o = k - nw;
+    float s = 0.f;
+    for (int c = 0; c < chunks; ++c) s += bpartial[(int64_t)c * co + o];
+    grad[b_off + o] += s;
+  }
+}
+
+// ---- optimiser and weight preparation ---------------------------------------------
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            int64_t n, float lr, float beta1, float beta2, float eps, float bc1, float bc2,
+                            float grad_scale) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float gk = g[k] * grad_scale;
+    const float mk = beta1 * m[k] + (1.f - beta1) * gk;
+    const float vk = beta2 * v[k] + (1.f - beta2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    w[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+    g[k] = 0.f;
+  }
+}
+
+__global__ void prep_kernel(const float* __restrict__ p, Derived* __restrict__ dw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < T * C) {
+    const int t = k / C, c = k % C;
+    dw->w1f[k] = round_bf(p[kW1 + (int64_t)c * T + t]);
+    dw->w4f[k] = round_bf(p[kW4 + (int64_t)c * T + t]);
+    dw->w4b[k] = round_bf(p[kW4 + (int64_t)c * T + (T - 1 - t)]);
+  }
+  if (k < C) {
+    dw->b1[k] = p[kB1 + k];
+    dw->b2[k] = p[kB2 + k];
+    dw->b3[k] = p[kB3 + k];
+  }
+  if (k == 0) dw->b4[0] = p[kB4];
+  if (k < T * C * C) {
+    const int t = k / (C * C), i = (k / C) % C, o = k % C;  // [t][i][o]
+    dw->w2f[k] = __float2bfloat16_rn(p[kW2 + ((int64_t)o * C + i) * T + t]);
+    dw->w3f[k] = __float2bfloat16_rn(p[kW3 + ((int64_t)o * C + i) * T + t]);
+    // input gradient: input channel i' = o of the layer, output o' = i, flipped tap
+    dw->w2b[k] = __float2bfloat16_rn(p[kW2 + ((int64_t)i * C + o) * T + (T - 1 - t)]);
+    dw->w3b[k] = __float2bfloat16_rn(p[kW3 + ((int64_t)i * C + o) * T + (T - 1 - t)]);
+  }
+}
+
+// RMS of a vector into *scale (FP32): sqrt(sum x^2 / n); 1 when it is zero.
+__global__ void __launch_bounds__(256) rms_kernel(const float* __restrict__ x, int64_t n, float* scale, Reduce red) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)x[i] * (double)x[i];
+  double tot;
+  if (dev::grid_sum_last(acc, red, &tot, sh)) {
+    const double r = sqrt(tot / (double)n);
+    *scale = r > 0.0 ? (float)r : 1.f;
+  }
+}
+
+}  // namespace net
+}  // namespace tca
+
+using namespace tca;
+using namespace tca::net;
+
+struct tca_net_s {
+  float* params = nullptr;  // master FP32, packed
+  float* grads = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  Derived* dw = nullptr;
+  int64_t adam_t = 0;
+  // activation buffers, sized for cap voxels
+  int64_t cap = 0;
+  __nv_bfloat16* h[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16* gbuf[2] = {nullptr, nullptr};
+  float* y = nullptr;
+  float* g = nullptr;
+  float* partial = nullptr;   // weight-gradient chunk partials
+  float* bpartial = nullptr;
+  int chunks_cap = 0;
+  double* loss = nullptr;     // device accumulator
+  float* scale = nullptr;     // device scalar (RMS of the input)
+  Reduce red;
+  int num_sms = 0;
+};
+
+namespace {
+
+constexpr int kMaxChunks = 256;
+constexpr size_t kConvSmem = (size_t)T * C * C * 2;  // bf16 weights of one 32 -> 32 layer
+
+tca_status net_alloc(tca_net_s* n) {
+  cudaError_t e = cudaMalloc((void**)&n->params, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->grads, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->adam_m, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->adam_v, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->dw, sizeof(Derived));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->partial, sizeof(float) * (size_t)kMaxChunks * T * C * C);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->bpartial, sizeof(float) * (size_t)kMaxChunks * C);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->scale, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->red.partials, sizeof(double) * 4096);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->red.ticket, sizeof(unsigned int) * 2);
+  if (e == cudaSuccess) e = cudaMemset(n->red.ticket, 0, sizeof(unsigned int) * 2);
+  if (e == cudaSuccess) e = cudaMemset(n->grads, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(n->adam_v, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(n->loss, 0, sizeof(double));
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return TCA_ERR_ALLOC;
+  }
+  n->red.max_blocks = 4096;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  return TCA_OK;
+}
+
+tca_status ensure_act(tca_net_s* n, int64_t V) {
+  if (V <= n->cap) return TCA_OK;
+  for (auto*& p : n->h) { cudaFree(p); p = nullptr; }
+  for (auto*& p : n->gbuf) { cudaFree(p); p = nullptr; }
+  cudaFree(n->y);
+  cudaFree(n->g);
+  n->y = n->g = nullptr;
+  n->cap = 0;
+  cudaError_t e = cudaSuccess;
+  for (auto*& p : n->h)
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p, sizeof(__nv_bfloat16) * C * (size_t)V);
+  for (auto*& p : n->gbuf)
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p, sizeof(__nv_bfloat16) * C * (size_t)V);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->y, sizeof(float) * (size_t)V);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->g, sizeof(float) * (size_t)V);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return TCA_ERR_ALLOC;
+  }
+  n->cap = V;
+  return TCA_OK;
+}
+
+tca_status get_dims(const int64_t* dims, Dims* d) {
+  for (int k = 0; k < 4; ++k)
+    if (dims[k] <= 0 || dims[k] > 65536) return TCA_ERR_INVALID_ARG;
+  d->D = (int)dims[0];
+  d->H = (int)dims[1];
+  d->W = (int)dims[2];
+  d->B = (int)dims[3];
+  d->V = dims[0] * dims[1] * dims[2] * dims[3];
+  if ((int64_t)d->D * d->H > (1 << 30) || d->V > ((int64_t)1 << 34)) return TCA_ERR_INVALID_ARG;
+  return TCA_OK;
+}
+
+int grid_for(const tca_net_s* n, int64_t V, int per_sm) {
+  const int64_t want = (V + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)n->num_sms * per_sm));
+}
+
+tca_status prep(tca_net_s* n, cudaStream_t s) {
+  prep_kernel<<<(T * C * C + 255) / 256, 256, 0, s>>>(n->params, n->dw);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+tca_status conv32(tca_net_s* n, const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
+                  const __nv_bfloat16* mask, __nv_bfloat16* out, const Dims& d, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(conv32to32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    cudaFuncSetAttribute(conv32to32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    attr = true;
+  }
+  const int grid = grid_for(n, d.V, 3);
+  if (mask) conv32to32_kernel<true><<<grid, kThreads, kConvSmem, s>>>(in, w, bias, mask, out, d);
+  else conv32to32_kernel<false><<<grid, kThreads, kConvSmem, s>>>(in, w, bias, nullptr, out, d);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+// Forward pass into n->h[0..2] and y (y = s Net(u / s) when scaled).
+tca_status forward(tca_net_s* n, const float* u, float* y, const Dims& d, bool scaled, cudaStream_t s) {
+  const int grid = grid_for(n, d.V, 8);
+  conv1to32_kernel<false><<<grid, kThreads, 0, s>>>(u, scaled ? n->scale : nullptr, DW(n, w1f), DW(n, b1), nullptr,
+                                                     n->h[0], d);
+  TCA_LAUNCH_CHECK();
+  TCA_TRY(conv32(n, n->h[0], DW(n, w2f), DW(n, b2), nullptr, n->h[1], d, s));
+  TCA_TRY(conv32(n, n->h[1], DW(n, w3f), DW(n, b3), nullptr, n->h[2], d, s));
+  conv32to1_kernel<<<grid, kThreads, 0, s>>>(n->h[2], DW(n, w4f), DW(n, b4), scaled ? n->scale : nullptr, y, d);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+template <int CG, int CX>
+tca_status wgrad(tca_net_s* n, const void* G, const void* X, const Dims& d, int co, int ci, int64_t w_off,
+                 int64_t b_off, cudaStream_t s) {
+  constexpr int combos = T * (CG == 1 ? 1 : CG / 4) * (CX == 1 ? 1 : CX / 4);
+  const int bx = (combos + 191) / 192;
+  const int rows = d.D * d.H;
+  const int want = std::max(1, std::min({kMaxChunks, rows, (n->num_sms * 4) / bx}));
+  const int rpc = (rows + want - 1) / want;
+  const int chunks = (rows + rpc - 1) / rpc;
+  dim3 grid(bx, chunks);
+  wgrad_kernel<CG, CX><<<grid, 192, 0, s>>>(G, X, n->partial, d, rpc);
+  TCA_LAUNCH_CHECK();
+  bgrad_kernel<CG><<<chunks, 256, 0, s>>>(G, n->bpartial, d, rpc);
+  TCA_LAUNCH_CHECK();
+  const int nk = T * co * ci + co;
+  reduce_grads_kernel<<<(nk + 255) / 256, 256, 0, s>>>(n->partial, n->bpartial, chunks, co, ci, n->grads, w_off,
+                                                       b_off);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t tca_net_param_count(void) { return kParams; }
+
+extern "C" tca_status tca_net_create(tca_net_t* out, const float* params, cudaStream_t s) {
+  if (!out || !params) return TCA_ERR_INVALID_ARG;
+  *out = nullptr;
+  tca_net_s* n = new tca_net_s();
+  tca_status st = net_alloc(n);
+  if (st == TCA_OK) st = tca_net_set_params(n, params, s);
+  if (st != TCA_OK) {
+    tca_net_destroy(n);
+    return st;
+  }
+  *out = n;
+  return TCA_OK;
+}
+
+extern "C" void tca_net_destroy(tca_net_t n) {
+  if (!n) return;
+  cudaFree(n->params);
+  cudaFree(n->grads);
+  cudaFree(n->adam_m);
+  cudaFree(n->adam_v);
+  cudaFree(n->dw);
+  for (auto* p : n->h) cudaFree(p);
+  for (auto* p : n->gbuf) cudaFree(p);
+  cudaFree(n->y);
+  cudaFree(n->g);
+  cudaFree(n->partial);
+  cudaFree(n->bpartial);
+  cudaFree(n->loss);
+  cudaFree(n->scale);
+  cudaFree(n->red.partials);
+  cudaFree(n->red.ticket);
+  delete n;
+}
+
+extern "C" tca_status tca_net_set_params(tca_net_t n, const float* params, cudaStream_t s) {
+  if (!n || !params) return TCA_ERR_INVALID_ARG;
+  TCA_CUDA_TRY(cudaMemcpyAsync(n->params, params, sizeof(float) * kParams, cudaMemcpyHostToDevice, s));
+  TCA_CUDA_TRY(cudaMemsetAsync(n->adam_m, 0, sizeof(float) * kParams, s));
+  TCA_CUDA_TRY(cudaMemsetAsync(n->adam_v, 0, sizeof(float) * kParams, s));
+  TCA_CUDA_TRY(cudaMemsetAsync(n->grads, 0, sizeof(float) * kParams, s));
+  n->adam_t = 0;
+  TCA_TRY(prep(n, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return TCA_OK;
+}
+
+extern "C" tca_status tca_net_get_params(tca_net_t n, float* params, cudaStream_t s) {
+  if (!n || !params) return TCA_ERR_INVALID_ARG;
+  TCA_CUDA_TRY(cudaMemcpyAsync(params, n->params, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return TCA_OK;
+}
+
+extern "C" tca_status tca_net_get_grads(tca_net_t n, float* grads, cudaStream_t s) {
+  if (!n || !grads) return TCA_ERR_INVALID_ARG;
+  TCA_CUDA_TRY(cudaMemcpyAsync(grads, n->grads, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return TCA_OK;
+}
+
+extern "C" tca_status tca_net_forward(tca_net_t n, const int64_t* dims, const float* u, float* y, cudaStream_t s) {
+  if (!n || !dims || !u || !y) return TCA_ERR_INVALID_ARG;
+  Dims d;
+  TCA_TRY(get_dims(dims, &d));
+  if (!is_device_ptr(u) || !is_device_ptr(y)) return TCA_ERR_UNSUPPORTED;
+  TCA_TRY(ensure_act(n, d.V));
+  return forward(n, u, y, d, false, s);
+}
+
+extern "C" tca_status tca_net_accumulate(tca_net_t n, const int64_t* dims, const float* u, const float* t,
+                                         cudaStream_t s) {
+  if (!n || !dims || !u || !t) return TCA_ERR_INVALID_ARG;
+  Dims d;
+  TCA_TRY(get_dims(dims, &d));
+  if (!is_device_ptr(u) || !is_device_ptr(t)) return TCA_ERR_UNSUPPORTED;
+  TCA_TRY(ensure_act(n, d.V));
+  TCA_TRY(forward(n, u, n->y, d, false, s));
+  loss_kernel<<<std::min<int64_t>((d.V + 255) / 256, 1024), 256, 0, s>>>(n->y, t, n->g, d, n->loss, n->red);
+  TCA_LAUNCH_CHECK();
+  // Layer 4: dW4 from g and h3; input gradient dh3 = conv(g, W4 flipped) masked by h3 > 0.
+  TCA_TRY((wgrad<1, C>(n, n->g, n->h[2], d, 1, C, kW4, kB4, s)));
+  const int grid = grid_for(n, d.V, 8);
+  conv1to32_kernel<true><<<grid, kThreads, 0, s>>>(n->g, nullptr, DW(n, w4b), nullptr, n->h[2], n->gbuf[0], d);
+  TCA_LAUNCH_CHECK();
+  // Layer 3: dW3 from dz3 = gbuf[0] and h2; dh2 = conv(dz3, W3^T flipped) masked by h2 > 0.
+  TCA_TRY((wgrad<C, C>(n, n->gbuf[0], n->h[1], d, C, C, kW3, kB3, s)));
+  TCA_TRY(conv32(n, n->gbuf[0], DW(n, w3b), nullptr, n->h[1], n->gbuf[1], d, s));
+  // Layer 2: dW2 from dz2 = gbuf[1] and h1; dh1 masked by h1 > 0.
+  TCA_TRY((wgrad<C, C>(n, n->gbuf[1], n->h[0], d, C, C, kW2, kB2, s)));
+  TCA_TRY(conv32(n, n->gbuf[1], DW(n, w2b), nullptr, n->h[0], n->gbuf[0], d, s));
+  // Layer 1: dW1 from dz1 = gbuf[0] and u.
+  TCA_TRY((wgrad<C, 1>(n, n->gbuf[0], u, d, C, 1, kW1, kB1, s)));
+  return TCA_OK;
+}
+
+extern "C" tca_status tca_net_take_loss(tca_net_t n, double* loss, cudaStream_t s) {
+  if (!n || !loss) return TCA_ERR_INVALID_ARG;
+  TCA_CUDA_TRY(cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaMemsetAsync(n->loss, 0, sizeof(double), s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return TCA_OK;
+}
+
+extern "C" tca_status tca_net_adam(tca_net_t n, float lr, float beta1, float beta2, float eps, float grad_scale,
+                                   cudaStream_t s) {
+  if (!n || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return TCA_ERR_INVALID_ARG;
+  n->adam_t += 1;
+  const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)n->adam_t));
+  const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)n->adam_t));
+  adam_kernel<<<(int)((kParams + 255) / 256), 256, 0, s>>>(n->params, n->grads, n->adam_m, n->adam_v, kParams, lr,
+                                                          beta1, beta2, eps, bc1, bc2, grad_scale);
+  TCA_LAUNCH_CHECK();
+  return prep(n, s);
+}
+
+// x0 = s Net(A^T b / s), s = RMS(A^T b), then CG from x0 (tca_solve with x0_given).
+extern "C" tca_status tca_solve_net(tca_plan_t plan, tca_net_t n, const void* b, void* x, const tca_solve_opts* opts,
+                                    tca_solve_info* info, cudaStream_t s) {
+  if (!plan || !n || !b || !x) return TCA_ERR_INVALID_ARG;
+  if (plan->prec == TCA_F64) return TCA_ERR_UNSUPPORTED;
+  if (plan->d != 4 && plan->d != 3) return TCA_ERR_UNSUPPORTED;
+  if (!is_device_ptr(b) || !is_device_ptr(x)) return TCA_ERR_UNSUPPORTED;
+  int64_t dims[4] = {plan->n[0], plan->n[1], plan->n[2], plan->d == 4 ? plan->n[3] : 1};
+  Dims d;
+  TCA_TRY(get_dims(dims, &d));
+  TCA_TRY(ensure_act(n, d.V));
+  // A^T b (FP32) into the net's output buffer, its RMS, then the network.
+  TCA_TRY(tca_apply_T(plan, b, n->y, s));
+  rms_kernel<<<std::min<int64_t>((d.V + 255) / 256, 1024), 256, 0, s>>>(n->y, d.V, n->scale, n->red);
+  TCA_LAUNCH_CHECK();
+  TCA_TRY(forward(n, n->y, (float*)x, d, true, s));
+  tca_solve_opts o = opts ? *opts : tca_solve_opts{};
+  if (!opts) {
+    o.rtol = 1e-6;
+    o.max_iter = 10000;
+  }
+  o.x0_given = 1;
+  return tca_solve(plan, b, x, &o, info, s);
+}

@@ -39,6 +39,7 @@ __all__ = [
     "instance_dense_3d",
     "instance_bspline",
     "instance_batched",
+    "net_init_params",
 ]
 
 
@@ -233,3 +234,22 @@ def instance_batched(index: int, base_seed: int = 100, lo: int = 24, hi: int = 9
     x_true = smooth_random_field(tuple(dims), 4.0, rng, dtype=np.float32)
     noise = 0.01 * rng.standard_normal(tuple(f.m for f in factors), dtype=np.float32)
     return Instance(tuple(dims), factors, x_true, noise, lam, seed)
+
+
+NET_LAYERS = ((1, 32), (32, 32), (32, 32), (32, 1))  # (c_in, c_out) of the 4 convolution layers
+
+
+def net_init_params(seed: int) -> np.ndarray:
+    """Packed FP32 initial parameters of the 4-layer 3x3x3 network.
+
+    Per layer: W[c_out][c_in][3][3][3] ~ N(0, 2 / (27 c_in)) (He-normal), the
+    last layer scaled by 0.1, then b[c_out] = 0.
+    """
+    rng = np.random.default_rng(seed)
+    parts = []
+    for li, (ci, co) in enumerate(NET_LAYERS):
+        w = rng.standard_normal((co, ci, 3, 3, 3)) * math.sqrt(2.0 / (27 * ci))
+        if li == len(NET_LAYERS) - 1:
+            w *= 0.1
+        parts += [w.ravel(), np.zeros(co)]
+    return np.concatenate(parts).astype(np.float32)

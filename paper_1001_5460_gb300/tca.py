@@ -83,6 +83,27 @@ _lib.tca_autotune.argtypes = [_vp, _vp]
 _lib.tca_autotune.restype = ctypes.c_int
 _lib.tca_autotuned_chunks.argtypes = [_vp]
 _lib.tca_autotuned_chunks.restype = ctypes.c_int
+_lib.tca_net_param_count.argtypes = []
+_lib.tca_net_param_count.restype = ctypes.c_int64
+_lib.tca_net_create.argtypes = [ctypes.POINTER(_vp), _vp, _vp]
+_lib.tca_net_create.restype = ctypes.c_int
+for _name in ("tca_net_set_params", "tca_net_get_params", "tca_net_get_grads"):
+    getattr(_lib, _name).argtypes = [_vp, _vp, _vp]
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.tca_net_forward.argtypes = [_vp, _i64p, _vp, _vp, _vp]
+_lib.tca_net_forward.restype = ctypes.c_int
+_lib.tca_net_accumulate.argtypes = [_vp, _i64p, _vp, _vp, _vp]
+_lib.tca_net_accumulate.restype = ctypes.c_int
+_lib.tca_net_take_loss.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.tca_net_take_loss.restype = ctypes.c_int
+_lib.tca_net_adam.argtypes = [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              _vp]
+_lib.tca_net_adam.restype = ctypes.c_int
+_lib.tca_solve_net.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info),
+                               _vp]
+_lib.tca_solve_net.restype = ctypes.c_int
+_lib.tca_net_destroy.argtypes = [_vp]
+_lib.tca_net_destroy.restype = None
 _lib.tca_rel_residual_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
 _lib.tca_rel_residual_noalloc.restype = ctypes.c_int
 _lib.tca_destroy.argtypes = [_vp]
@@ -159,7 +180,10 @@ def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
 
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_rel_residual_noalloc", "tca_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
+            "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
+            "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
+            "tca_net_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
 
 
 class Factor:
@@ -283,3 +307,87 @@ def solve_batched(plans, bs, xs, rtol: float = 1e-6, max_iter: int = 10000, x0_g
 def plan_from_instance(inst, precision="f32", reg_mask=None, stream=None) -> Plan:
     """Plan for a synthetic ``synth.Instance``."""
     return Plan(inst.shape, inst.factors, lam=inst.lam, reg_mask=reg_mask, precision=precision, stream=stream)
+
+
+def _dims4(shape) -> ctypes.Array:
+    shape = tuple(int(v) for v in shape)
+    if len(shape) == 3:
+        shape = shape + (1,)
+    if len(shape) != 4:
+        raise ValueError("network tensors are 3D or 4D")
+    return (ctypes.c_int64 * 4)(*shape)
+
+
+class Net:
+    """The 4-layer 3x3x3 convolutional network that supplies the CG initial guess."""
+
+    def __init__(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.param_count():
+            raise ValueError(f"expected {self.param_count()} parameters, got {p.size}")
+        h = _vp()
+        _check(_lib.tca_net_create(ctypes.byref(h), p.ctypes.data, _stream(stream)), "tca_net_create")
+        self._h = h
+
+    @staticmethod
+    def param_count() -> int:
+        return int(_lib.tca_net_param_count())
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.tca_net_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+    def params(self, stream=None) -> np.ndarray:
+        out = np.empty(self.param_count(), np.float32)
+        _check(_lib.tca_net_get_params(self._h, out.ctypes.data, _stream(stream)), "tca_net_get_params")
+        return out
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(_lib.tca_net_set_params(self._h, p.ctypes.data, _stream(stream)), "tca_net_set_params")
+
+    def grads(self, stream=None) -> np.ndarray:
+        out = np.empty(self.param_count(), np.float32)
+        _check(_lib.tca_net_get_grads(self._h, out.ctypes.data, _stream(stream)), "tca_net_get_grads")
+        return out
+
+    def forward(self, u, y, stream=None):
+        _check(_lib.tca_net_forward(self._h, _dims4(u.shape), _ptr(u), _ptr(y), _stream(stream)), "tca_net_forward")
+        return y
+
+    def accumulate(self, u, t, stream=None):
+        _check(_lib.tca_net_accumulate(self._h, _dims4(u.shape), _ptr(u), _ptr(t), _stream(stream)),
+               "tca_net_accumulate")
+
+    def take_loss(self, stream=None) -> float:
+        v = ctypes.c_double()
+        _check(_lib.tca_net_take_loss(self._h, ctypes.byref(v), _stream(stream)), "tca_net_take_loss")
+        return float(v.value)
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, grad_scale: float = 1.0,
+             stream=None):
+        _check(_lib.tca_net_adam(self._h, lr, beta1, beta2, eps, grad_scale, _stream(stream)), "tca_net_adam")
+
+    def solve(self, plan: "Plan", b, x, rtol: float = 1e-6, max_iter: int = 10000, check_every: int = 16,
+              inner_rtol: float = 0.0, max_refine: int = 0, stream=None, raise_on_error: bool = True,
+              profile: bool = False):
+        """tca_solve from the initial guess x0 = s Net(A^T b / s); returns (status, info dict)."""
+        opts = tca_solve_opts(float(rtol), int(max_iter), 1, float(inner_rtol), int(max_refine), int(check_every),
+                              1 if profile else 0)
+        info = tca_solve_info()
+        st = _lib.tca_solve_net(plan.handle, self._h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info),
+                                _stream(stream))
+        if raise_on_error:
+            _check(st, "tca_solve_net", ok=(OK, ERR_NOT_CONVERGED))
+        return st, _info_dict(info)

@@ -84,3 +84,32 @@ def test_product_path_has_no_cpu_fallback():
     for path in glob.glob(os.path.join(pkg, "*.py")) + glob.glob(os.path.join(pkg, "csrc", "*")):
         text = open(path).read()
         assert "import oracle" not in text and "from oracle" not in text, path
+
+
+def test_net_entry_points_check_arguments(tca):
+    from oracle import net_oracle as NO
+
+    assert tca.Net.param_count() == NO.n_params()
+    h = ctypes.c_void_p()
+    assert tca._lib.tca_net_create(ctypes.byref(h), None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_net_create(None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_net_forward(None, None, None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_net_accumulate(None, None, None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_net_adam(None, 1e-3, 0.9, 0.999, 1e-8, 1.0, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_solve_net(None, None, None, None, None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_solve_batched(0, None, None, None, None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_autotune(None, None) == tca.ERR_INVALID_ARG
+    tca._lib.tca_net_destroy(None)
+
+
+def test_net_init_params_layout():
+    from oracle import net_oracle as NO
+    from paper_1001_5460_gb300 import synth
+
+    p = synth.net_init_params(3)
+    assert p.dtype == np.float32 and p.size == NO.n_params()
+    layers = NO.unpack_params(p.astype(np.float64))
+    for li, ((w, b), (ci, co)) in enumerate(zip(layers, NO.LAYERS)):
+        assert w.shape == (co, ci, 3, 3, 3) and not b.any()
+        std = np.sqrt(2.0 / (27 * ci)) * (0.1 if li == 3 else 1.0)
+        assert abs(w.std() / std - 1.0) < 0.25
