@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
-    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense", "batched"],
+    ap.add_argument("--train-instances", type=int, default=100, help="learned case: training instances (64^3 x 4)")
+    ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
+    ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense", "batched", "learned"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -84,6 +87,9 @@ def run_case(args, local):
         return
     if args.case == "batched":
         run_batched(args, device)
+        return
+    if args.case == "learned":
+        run_learned(args, device)
         return
     inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, with_truth=False)
     plan = tca.plan_from_instance(inst, precision="f32")
@@ -184,6 +190,107 @@ def run_batched(args, device):
         "slowest_alone": [{"shape": list(insts[k].shape), "kind": insts[k].factors[0].kind,
                            "iters": seq_infos[k]["iters"], "ms": round(1e3 * seq_infos[k]["seconds"], 2)}
                           for k in slowest],
+    }), flush=True)
+
+
+TRAIN_SHAPE = (64, 64, 64, 4)
+
+
+def run_learned(args, device):
+    """Learned initial guess: train the network on (A^T b, x) pairs that the plain solver produces on
+    64x64x64x4 B-spline instances, then solve held-out 160x160x160x8 instances from x0 = s Net(A^T b / s)
+    and compare with plain CG from zero at the same true relative residual (1e-6)."""
+    import torch
+
+    from paper_1001_5460_gb300 import synth, tca
+
+    t_start = time.perf_counter()
+    rng = np.random.default_rng(77)
+    # Pool of smooth fields (unit RMS); each training right-hand side is A x + noise with a field
+    # from the pool, flipped along random modes, so that every pair is distinct.
+    pool = [torch.from_numpy(synth.smooth_random_field(TRAIN_SHAPE, 4.0, rng)).to(device) for _ in range(16)]
+    us, ts = [], []
+    gen_iters = 0
+    for k in range(args.train_instances):
+        inst = synth.instance_bspline(TRAIN_SHAPE, seed=5000 + k, with_truth=False)
+        plan = tca.plan_from_instance(inst)
+        b = torch.empty(inst.sample_shape, dtype=torch.float32, device=device)
+        u = torch.empty(TRAIN_SHAPE, dtype=torch.float32, device=device)
+        for j in range(args.rhs_per_instance):
+            xt = pool[int(rng.integers(len(pool)))]
+            dims = [d for d in range(3) if rng.random() < 0.5]
+            if dims:
+                xt = torch.flip(xt, dims)
+            plan.apply(xt.contiguous(), b)
+            b += 0.01 * torch.randn(b.shape, device=device)
+            plan.apply_T(b, u)
+            x = torch.empty_like(u)
+            _, info = plan.solve(b, x, rtol=RTOL)
+            gen_iters += info["iters"]
+            s = torch.sqrt(torch.mean(u.double() ** 2)).float()
+            us.append((u / s).contiguous())
+            ts.append((x / s).contiguous())
+        plan.close()
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_start
+    npairs = len(us)
+    net = tca.Net(synth.net_init_params(7))
+    steps = int(args.epochs * npairs)
+    order = rng.permutation(npairs)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(steps):
+        k = int(order[step % npairs])
+        net.accumulate(us[k], ts[k])
+        lr = 2e-3 * (0.5 * (1 + np.cos(np.pi * step / max(steps, 1))))  # cosine decay
+        net.adam(lr)
+        if step % 50 == 0 or step == steps - 1:
+            losses.append((step, net.take_loss()))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del us, ts
+    # Held-out evaluation at the full size.
+    evals = []
+    for seed in (9001, 9002):
+        inst = synth.instance_bspline(SHAPE, seed=seed, lam=LAM)
+        plan = tca.plan_from_instance(inst)
+        xt = torch.from_numpy(inst.x_true).to(device)
+        b = torch.empty(inst.sample_shape, dtype=torch.float32, device=device)
+        plan.apply(xt, b)
+        b += torch.from_numpy(inst.noise).to(device)
+        x = torch.empty(SHAPE, dtype=torch.float32, device=device)
+        for _ in range(2):  # warm-up: graphs, workspaces
+            plan.solve(b, x, rtol=RTOL)
+            net.solve(plan, b, x, rtol=RTOL)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        res = {}
+        for name, fn in (("plain", lambda: plan.solve(b, x, rtol=RTOL)), ("net", lambda: net.solve(plan, b, x, rtol=RTOL))):
+            e0.record()
+            for _ in range(args.steps):
+                _, info = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = {"ms": round(e0.elapsed_time(e1) / args.steps, 3), "iters": info["iters"],
+                         "rel_res_true": info["rel_res_true"]}
+        # network forward alone at this size
+        u = torch.empty(SHAPE, dtype=torch.float32, device=device)
+        y = torch.empty_like(u)
+        plan.apply_T(b, u)
+        net.forward(u, y)
+        e0.record()
+        for _ in range(args.steps):
+            net.forward(u, y)
+        e1.record()
+        torch.cuda.synchronize()
+        res["net_forward_ms"] = round(e0.elapsed_time(e1) / args.steps, 3)
+        evals.append({"seed": seed, **res})
+        plan.close()
+    print(json.dumps({
+        "case": "learned", "train_pairs": npairs, "train_shape": list(TRAIN_SHAPE), "gen_s": round(t_gen, 2),
+        "gen_iters_mean": round(gen_iters / max(npairs, 1), 1), "train_steps": steps,
+        "train_s": round(t_train, 2), "train_ms_per_step": round(1e3 * t_train / max(steps, 1), 3),
+        "loss": losses[:3] + losses[-3:], "eval_shape": list(SHAPE), "eval": evals,
     }), flush=True)
 
 

@@ -82,6 +82,13 @@ TCA_API tca_status tca_net_adam(tca_net_t net, float lr, float beta1, float beta
 TCA_API tca_status tca_solve_net(tca_plan_t plan, tca_net_t net, const void* b, void* x, const tca_solve_opts* opts,
                                  tca_solve_info* info, cudaStream_t stream);
 
+/* Run the 32 -> 32 channel layers (forward and input gradients) on the
+ * tensor cores (enable != 0, the default: tcgen05 implicit GEMM, BF16
+ * operands, FP32 accumulation in tensor memory) or on the CUDA cores (FP32
+ * FMA).  Both compute the same sums; the tensor-core path applies when the
+ * batch extent B is at most 24 and falls back to the CUDA cores otherwise. */
+TCA_API tca_status tca_net_use_tensor_cores(tca_net_t net, int enable);
+
 /* Free the network (NULL is ignored). */
 TCA_API void tca_net_destroy(tca_net_t net);
 

@@ -23,8 +23,6 @@
 
 namespace tca {
 
-extern __device__ int g_wait_timeout;
-
 namespace {
 
 constexpr int kM = 128;
@@ -60,7 +58,8 @@ struct TcGeom {
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(const float* __restrict__ x, float* __restrict__ y,
-                                                                 const float* __restrict__ a, TcGeom g) {
+                                                                 const float* __restrict__ a, TcGeom g,
+                                                                 int* __restrict__ timeout_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(const float* __
     asm volatile("tcgen05.fence::before_thread_sync;");
     if (__syncthreads_or(timed_out)) break;
   }
-  if (timed_out && tid == 0) atomicExch(&g_wait_timeout, 1);
+  if (timed_out && tid == 0 && timeout_flag) atomicExch(timeout_flag, 1);
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -273,7 +272,8 @@ tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, 
   }
   // One CTA per SM: its shared memory and TMEM columns leave room for nothing else of this kernel.
   const int64_t grid = std::min<int64_t>(g.tiles, (int64_t)tc_sm_count());
-  dense_tc_kernel<<<(unsigned)std::max<int64_t>(grid, 1), kTcThreads, bytes, s>>>(x, y, d.a32, g);
+  dense_tc_kernel<<<(unsigned)std::max<int64_t>(grid, 1), kTcThreads, bytes, s>>>(x, y, d.a32, g,
+                                                                                  wait_timeout_flag());
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }

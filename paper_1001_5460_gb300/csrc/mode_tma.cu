@@ -342,6 +342,15 @@ int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W) {
   return rb;
 }
 
+int* wait_timeout_flag() {
+  static int* addr = nullptr;
+  if (!addr) {
+    void* a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_wait_timeout) == cudaSuccess) addr = static_cast<int*>(a);
+  }
+  return addr;
+}
+
 tca_status read_wait_timeout(int* flag, bool reset) {
   TCA_CUDA_TRY(cudaMemcpyFromSymbol(flag, g_wait_timeout, sizeof(int)));
   if (reset && *flag) {

@@ -57,6 +57,13 @@ struct Derived {
   __align__(16) __nv_bfloat16 w3f[T * C * C];
   __align__(16) __nv_bfloat16 w2b[T * C * C];  // [t][o][i] = W2[o][i][26 - t]: input gradient of layer 2
   __align__(16) __nv_bfloat16 w3b[T * C * C];
+  // The same four 32 -> 32 weight sets in the tensor-core operand layout
+  // (canonical K-major, no swizzle): tap t, output channel o (N row),
+  // input channel i (K) at byte t 2048 + (i / 8) 512 + o 16 + (i % 8) 2.
+  __align__(16) __nv_bfloat16 w2f_tc[T * C * C];
+  __align__(16) __nv_bfloat16 w3f_tc[T * C * C];
+  __align__(16) __nv_bfloat16 w2b_tc[T * C * C];
+  __align__(16) __nv_bfloat16 w3b_tc[T * C * C];
 };
 
 // Address of a member of the device-resident Derived block.
@@ -268,6 +275,216 @@ __global__ void __launch_bounds__(kThreads) conv32to32_kernel(const __nv_bfloat1
   }
 }
 
+// ---- 32 -> 32 channels on the tensor cores -----------------------------------------
+// The same convolution as an implicit GEMM on tcgen05 (BF16 operands, FP32
+// accumulators in tensor memory).  A tile is 128 consecutive voxels of one
+// row (z, y) of the volume (the flattened (x, n) index); per tap (a, b, e)
+// the A operand is the input rows (z + a - 1, y + b - 1) shifted by (e - 1) B
+// voxels, K = 32 input channels, N = 32 output channels:
+//   D[r][o] += sum_i in[v_r + off t][i] W[t][o][i]      (27 taps x 2 MMAs of K = 16)
+// A CTA walks a column of tiles along y for fixed (z, segment): input strips
+// (128 + 2B voxels x 32 channels of one row (z', y')) stay in a 5-row ring in
+// shared memory, each new y loads the three strips of row y + 2 (cp.async
+// with zero fill at the volume's edges), so every input row is read about
+// once per (z', segment) column.  Strip layout: [channel chunk c (4)][voxel
+// s][16 bytes] - the canonical no-swizzle K-major layout (8 voxel rows x
+// 16 bytes per core matrix), so a tap's shift is just a start address.  Two
+// TMEM accumulators alternate: the epilogue of tile y - 1 (bias + ReLU or the
+// ReLU mask, bfloat16, 64 bytes per voxel) overlaps the MMAs of tile y.
+namespace tc {
+
+constexpr int kTile = 128;
+constexpr int kRing = 5;
+constexpr int kThr = 128;
+constexpr long long kWaitLimit = 1ll << 26;
+constexpr int kWBytes = T * C * C * 2;  // 55296
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+struct Args {
+  const __nv_bfloat16* in;
+  __nv_bfloat16* out;
+  const __nv_bfloat16* w;     // tensor-core layout, 27 x 2048 bytes
+  const float* bias;          // forward: bias + ReLU; null: mask mode
+  const __nv_bfloat16* mask;  // mask mode: out = acc * (mask > 0)
+  int D, H, W, B;
+  int L, segs, S, ychunk, ychunks;
+  int64_t items;
+};
+
+// Issue the three strips (z - 1 .. z + 1) of row yr for segment seg into ring slot.
+__device__ __forceinline__ void load_row(const Args& g, unsigned char* ring, int z, int yr, int seg, int tid) {
+  unsigned char* slot = ring + (size_t)(((yr % kRing) + kRing) % kRing) * 3 * 4 * g.S * 16;
+  const int n16 = 3 * 4 * g.S;
+  for (int idx = tid; idx < n16; idx += kThr) {
+    const int c = idx & 3;
+    const int s = (idx >> 2) % g.S;
+    const int dz = idx / (4 * g.S);
+    const int zz = z + dz - 1;
+    const int vl = seg * kTile - g.B + s;
+    const bool ok = zz >= 0 && zz < g.D && yr >= 0 && yr < g.H && vl >= 0 && vl < g.L;
+    const __nv_bfloat16* src = ok ? g.in + (((int64_t)zz * g.H + yr) * g.L + vl) * C + c * 8 : g.in;
+    unsigned char* dst = slot + ((size_t)dz * 4 + c) * g.S * 16 + (size_t)s * 16;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ bool wait_bar(unsigned bar, int parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  unsigned char* sw = base;                       // weights
+  unsigned char* ring = base + kWBytes;           // kRing x 3 x 4 x S x 16
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kRing * 3 * 4 * g.S * 16);
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2);
+  float* sbias = reinterpret_cast<float*>(tslot + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int k = tid; k < kWBytes / 16; k += kThr)
+    reinterpret_cast<uint4*>(sw)[k] = __ldg(reinterpret_cast<const uint4*>(g.w) + k);
+  if (tid < C) sbias[tid] = g.bias ? g.bias[tid] : 0.f;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const unsigned tmem = *tslot;
+  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(C >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
+  const unsigned sw_a = su32(sw), ring_a = su32(ring);
+  const unsigned strip_bytes = 4u * g.S * 16u;
+  int parity[2] = {0, 0};
+  bool timed_out = false;
+
+  for (int64_t item = blockIdx.x; item < g.items && !timed_out; item += gridDim.x) {
+    const int yc = (int)(item % g.ychunks);
+    const int seg = (int)((item / g.ychunks) % g.segs);
+    const int z = (int)(item / ((int64_t)g.ychunks * g.segs));
+    const int y0 = yc * g.ychunk, y1 = min(g.H, y0 + g.ychunk);
+    // Prologue: rows y0 - 1 .. y0 + 2; iteration y issues row y + 3.
+    for (int r = y0 - 1; r <= y0 + 2; ++r) load_row(g, ring, z, r, seg, tid);
+    for (int y = y0; y <= y1; ++y) {
+      if (y < y1) {
+        // Rows <= y + 1 have landed; row y + 2 (the newest group) may still be in flight.
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+          const unsigned dtm = tmem + (unsigned)((y & 1) * C);
+          int first = 1;
+          for (int t = 0; t < T; ++t) {
+            const int a = t / 9, b = (t / 3) % 3, e = t % 3;
+            const unsigned strip = ring_a + (unsigned)((((y + b - 1) % kRing + kRing) % kRing) * 3 + a) * strip_bytes;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint64_t ad = desc(strip + (unsigned)(2 * ks) * g.S * 16u + (unsigned)(e * g.B) * 16u,
+                                       (unsigned)g.S * 16u, 128u);
+              const uint64_t bd = desc(sw_a + (unsigned)t * 2048u + (unsigned)(2 * ks) * 512u, 512u, 128u);
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0u : 1u));
+              first = 0;
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(&bars[y & 1])));
+        }
+      }
+      if (y > y0) {
+        // Epilogue of tile y - 1.
+        const int yp = y - 1, sl = yp & 1;
+        const bool ok = __all_sync(0xffffffffu, wait_bar(su32(&bars[sl]), parity[sl]));
+        parity[sl] ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!ok) {
+          timed_out = true;
+        } else {
+          const int row = 32 * warp + lane;
+          const int vl = seg * kTile + row;
+          unsigned v[32];
+          const unsigned taddr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(sl * C);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          if (vl < g.L) {
+            const int64_t vox = ((int64_t)z * g.H + yp) * g.L + vl;
+            float acc[C];
+            if (g.mask) {
+              float h[C];
+              load32(g.mask + vox * C, h);
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] = h[c] > 0.f ? __uint_as_float(v[c]) : 0.f;
+            } else {
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] = fmaxf(__uint_as_float(v[c]) + sbias[c], 0.f);
+            }
+            store32(g.out + vox * C, acc);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      }
+      // Ring slot of row y - 2 is free for row y + 3: tile y - 1's MMAs (the
+      // last to read it) completed in the epilogue above, and at y0 the
+      // previous item's MMAs all completed before its end.
+      if (y < y1) load_row(g, ring, z, y + 3, seg, tid);
+      if (__syncthreads_or(timed_out)) {
+        timed_out = true;
+        break;
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+  }
+  if (timed_out && tid == 0 && timeout_flag) atomicExch(timeout_flag, 1);
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+  }
+}
+
+size_t smem_bytes(int S) { return 128 + (size_t)kWBytes + (size_t)kRing * 3 * 4 * S * 16 + 16 + 16 + C * 4; }
+
+}  // namespace tc
+
 // ---- loss ----------------------------------------------------------------------
 // g = bf16(2 (y - t) / V);  loss += sum (y - t)^2 / V  (last block adds to *loss).
 __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
@@ -422,6 +639,12 @@ __global__ void prep_kernel(const float* __restrict__ p, Derived* __restrict__ d
     // input gradient: input channel i' = o of the layer, output o' = i, flipped tap
     dw->w2b[k] = __float2bfloat16_rn(p[kW2 + ((int64_t)i * C + o) * T + (T - 1 - t)]);
     dw->w3b[k] = __float2bfloat16_rn(p[kW3 + ((int64_t)i * C + o) * T + (T - 1 - t)]);
+    // tensor-core layout: element index of (t, N row o, K col i)
+    const int tc = t * C * C + (i / 8) * (8 * C) + o * 8 + (i % 8);
+    dw->w2f_tc[tc] = dw->w2f[k];
+    dw->w3f_tc[tc] = dw->w3f[k];
+    dw->w2b_tc[tc] = dw->w2b[k];
+    dw->w3b_tc[tc] = dw->w3b[k];
   }
 }
 
@@ -464,6 +687,7 @@ struct tca_net_s {
   float* scale = nullptr;     // device scalar (RMS of the input)
   Reduce red;
   int num_sms = 0;
+  bool force_cuda_cores = false;  // 32 -> 32 layers on the CUDA cores (tests of both paths)
 };
 
 namespace {
@@ -545,8 +769,59 @@ tca_status prep(tca_net_s* n, cudaStream_t s) {
   return TCA_OK;
 }
 
-tca_status conv32(tca_net_s* n, const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
-                  const __nv_bfloat16* mask, __nv_bfloat16* out, const Dims& d, cudaStream_t s) {
+// Work split of the tensor-core convolution: columns (z, segment) of tiles,
+// cut along y into chunks so that the persistent CTAs get balanced waves
+// (each chunk also reloads three halo rows).
+tc::Args tc_geometry(const tca_net_s* n, const Dims& d) {
+  tc::Args g{};
+  g.D = d.D;
+  g.H = d.H;
+  g.W = d.W;
+  g.B = d.B;
+  g.L = d.W * d.B;
+  g.segs = (g.L + tc::kTile - 1) / tc::kTile;
+  g.S = tc::kTile + 2 * d.B;
+  const int64_t cols = (int64_t)d.D * g.segs;
+  const int sms = std::max(1, n->num_sms);
+  int best = d.H;
+  double best_cost = 1e300;
+  for (int nc = 1; nc <= d.H; ++nc) {
+    const int ych = (d.H + nc - 1) / nc;
+    const int64_t items = cols * ((d.H + ych - 1) / ych);
+    const double cost = (double)((items + sms - 1) / sms) * (ych + 3);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = ych;
+    }
+  }
+  g.ychunk = best;
+  g.ychunks = (d.H + best - 1) / best;
+  g.items = cols * g.ychunks;
+  return g;
+}
+
+bool tc_supported(const Dims& d) { return d.B <= 24; }
+
+tca_status conv32(tca_net_s* n, const __nv_bfloat16* in, const __nv_bfloat16* w, const __nv_bfloat16* w_tc,
+                  const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out, const Dims& d, cudaStream_t s) {
+  if (w_tc && tc_supported(d) && !n->force_cuda_cores) {
+    tc::Args g = tc_geometry(n, d);
+    g.in = in;
+    g.out = out;
+    g.w = w_tc;
+    g.bias = mask ? nullptr : bias;
+    g.mask = mask;
+    const size_t smem = tc::smem_bytes(g.S);
+    static bool tc_attr = false;
+    if (!tc_attr) {
+      cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      tc_attr = true;
+    }
+    const int grid = (int)std::min<int64_t>(g.items, (int64_t)std::max(1, n->num_sms));
+    tc::conv_tc_kernel<<<grid, tc::kThr, smem, s>>>(g, wait_timeout_flag());
+    TCA_LAUNCH_CHECK();
+    return TCA_OK;
+  }
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(conv32to32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
@@ -566,8 +841,8 @@ tca_status forward(tca_net_s* n, const float* u, float* y, const Dims& d, bool s
   conv1to32_kernel<false><<<grid, kThreads, 0, s>>>(u, scaled ? n->scale : nullptr, DW(n, w1f), DW(n, b1), nullptr,
                                                      n->h[0], d);
   TCA_LAUNCH_CHECK();
-  TCA_TRY(conv32(n, n->h[0], DW(n, w2f), DW(n, b2), nullptr, n->h[1], d, s));
-  TCA_TRY(conv32(n, n->h[1], DW(n, w3f), DW(n, b3), nullptr, n->h[2], d, s));
+  TCA_TRY(conv32(n, n->h[0], DW(n, w2f), DW(n, w2f_tc), DW(n, b2), nullptr, n->h[1], d, s));
+  TCA_TRY(conv32(n, n->h[1], DW(n, w3f), DW(n, w3f_tc), DW(n, b3), nullptr, n->h[2], d, s));
   conv32to1_kernel<<<grid, kThreads, 0, s>>>(n->h[2], DW(n, w4f), DW(n, b4), scaled ? n->scale : nullptr, y, d);
   TCA_LAUNCH_CHECK();
   return TCA_OK;
@@ -598,9 +873,16 @@ tca_status wgrad(tca_net_s* n, const void* G, const void* X, const Dims& d, int 
 
 extern "C" int64_t tca_net_param_count(void) { return kParams; }
 
+extern "C" tca_status tca_net_use_tensor_cores(tca_net_t n, int enable) {
+  if (!n) return TCA_ERR_INVALID_ARG;
+  n->force_cuda_cores = enable == 0;
+  return TCA_OK;
+}
+
 extern "C" tca_status tca_net_create(tca_net_t* out, const float* params, cudaStream_t s) {
   if (!out || !params) return TCA_ERR_INVALID_ARG;
   *out = nullptr;
+  (void)wait_timeout_flag();
   tca_net_s* n = new tca_net_s();
   tca_status st = net_alloc(n);
   if (st == TCA_OK) st = tca_net_set_params(n, params, s);
@@ -684,10 +966,10 @@ extern "C" tca_status tca_net_accumulate(tca_net_t n, const int64_t* dims, const
   TCA_LAUNCH_CHECK();
   // Layer 3: dW3 from dz3 = gbuf[0] and h2; dh2 = conv(dz3, W3^T flipped) masked by h2 > 0.
   TCA_TRY((wgrad<C, C>(n, n->gbuf[0], n->h[1], d, C, C, kW3, kB3, s)));
-  TCA_TRY(conv32(n, n->gbuf[0], DW(n, w3b), nullptr, n->h[1], n->gbuf[1], d, s));
+  TCA_TRY(conv32(n, n->gbuf[0], DW(n, w3b), DW(n, w3b_tc), nullptr, n->h[1], n->gbuf[1], d, s));
   // Layer 2: dW2 from dz2 = gbuf[1] and h1; dh1 masked by h1 > 0.
   TCA_TRY((wgrad<C, C>(n, n->gbuf[1], n->h[0], d, C, C, kW2, kB2, s)));
-  TCA_TRY(conv32(n, n->gbuf[1], DW(n, w2b), nullptr, n->h[0], n->gbuf[0], d, s));
+  TCA_TRY(conv32(n, n->gbuf[1], DW(n, w2b), DW(n, w2b_tc), nullptr, n->h[0], n->gbuf[0], d, s));
   // Layer 1: dW1 from dz1 = gbuf[0] and u.
   TCA_TRY((wgrad<C, 1>(n, n->gbuf[0], u, d, C, 1, kW1, kB1, s)));
   return TCA_OK;

@@ -364,6 +364,7 @@ extern "C" tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, con
   const uint32_t mask = reg ? reg->reg_mode_mask : 0u;
 
   static std::atomic<uint64_t> generations{0};
+  (void)wait_timeout_flag();  // resolve the flag's device address outside any stream capture
   tca_plan_s* p = new tca_plan_s();
   p->generation = ++generations;
   p->d = order;

@@ -220,6 +220,8 @@ int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W);
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
                            cudaStream_t s);
 tca_status read_wait_timeout(int* flag, bool reset);
+// Device address of the wait-timeout flag (for kernels in other translation units).
+int* wait_timeout_flag();
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);

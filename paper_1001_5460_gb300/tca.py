@@ -102,6 +102,8 @@ _lib.tca_net_adam.restype = ctypes.c_int
 _lib.tca_solve_net.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info),
                                _vp]
 _lib.tca_solve_net.restype = ctypes.c_int
+_lib.tca_net_use_tensor_cores.argtypes = [_vp, ctypes.c_int]
+_lib.tca_net_use_tensor_cores.restype = ctypes.c_int
 _lib.tca_net_destroy.argtypes = [_vp]
 _lib.tca_net_destroy.restype = None
 _lib.tca_rel_residual_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
@@ -183,7 +185,7 @@ def exported_symbols() -> list[str]:
             "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
-            "tca_net_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
+            "tca_net_use_tensor_cores", "tca_net_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
 
 
 class Factor:
@@ -347,6 +349,9 @@ class Net:
             self.close()
         except Exception:  # pragma: no cover - interpreter shutdown
             pass
+
+    def use_tensor_cores(self, enable: bool = True):
+        _check(_lib.tca_net_use_tensor_cores(self._h, 1 if enable else 0), "tca_net_use_tensor_cores")
 
     def params(self, stream=None) -> np.ndarray:
         out = np.empty(self.param_count(), np.float32)
