@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--train-instances", type=int, default=100, help="learned case: training instances (64^3 x 4)")
     ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
     ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
-    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense", "batched", "learned"],
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense", "batched", "learned", "netfwd"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -90,6 +90,26 @@ def run_case(args, local):
         return
     if args.case == "learned":
         run_learned(args, device)
+        return
+    if args.case == "netfwd":
+        # The network's forward pass alone on a full-size tensor (random weights and input).
+        shape = (64, 64, 64, 8) if args.small else SHAPE
+        net = tca.Net(synth.net_init_params(1))
+        u = torch.randn(shape, dtype=torch.float32, device=device)
+        y = torch.empty_like(u)
+        for _ in range(args.warmup):
+            net.forward(u, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            net.forward(u, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        flops = 2 * u.numel() * 27 * (32 + 32 * 32 * 2 + 32)
+        print(json.dumps({"case": "netfwd", "shape": list(shape), "ms": round(ms, 4),
+                          "tflops": round(flops / ms / 1e9, 2)}), flush=True)
         return
     inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, with_truth=False)
     plan = tca.plan_from_instance(inst, precision="f32")
