@@ -70,11 +70,14 @@ typedef enum {
 } tca_status;
 
 /* Arithmetic of a plan.  TCA_F64: double data, double arithmetic.  TCA_F32:
- * float data and arithmetic, inner products accumulated to double.  The _IR
- * forms keep float data at the boundary; the inner CG runs with reduced
- * precision operands (bf16 vector storage, or tf32 tensor-core products for
- * dense factors) and iterative refinement restores the accuracy from an FP64
- * residual. */
+ * float data and arithmetic, inner products accumulated to double (dense
+ * factors: 3xTF32 tensor-core products, about FP32 accuracy).  The _IR forms
+ * keep float data at the boundary and solve by iterative refinement: an
+ * outer loop on the FP64-accurate (double-float) residual and an inner CG to
+ * a loose tolerance with reduced-precision operators - plain TF32
+ * tensor-core products for dense factors (both _IR forms in this version);
+ * banded factors run the inner CG in FP32 (bf16 vector storage is not
+ * implemented yet). */
 typedef enum { TCA_F64 = 0, TCA_F32 = 1, TCA_BF16_IR = 2, TCA_TF32_IR = 3 } tca_precision;
 
 typedef enum {
