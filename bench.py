@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
+    ap.add_argument("--shape", default=None, help="sweep cases: tensor shape n1,n2,n3,n4 (profiling runs)")
     ap.add_argument("--train-instances", type=int, default=100, help="learned case: training instances (64^3 x 4)")
     ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
     ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
@@ -111,9 +112,10 @@ def run_case(args, local):
         print(json.dumps({"case": "netfwd", "shape": list(shape), "ms": round(ms, 4),
                           "tflops": round(flops / ms / 1e9, 2)}), flush=True)
         return
-    inst = synth.instance_bspline(SHAPE, seed=SEED, lam=LAM, with_truth=False)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else SHAPE
+    inst = synth.instance_bspline(shape, seed=SEED, lam=LAM, with_truth=False)
     plan = tca.plan_from_instance(inst, precision="f32")
-    x = torch.randn(SHAPE, dtype=torch.float32, device=device)
+    x = torch.randn(shape, dtype=torch.float32, device=device)
     N = x.numel()
     if args.case == "cgsweep":
         # A few CG iterations on random data: the CG-mode fused sweep in its solve context.
@@ -128,10 +130,10 @@ def run_case(args, local):
         fn, nbytes = (lambda: plan.apply_normal(x, y)), 2 * N * 4
     elif args.case == "gram":
         y = torch.empty_like(x)
-        fn, nbytes = (lambda: plan.apply_mode(0, tca.OP_GRAM, SHAPE, x, y)), 2 * N * 4
+        fn, nbytes = (lambda: plan.apply_mode(0, tca.OP_GRAM, shape, x, y)), 2 * N * 4
     else:
-        y = torch.empty((inst.factors[0].m,) + SHAPE[1:], dtype=torch.float32, device=device)
-        fn, nbytes = (lambda: plan.apply_mode(0, tca.OP_FACTOR, SHAPE, x, y)), (N + y.numel()) * 4
+        y = torch.empty((inst.factors[0].m,) + shape[1:], dtype=torch.float32, device=device)
+        fn, nbytes = (lambda: plan.apply_mode(0, tca.OP_FACTOR, shape, x, y)), (N + y.numel()) * 4
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()

@@ -559,6 +559,454 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised variant for n4 = 8 (the 4D workloads): the same sweep with
+// the work of a plane split between two warp groups that run one plane apart.
+//   loader/in-plane warps (A, 8 warps): copy the halo tiles of r and p_old
+//     (cp.async, 3 stages), form p = r + beta p_old, apply G_3, G_4 along the
+//     rows of the halo tile (S1) and lambda (L_3 + L_4) on the core rows (SL);
+//   column/ring warps (B, 8 warps): G_2 and lambda L_2 down the columns, the
+//     scatter into the 7-slot register ring along mode 1, the outputs q and
+//     p_new and the partial <p, q>.
+// A hands plane j to B through the double-buffered P / S1 / SL tiles and two
+// pairs of named barriers (FULL: A -> B, EMPTY: B -> A), so A's in-plane work
+// on plane j + 1 overlaps B's column and ring work on plane j.  The groups
+// rebalance the register file (setmaxnreg): only B holds the ring.
+namespace ws {
+
+constexpr int NA = 256, NB = 256, NT = NA + NB;
+constexpr int REG_A = 104, REG_B = 152;  // 256 x 104 + 256 x 152 = 65536 = 512 x 128 at launch
+constexpr int BAR_A = 1, BAR_FULL = 2, BAR_EMPTY = 4;
+
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <bool CG>
+__global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
+  constexpr int N4 = 8, T2 = 16, T3 = 16, T3P = 2, STAGES = 3;
+  using C = Cfg<N4, T2, T3, T3P, NB, STAGES, true>;  // smem layout of the CG configuration (P tiles, ring)
+  constexpr int H2 = C::H2, ROW = C::ROW, ROW1 = C::ROW1, P = C::P;
+  constexpr int NIN = CG ? 2 : 1;
+  extern __shared__ __align__(16) float sm[];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+
+  if constexpr (CG) {
+    if (cg_done(a.scal)) return;
+  }
+  const float beta = CG ? (float)a.scal->beta : 0.f;
+
+  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const int bid = blockIdx.x;
+  const int chunk_id = bid % a.nchunks;
+  const int tile = bid / a.nchunks;
+  const int t3i = tile % a.tiles3, t2i = tile / a.tiles3;
+  const int i2_0 = t2i * T2, i3_0 = t3i * T3;
+  const int c0 = chunk_id * a.chunk;
+  const int c1 = min(n1, c0 + a.chunk);
+  const int jb = max(0, c0 - kGramHalf);
+  const int je = min(n1, c1 + kGramHalf);
+  const int nplanes = je - jb;
+
+  float* s_in = sm + C::OFF_IN;
+  float* s_ring = sm + C::OFF_RING;
+  float* g3s = sm + C::OFF_G3;
+  float* l3s = sm + C::OFF_L3;
+  float* g4s = sm + C::OFF_G4;
+  float* l4s = sm + C::OFF_L4;
+  float* g2s = sm + C::OFF_G2;
+  float* l2s = sm + C::OFF_L2;
+  double* s_red = reinterpret_cast<double*>(sm + C::OFF_RED);
+
+  for (int t = tid; t < T3 * 8; t += NT) {
+    const int r = t >> 3, e = t & 7, i3 = i3_0 + r;
+    g3s[t] = (i3 < n3 && e < 7) ? a.g[2][(int64_t)i3 * 7 + e] : 0.f;
+    l3s[t] = (i3 < n3 && e < 5) ? a.l[2][(int64_t)i3 * 5 + e] : 0.f;
+  }
+  for (int t = tid; t < 7 * T2; t += NT) {
+    const int e = t / T2, r = t % T2, i2 = i2_0 + r;
+    g2s[t] = i2 < n2 ? a.g[1][(int64_t)i2 * 7 + e] : 0.f;
+    if (e < 5) l2s[t] = i2 < n2 ? a.l[1][(int64_t)i2 * 5 + e] : 0.f;
+  }
+  for (int t = tid; t < 7 * N4; t += NT) {
+    const int e = t / N4, i4 = t % N4;
+    g4s[t] = a.g[3][i4 * 7 + e];
+    if (e < 5) l4s[t] = a.l[3][i4 * 5 + e];
+  }
+  __syncthreads();
+
+  const int64_t plane = (int64_t)n2 * n3 * N4;
+  double dot = 0.0;
+
+  if (warp < NA / 32) {
+    // ======================= A: loads, p, stage A =======================
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_A));
+    constexpr int ELEMS = H2 * C::H3 * 2;  // 16-byte copies per tensor and plane
+    constexpr int NCP = (ELEMS + NA - 1) / NA;
+    int cp_dst[NCP], cp_src[NCP];
+#pragma unroll
+    for (int i = 0; i < NCP; ++i) {
+      const int t = tid + i * NA;
+      cp_dst[i] = -1;
+      cp_src[i] = -1;
+      if (t < ELEMS) {
+        const int v = t & 1, rc = t >> 1;
+        const int cc = rc % C::H3, rr = rc / C::H3;
+        const int i2 = i2_0 - 3 + rr, i3 = i3_0 - 3 + cc;
+        const bool ok = (unsigned)i2 < (unsigned)n2 && (unsigned)i3 < (unsigned)n3;
+        cp_dst[i] = rr * ROW + cc * N4 + 4 * v;
+        cp_src[i] = ok ? (i2 * n3 + i3) * N4 + 4 * v : -1;
+      }
+    }
+    auto issue = [&](int jj, int buf) {
+#pragma unroll
+      for (int src_i = 0; src_i < NIN; ++src_i) {
+        const float* g = (CG && src_i == 0) ? a.r : a.pold;
+        float* dst = s_in + (buf * 2 + src_i) * C::TILE;
+        const float* gp = g + (int64_t)jj * plane;
+#pragma unroll
+        for (int i = 0; i < NCP; ++i) {
+          if (cp_dst[i] < 0) continue;
+          const bool ok = cp_src[i] >= 0;
+          cp_async16(dst + cp_dst[i], ok ? gp + cp_src[i] : g, ok);
+        }
+      }
+    };
+#pragma unroll 1
+    for (int s = 0; s < STAGES - 1; ++s) {
+      if (jb + s < je) issue(jb + s, s);
+      cp_async_commit();
+    }
+#pragma unroll 1
+    for (int it = 0; it < nplanes; ++it) {
+      const int j = jb + it;
+      const int par = it & 1;
+      const int buf = it % STAGES;
+      cp_async_wait<STAGES - 2>();
+      bar_sync(BAR_A, NA);  // plane j landed for every A thread; all are done with plane j - 1's stage
+      {
+        const int jn = j + STAGES - 1;
+        if (jn < je) issue(jn, (it + STAGES - 1) % STAGES);
+        cp_async_commit();
+      }
+      if (it >= 2) bar_sync(BAR_EMPTY + par, NT);  // B is done with the buffers of plane j - 2
+      float* pdst = sm + C::OFF_P + par * C::TILE;
+      {
+        const float4* pp = reinterpret_cast<const float4*>(s_in + (buf * 2 + (CG ? 1 : 0)) * C::TILE);
+        float4* out = reinterpret_cast<float4*>(pdst);
+        if constexpr (CG) {
+          const float4* rr = reinterpret_cast<const float4*>(s_in + (buf * 2 + 0) * C::TILE);
+          for (int t = tid; t < C::TILE / 4; t += NA) {
+            const float4 x = rr[t], y = pp[t];
+            out[t] = make_float4(fmaf(beta, y.x, x.x), fmaf(beta, y.y, x.y), fmaf(beta, y.z, x.z),
+                                 fmaf(beta, y.w, x.w));
+          }
+        } else {
+          for (int t = tid; t < C::TILE / 4; t += NA) out[t] = pp[t];
+        }
+      }
+      bar_sync(BAR_A, NA);
+      const float* src = pdst;
+      float* s_s1 = sm + C::OFF_S1 + par * C::S1N;
+      float* s_sl = sm + C::OFF_SL + par * C::SLN;
+      // ---- stage A (one halo row, two columns, eight lanes per thread) ----
+      for (int slot = tid; slot < H2 * C::NBQ; slot += NA) {
+        const int ar = slot % H2;
+        const int bq = slot / H2;
+        const int b0 = bq * T3P;
+        constexpr int NV = 4;
+        float2 v[T3P + 6][NV];
+        const float* rowp = src + ar * ROW + b0 * N4;
+#pragma unroll
+        for (int t = 0; t < T3P + 6; ++t) {
+          const float4 lo = reinterpret_cast<const float4*>(rowp + t * N4)[0];
+          const float4 hi = reinterpret_cast<const float4*>(rowp + t * N4)[1];
+          v[t][0] = make_float2(lo.x, lo.y); v[t][1] = make_float2(lo.z, lo.w);
+          v[t][2] = make_float2(hi.x, hi.y); v[t][3] = make_float2(hi.z, hi.w);
+        }
+        float2 u[T3P][NV];
+#pragma unroll
+        for (int t = 0; t < T3P; ++t) {
+          const float4 ga = *reinterpret_cast<const float4*>(g3s + (b0 + t) * 8);
+          const float4 gb = *reinterpret_cast<const float4*>(g3s + (b0 + t) * 8 + 4);
+          const float gc[7] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z};
+#pragma unroll
+          for (int m = 0; m < NV; ++m) {
+            float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int e = 0; e < 7; ++e) s2 = ffma2(bc2(gc[e]), v[t + e][m], s2);
+            u[t][m] = s2;
+          }
+        }
+        float2 o[T3P][NV];
+        {
+          float2 od[T3P][NV + 1];
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) {
+            od[t][0] = make_float2(0.f, u[t][0].x);
+#pragma unroll
+            for (int k = 1; k < NV; ++k) od[t][k] = make_float2(u[t][k - 1].y, u[t][k].x);
+            od[t][NV] = make_float2(u[t][NV - 1].y, 0.f);
+#pragma unroll
+            for (int m = 0; m < NV; ++m) o[t][m] = make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int mm = 0; mm < NV / 2; ++mm) {
+#pragma unroll
+            for (int e = 0; e < 7; ++e) {
+              const int d = e - 3;
+              const float4 c4 = *reinterpret_cast<const float4*>(g4s + e * N4 + 4 * mm);
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                const int m = 2 * mm + hh;
+                const float2 cf = hh ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+#pragma unroll
+                for (int t = 0; t < T3P; ++t) {
+                  if ((d & 1) == 0) {
+                    const int pi = m + d / 2;
+                    if (pi >= 0 && pi < NV) o[t][m] = ffma2(cf, u[t][pi], o[t][m]);
+                  } else {
+                    const int pi = m + (d + 1) / 2;
+                    if (pi >= 0 && pi <= NV) o[t][m] = ffma2(cf, od[t][pi], o[t][m]);
+                  }
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < T3P; ++t) {
+          float* dst = s_s1 + ar * ROW1 + (b0 + t) * N4;
+          reinterpret_cast<float4*>(dst)[0] = make_float4(o[t][0].x, o[t][0].y, o[t][1].x, o[t][1].y);
+          reinterpret_cast<float4*>(dst)[1] = make_float4(o[t][2].x, o[t][2].y, o[t][3].x, o[t][3].y);
+        }
+        if (ar >= 3 && ar < 3 + T2) {
+          float2 lin[T3P][NV];
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) {
+            const float4 la = *reinterpret_cast<const float4*>(l3s + (b0 + t) * 8);
+            const float lc[5] = {la.x, la.y, la.z, la.w, l3s[(b0 + t) * 8 + 4]};
+#pragma unroll
+            for (int m = 0; m < NV; ++m) {
+              float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int e = 0; e < 5; ++e) s2 = ffma2(bc2(lc[e]), v[t + 1 + e][m], s2);
+              lin[t][m] = s2;
+            }
+          }
+          float2 od[T3P][NV + 1];
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) {
+            od[t][0] = make_float2(0.f, v[t + 3][0].x);
+#pragma unroll
+            for (int k = 1; k < NV; ++k) od[t][k] = make_float2(v[t + 3][k - 1].y, v[t + 3][k].x);
+            od[t][NV] = make_float2(v[t + 3][NV - 1].y, 0.f);
+          }
+#pragma unroll
+          for (int mm = 0; mm < NV / 2; ++mm) {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+              const int d = e - 2;
+              const float4 c4 = *reinterpret_cast<const float4*>(l4s + e * N4 + 4 * mm);
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                const int m = 2 * mm + hh;
+                const float2 cf = hh ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+#pragma unroll
+                for (int t = 0; t < T3P; ++t) {
+                  if ((d & 1) == 0) {
+                    const int pi = m + d / 2;
+                    if (pi >= 0 && pi < NV) lin[t][m] = ffma2(cf, v[t + 3][pi], lin[t][m]);
+                  } else {
+                    const int pi = m + (d + 1) / 2;
+                    if (pi >= 0 && pi <= NV) lin[t][m] = ffma2(cf, od[t][pi], lin[t][m]);
+                  }
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < T3P; ++t) {
+            float* dst = s_sl + (ar - 3) * ROW1 + (b0 + t) * N4;
+            reinterpret_cast<float4*>(dst)[0] = make_float4(lin[t][0].x, lin[t][0].y, lin[t][1].x, lin[t][1].y);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(lin[t][2].x, lin[t][2].y, lin[t][3].x, lin[t][3].y);
+          }
+        }
+      }
+      __threadfence_block();
+      bar_arrive(BAR_FULL + par, NT);  // plane j's P, S1 and SL tiles are ready for B
+    }
+    cp_async_wait<0>();
+    for (int it = max(0, nplanes - 2); it < nplanes; ++it) bar_sync(BAR_EMPTY + (it & 1), NT);
+  } else {
+    // ======================= B: columns, ring, outputs =======================
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_B));
+    const int tb = tid - NA;
+    const int i4b = tb % N4;
+    const int bcol = (tb / N4) % T3;
+    const int a0 = (tb / (N4 * T3)) * P;
+    const bool col_ok = (i3_0 + bcol) < n3;
+    const int64_t out_base = ((int64_t)(i2_0 + a0) * n3 + i3_0 + bcol) * N4 + i4b;
+    const int64_t row_step = (int64_t)n3 * N4;
+    unsigned row_ok = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) row_ok |= (col_ok && (i2_0 + a0 + k) < n2) ? (1u << k) : 0u;
+
+    float2 acc[P / 2][7];
+#pragma unroll
+    for (int k = 0; k < P / 2; ++k)
+#pragma unroll
+      for (int e = 0; e < 7; ++e) acc[k][e] = make_float2(0.f, 0.f);
+    float2 w2[P / 2], lin2[P / 2], pc2[P / 2];
+    float g1r[7], l1r[5];
+#pragma unroll
+    for (int k2 = 0; k2 < P / 2; ++k2) w2[k2] = lin2[k2] = pc2[k2] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < 7; ++e) g1r[e] = 0.f;
+#pragma unroll
+    for (int e = 0; e < 5; ++e) l1r[e] = 0.f;
+
+#pragma unroll 1
+    for (int j = jb; j < c1 + kGramHalf; ++j) {
+      const int it = j - jb;
+      const bool have = j < je;
+      const int par = it & 1;
+      if (have) {
+        bar_sync(BAR_FULL + par, NT);
+        const float* src = sm + C::OFF_P + par * C::TILE;
+        const float* s_s1 = sm + C::OFF_S1 + par * C::S1N;
+        const float* s_sl = sm + C::OFF_SL + par * C::SLN;
+        float s1c[P + 6];
+#pragma unroll
+        for (int k = 0; k < P + 6; ++k) s1c[k] = s_s1[(a0 + k) * ROW1 + bcol * N4 + i4b];
+        float s0c[P + 4];
+#pragma unroll
+        for (int k = 0; k < P + 4; ++k) s0c[k] = src[(a0 + 1 + k) * ROW + (bcol + 3) * N4 + i4b];
+        float slv[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) slv[k] = s_sl[(a0 + k) * ROW1 + bcol * N4 + i4b];
+        __threadfence_block();
+        bar_arrive(BAR_EMPTY + par, NT);  // everything B reads of plane j is in registers
+#pragma unroll
+        for (int e = 0; e < 7; ++e) g1r[e] = __ldg(a.g[0] + (int64_t)j * 7 + e);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) l1r[e] = __ldg(a.l[0] + (int64_t)j * 5 + e);
+        const bool own_plane = (j >= c0) && (j < c1);
+        float* pn = CG ? a.pnew + (int64_t)j * plane + out_base : nullptr;
+#pragma unroll
+        for (int h = 0; h < P / 4; ++h) {
+          float4 g2f[7], l2f[5];
+#pragma unroll
+          for (int e = 0; e < 7; ++e) g2f[e] = *reinterpret_cast<const float4*>(g2s + e * T2 + a0 + 4 * h);
+#pragma unroll
+          for (int e = 0; e < 5; ++e) l2f[e] = *reinterpret_cast<const float4*>(l2s + e * T2 + a0 + 4 * h);
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int k2 = 2 * h + hh;
+            const int k = 2 * k2;
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int e = 0; e < 7; ++e) {
+              const float2 cf = hh ? make_float2(g2f[e].z, g2f[e].w) : make_float2(g2f[e].x, g2f[e].y);
+              w = ffma2(cf, make_float2(s1c[k + e], s1c[k + 1 + e]), w);
+            }
+            float2 lin = make_float2(slv[k], slv[k + 1]);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+              const float2 cf = hh ? make_float2(l2f[e].z, l2f[e].w) : make_float2(l2f[e].x, l2f[e].y);
+              lin = ffma2(cf, make_float2(s0c[k + e], s0c[k + 1 + e]), lin);
+            }
+            const float2 pcv = make_float2(s0c[k + 2], s0c[k + 3]);
+            w2[k2] = w;
+            lin2[k2] = lin;
+            pc2[k2] = pcv;
+            if constexpr (CG) {
+              float* ring = s_ring + (j & 3) * C::CORE;
+              ring[(k) * NB + tb] = pcv.x;
+              ring[(k + 1) * NB + tb] = pcv.y;
+              if (own_plane && ((row_ok >> k) & 1u)) pn[k * row_step] = pcv.x;
+              if (own_plane && ((row_ok >> (k + 1)) & 1u)) pn[(k + 1) * row_step] = pcv.y;
+            }
+          }
+        }
+      }
+      const int c = j - kGramHalf;
+      auto step = [&](auto tag) {
+        constexpr int S = decltype(tag)::value;
+        if (have) {
+#pragma unroll
+          for (int k2 = 0; k2 < P / 2; ++k2) {
+#pragma unroll
+            for (int d = -3; d <= 3; ++d)
+              acc[k2][(S + d + 7) % 7] = ffma2(bc2(g1r[3 + d]), w2[k2], acc[k2][(S + d + 7) % 7]);
+#pragma unroll
+            for (int d = -2; d <= 2; ++d)
+              acc[k2][(S + d + 7) % 7] = ffma2(bc2(l1r[2 + d]), pc2[k2], acc[k2][(S + d + 7) % 7]);
+            acc[k2][S].x += lin2[k2].x;
+            acc[k2][S].y += lin2[k2].y;
+          }
+        }
+        constexpr int E = (S + 4) % 7;
+        if (c >= c0) {
+          float part = 0.f;
+          float* qo = a.q + (int64_t)c * plane + out_base;
+          const float* ring = s_ring + (c & 3) * C::CORE + tb;
+#pragma unroll
+          for (int k2 = 0; k2 < P / 2; ++k2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int k = 2 * k2 + h;
+              if ((row_ok >> k) & 1u) {
+                const float qv = h ? acc[k2][E].y : acc[k2][E].x;
+                qo[k * row_step] = qv;
+                if constexpr (CG) part = fmaf(qv, ring[k * NB], part);
+              }
+            }
+          }
+          dot += (double)part;
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < P / 2; ++k2) acc[k2][E] = make_float2(0.f, 0.f);
+      };
+      switch (j % 7) {
+        case 0: step(std::integral_constant<int, 0>{}); break;
+        case 1: step(std::integral_constant<int, 1>{}); break;
+        case 2: step(std::integral_constant<int, 2>{}); break;
+        case 3: step(std::integral_constant<int, 3>{}); break;
+        case 4: step(std::integral_constant<int, 4>{}); break;
+        case 5: step(std::integral_constant<int, 5>{}); break;
+        default: step(std::integral_constant<int, 6>{}); break;
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (CG) {
+    double total;
+    if (dev::grid_sum_last(dot, a.red, &total, s_red)) {
+      Scalars* sc = a.scal;
+      sc->pq = total;
+      const double alpha = sc->rho / total;
+      if (!(total > 0.0) || !isfinite(alpha)) {
+        sc->breakdown = 1;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = alpha;
+      }
+    }
+  }
+}
+
+constexpr size_t ws_bytes() {
+  using C = Cfg<8, 16, 16, 2, NB, 3, true>;
+  return sizeof(float) * (size_t)(C::OFF_RED + 2 * (NT / 32));  // reduction scratch for 16 warps
+}
+
+}  // namespace ws
+
 template <int N4, int T2, int T3, int T3P, int NT, int STAGES, bool CG>
 tca_status launch_fused(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   using C = Cfg<N4, T2, T3, T3P, NT, STAGES, CG>;
@@ -605,6 +1053,49 @@ tca_status launch_fused(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   return TCA_OK;
 }
 
+template <bool CG>
+tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
+  constexpr size_t bytes = ws::ws_bytes();
+  static_assert(bytes <= 227 * 1024, "shared memory budget");
+  auto kfn = ws::fused_ws_kernel<CG>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return TCA_ERR_CUDA;
+    }
+    attr_done = true;
+  }
+  FusedArgs a = base;
+  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const int tiles2 = (n2 + 15) / 16, tiles3 = (n3 + 15) / 16;
+  const int tiles = tiles2 * tiles3;
+  int best_nc = 1;
+  double best_cost = 1e30;
+  for (int nc = 1; nc <= n1; ++nc) {
+    const int len = (n1 + nc - 1) / nc;
+    if ((int64_t)tiles * nc > p->red.max_blocks) break;
+    const int64_t waves = ((int64_t)tiles * nc + p->num_sms - 1) / p->num_sms;
+    const double cost = (double)waves * (len + 2 * kGramHalf);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best_nc = nc;
+    }
+  }
+  if (p->fused_nchunks > 0 && (int64_t)tiles * p->fused_nchunks <= p->red.max_blocks)
+    best_nc = std::min(p->fused_nchunks, n1);
+  p->fused_model_nchunks = best_nc;
+  a.chunk = (n1 + best_nc - 1) / best_nc;
+  a.nchunks = (n1 + a.chunk - 1) / a.chunk;
+  a.tiles3 = tiles3;
+  const int grid = tiles * a.nchunks;
+  if (grid > p->red.max_blocks) return TCA_ERR_UNSUPPORTED;
+  kfn<<<grid, ws::NT, bytes, s>>>(a);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
 }  // namespace
 
 tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, float* p_new, float* q,
@@ -634,7 +1125,7 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
   a.red = p->red;
   const int64_t n4 = dims[3];
   if (n4 == 8) {
-    return cg_mode ? launch_fused<8, 16, 16, 2, 256, 3, true>(p, a, s) : launch_fused<8, 16, 16, 2, 256, 3, false>(p, a, s);
+    return cg_mode ? launch_ws<true>(p, a, s) : launch_ws<false>(p, a, s);
   } else if (n4 == 4) {
     return cg_mode ? launch_fused<4, 16, 32, 4, 256, 3, true>(p, a, s) : launch_fused<4, 16, 32, 4, 256, 3, false>(p, a, s);
   } else if (n4 == 1) {
