@@ -880,15 +880,21 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
         const float* src = sm + C::OFF_P + par * C::TILE;
         const float* s_s1 = sm + C::OFF_S1 + par * C::S1N;
         const float* s_sl = sm + C::OFF_SL + par * C::SLN;
-        float s1c[P + 6];
+        // Column values as register pairs (rows 2i, 2i + 1): a tap whose rows
+        // pair up evenly uses one packed FMA, an odd tap two scalar FMAs.
+        float2 s1p[(P + 6) / 2];
 #pragma unroll
-        for (int k = 0; k < P + 6; ++k) s1c[k] = s_s1[(a0 + k) * ROW1 + bcol * N4 + i4b];
-        float s0c[P + 4];
+        for (int i = 0; i < (P + 6) / 2; ++i)
+          s1p[i] = make_float2(s_s1[(a0 + 2 * i) * ROW1 + bcol * N4 + i4b], s_s1[(a0 + 2 * i + 1) * ROW1 + bcol * N4 + i4b]);
+        float2 s0p[(P + 4) / 2];
 #pragma unroll
-        for (int k = 0; k < P + 4; ++k) s0c[k] = src[(a0 + 1 + k) * ROW + (bcol + 3) * N4 + i4b];
-        float slv[P];
+        for (int i = 0; i < (P + 4) / 2; ++i)
+          s0p[i] = make_float2(src[(a0 + 1 + 2 * i) * ROW + (bcol + 3) * N4 + i4b],
+                               src[(a0 + 2 + 2 * i) * ROW + (bcol + 3) * N4 + i4b]);
+        float2 slp[P / 2];
 #pragma unroll
-        for (int k = 0; k < P; ++k) slv[k] = s_sl[(a0 + k) * ROW1 + bcol * N4 + i4b];
+        for (int i = 0; i < P / 2; ++i)
+          slp[i] = make_float2(s_sl[(a0 + 2 * i) * ROW1 + bcol * N4 + i4b], s_sl[(a0 + 2 * i + 1) * ROW1 + bcol * N4 + i4b]);
         __threadfence_block();
         bar_arrive(BAR_EMPTY + par, NT);  // everything B reads of plane j is in registers
 #pragma unroll
@@ -912,15 +918,25 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 #pragma unroll
             for (int e = 0; e < 7; ++e) {
               const float2 cf = hh ? make_float2(g2f[e].z, g2f[e].w) : make_float2(g2f[e].x, g2f[e].y);
-              w = ffma2(cf, make_float2(s1c[k + e], s1c[k + 1 + e]), w);
+              if ((e & 1) == 0) {
+                w = ffma2(cf, s1p[(k + e) / 2], w);
+              } else {
+                w.x = fmaf(cf.x, s1p[(k + e) / 2].y, w.x);
+                w.y = fmaf(cf.y, s1p[(k + e + 1) / 2].x, w.y);
+              }
             }
-            float2 lin = make_float2(slv[k], slv[k + 1]);
+            float2 lin = slp[k2];
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
               const float2 cf = hh ? make_float2(l2f[e].z, l2f[e].w) : make_float2(l2f[e].x, l2f[e].y);
-              lin = ffma2(cf, make_float2(s0c[k + e], s0c[k + 1 + e]), lin);
+              if ((e & 1) == 0) {
+                lin = ffma2(cf, s0p[(k + e) / 2], lin);
+              } else {
+                lin.x = fmaf(cf.x, s0p[(k + e) / 2].y, lin.x);
+                lin.y = fmaf(cf.y, s0p[(k + e + 1) / 2].x, lin.y);
+              }
             }
-            const float2 pcv = make_float2(s0c[k + 2], s0c[k + 3]);
+            const float2 pcv = s0p[(k + 2) / 2];
             w2[k2] = w;
             lin2[k2] = lin;
             pc2[k2] = pcv;
