@@ -285,15 +285,20 @@ def run_learned(args, device):
         for _ in range(2):  # warm-up: graphs, workspaces
             plan.solve(b, x, rtol=RTOL)
             net.solve(plan, b, x, rtol=RTOL)
+            net.solve(plan, b, x, rtol=RTOL, net_every=16)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         res = {}
-        for name, fn in (("plain", lambda: plan.solve(b, x, rtol=RTOL)), ("net", lambda: net.solve(plan, b, x, rtol=RTOL))):
+        variants = (("plain", lambda: plan.solve(b, x, rtol=RTOL)),
+                    ("net_x0", lambda: net.solve(plan, b, x, rtol=RTOL)),
+                    ("net_x0_step16", lambda: net.solve(plan, b, x, rtol=RTOL, net_every=16)))
+        for name, fn in variants:
             e0.record()
             for _ in range(args.steps):
                 _, info = fn()
             e1.record()
             torch.cuda.synchronize()
             res[name] = {"ms": round(e0.elapsed_time(e1) / args.steps, 3), "iters": info["iters"],
+                         "net_steps": info["refinements"] if name != "plain" else 0,
                          "rel_res_true": info["rel_res_true"]}
         # network forward alone at this size
         u = torch.empty(SHAPE, dtype=torch.float32, device=device)

@@ -76,11 +76,17 @@ TCA_API tca_status tca_net_adam(tca_net_t net, float lr, float beta1, float beta
                                 cudaStream_t stream);
 
 /* Solve (A^T A + lambda R) x = A^T b like tca_solve, starting from
- * x0 = s Net(A^T b / s) with s the RMS of A^T b (FP32).  The plan must be
- * FP32 or an _IR precision, of order 3 (B = 1) or 4.  b and x: device
- * pointers.  opts->x0_given is ignored.  Synchronises the stream. */
+ * x0 = s Net(A^T b / s) with s the RMS of A^T b (FP32).  With net_every > 0
+ * the network is also applied as a preconditioner step: after every
+ * net_every CG iterations that did not converge, x += s' Net(r / s') with r
+ * the true residual A^T b - K x and s' its RMS, and CG restarts from x.  CG
+ * stays the judge of the error: the solve stops on the same true relative
+ * residual as tca_solve.  info->iters counts all CG iterations,
+ * info->refinements the preconditioner steps.  The plan must be FP32 or an
+ * _IR precision, of order 3 (B = 1) or 4.  b and x: device pointers.
+ * opts->x0_given is ignored.  Synchronises the stream. */
 TCA_API tca_status tca_solve_net(tca_plan_t plan, tca_net_t net, const void* b, void* x, const tca_solve_opts* opts,
-                                 tca_solve_info* info, cudaStream_t stream);
+                                 int net_every, tca_solve_info* info, cudaStream_t stream);
 
 /* Run the 32 -> 32 channel layers (forward and input gradients) on the
  * tensor cores (enable != 0, the default: tcgen05 implicit GEMM, BF16

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -997,9 +998,31 @@ extern "C" tca_status tca_net_adam(tca_net_t n, float lr, float beta1, float bet
 }
 
 // x0 = s Net(A^T b / s), s = RMS(A^T b), then CG from x0 (tca_solve with x0_given).
+namespace {
+
+__global__ void add_kernel(float* __restrict__ x, const float* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
+// kx <- rhs - kx
+__global__ void residual_kernel(const float* __restrict__ rhs, float* __restrict__ kx, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    kx[i] = rhs[i] - kx[i];
+}
+
+// d = s Net(v / s), s = RMS(v), into out (device, V floats).
+tca_status net_correction(tca_net_s* n, const float* v, float* out, const Dims& d, cudaStream_t s) {
+  rms_kernel<<<std::min<int64_t>((d.V + 255) / 256, 1024), 256, 0, s>>>(v, d.V, n->scale, n->red);
+  TCA_LAUNCH_CHECK();
+  return forward(n, v, out, d, true, s);
+}
+
+}  // namespace
+
 extern "C" tca_status tca_solve_net(tca_plan_t plan, tca_net_t n, const void* b, void* x, const tca_solve_opts* opts,
-                                    tca_solve_info* info, cudaStream_t s) {
-  if (!plan || !n || !b || !x) return TCA_ERR_INVALID_ARG;
+                                    int net_every, tca_solve_info* info, cudaStream_t s) {
+  if (!plan || !n || !b || !x || net_every < 0) return TCA_ERR_INVALID_ARG;
   if (plan->prec == TCA_F64) return TCA_ERR_UNSUPPORTED;
   if (plan->d != 4 && plan->d != 3) return TCA_ERR_UNSUPPORTED;
   if (!is_device_ptr(b) || !is_device_ptr(x)) return TCA_ERR_UNSUPPORTED;
@@ -1007,16 +1030,45 @@ extern "C" tca_status tca_solve_net(tca_plan_t plan, tca_net_t n, const void* b,
   Dims d;
   TCA_TRY(get_dims(dims, &d));
   TCA_TRY(ensure_act(n, d.V));
-  // A^T b (FP32) into the net's output buffer, its RMS, then the network.
+  const auto t0 = std::chrono::steady_clock::now();
+  // x0 = s Net(A^T b / s): A^T b (FP32) into the net's output buffer, then the network.
   TCA_TRY(tca_apply_T(plan, b, n->y, s));
-  rms_kernel<<<std::min<int64_t>((d.V + 255) / 256, 1024), 256, 0, s>>>(n->y, d.V, n->scale, n->red);
-  TCA_LAUNCH_CHECK();
-  TCA_TRY(forward(n, n->y, (float*)x, d, true, s));
+  TCA_TRY(net_correction(n, n->y, (float*)x, d, s));
   tca_solve_opts o = opts ? *opts : tca_solve_opts{};
   if (!opts) {
     o.rtol = 1e-6;
     o.max_iter = 10000;
   }
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 10000;
   o.x0_given = 1;
-  return tca_solve(plan, b, x, &o, info, s);
+  tca_solve_info acc{}, step{};
+  int corrections = 0;
+  tca_status st = TCA_OK;
+  for (;;) {
+    o.max_iter = net_every > 0 ? std::min(net_every, max_iter - acc.iters) : max_iter - acc.iters;
+    st = tca_solve(plan, b, x, &o, &step, s);
+    acc.iters += step.iters;
+    acc.refinements += step.refinements;
+    acc.rel_res_true = step.rel_res_true;
+    acc.rel_res_recursive = step.rel_res_recursive;
+    acc.sweep_ms += step.sweep_ms;
+    acc.sweep_launches += step.sweep_launches;
+    if (st != TCA_ERR_NOT_CONVERGED || net_every == 0 || acc.iters >= max_iter) break;
+    // Preconditioner step: x += s Net(r / s) on the residual r = A^T b - K x
+    // (A^T b in FP32 is still in the net's output buffer), then CG restarts from x.
+    const int vg = (int)std::min<int64_t>((d.V + 255) / 256, (int64_t)n->num_sms * 8);
+    TCA_TRY(tca_apply_normal(plan, x, n->g, s));
+    residual_kernel<<<vg, 256, 0, s>>>(n->y, n->g, d.V);
+    TCA_LAUNCH_CHECK();
+    TCA_TRY(net_correction(n, n->g, n->g, d, s));
+    add_kernel<<<vg, 256, 0, s>>>((float*)x, n->g, d.V);
+    TCA_LAUNCH_CHECK();
+    ++corrections;
+  }
+  if (info) {
+    *info = acc;
+    info->refinements = corrections;  // preconditioner steps taken inside the solve
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
 }

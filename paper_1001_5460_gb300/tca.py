@@ -99,8 +99,8 @@ _lib.tca_net_take_loss.restype = ctypes.c_int
 _lib.tca_net_adam.argtypes = [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               _vp]
 _lib.tca_net_adam.restype = ctypes.c_int
-_lib.tca_solve_net.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info),
-                               _vp]
+_lib.tca_solve_net.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.c_int,
+                               ctypes.POINTER(tca_solve_info), _vp]
 _lib.tca_solve_net.restype = ctypes.c_int
 _lib.tca_net_use_tensor_cores.argtypes = [_vp, ctypes.c_int]
 _lib.tca_net_use_tensor_cores.restype = ctypes.c_int
@@ -385,14 +385,14 @@ class Net:
         _check(_lib.tca_net_adam(self._h, lr, beta1, beta2, eps, grad_scale, _stream(stream)), "tca_net_adam")
 
     def solve(self, plan: "Plan", b, x, rtol: float = 1e-6, max_iter: int = 10000, check_every: int = 16,
-              inner_rtol: float = 0.0, max_refine: int = 0, stream=None, raise_on_error: bool = True,
-              profile: bool = False):
-        """tca_solve from the initial guess x0 = s Net(A^T b / s); returns (status, info dict)."""
+              inner_rtol: float = 0.0, max_refine: int = 0, net_every: int = 0, stream=None,
+              raise_on_error: bool = True, profile: bool = False):
+        """tca_solve from x0 = s Net(A^T b / s), plus a network step every net_every iterations (0: none)."""
         opts = tca_solve_opts(float(rtol), int(max_iter), 1, float(inner_rtol), int(max_refine), int(check_every),
                               1 if profile else 0)
         info = tca_solve_info()
-        st = _lib.tca_solve_net(plan.handle, self._h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info),
-                                _stream(stream))
+        st = _lib.tca_solve_net(plan.handle, self._h, _ptr(b), _ptr(x), ctypes.byref(opts), int(net_every),
+                                ctypes.byref(info), _stream(stream))
         if raise_on_error:
             _check(st, "tca_solve_net", ok=(OK, ERR_NOT_CONVERGED))
         return st, _info_dict(info)

@@ -96,7 +96,7 @@ def test_net_entry_points_check_arguments(tca):
     assert tca._lib.tca_net_forward(None, None, None, None, None) == tca.ERR_INVALID_ARG
     assert tca._lib.tca_net_accumulate(None, None, None, None, None) == tca.ERR_INVALID_ARG
     assert tca._lib.tca_net_adam(None, 1e-3, 0.9, 0.999, 1e-8, 1.0, None) == tca.ERR_INVALID_ARG
-    assert tca._lib.tca_solve_net(None, None, None, None, None, None, None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_solve_net(None, None, None, None, None, 0, None, None) == tca.ERR_INVALID_ARG
     assert tca._lib.tca_solve_batched(0, None, None, None, None, None, None) == tca.ERR_INVALID_ARG
     assert tca._lib.tca_autotune(None, None) == tca.ERR_INVALID_ARG
     tca._lib.tca_net_destroy(None)

@@ -172,3 +172,10 @@ def test_training_reduces_loss_and_solve_from_net_guess():
     rel = O.rel_residual(x_net.cpu().numpy(), bh, mats, inst.lam)
     assert rel <= 1.5e-6, (rel, info_net)
     assert info_net["iters"] <= info_plain["iters"], (info_net, info_plain)
+    # The network as a preconditioner step every 8 iterations: CG still judges the error.
+    x_pc = torch.empty_like(x_plain)
+    st, info_pc = net.solve(plan, b, x_pc, rtol=1e-6, net_every=8)
+    assert st == tca.OK
+    assert info_pc["refinements"] >= 1
+    rel = O.rel_residual(x_pc.cpu().numpy(), bh, mats, inst.lam)
+    assert rel <= 1.5e-6, (rel, info_pc)
