@@ -7,8 +7,8 @@
 // A tile is 128 consecutive positions (M = 128), K = n_in (padded to 8) and
 // N = n_out (padded to 16).  The factor is staged once per CTA in shared
 // memory in the canonical K-major core-matrix layout (8 rows x 16 bytes).  A
-// persistent CTA walks its tiles with three warp roles: four load warps (one
-// thread per tile row) read X from HBM and write the A tile, one thread issues
+// persistent CTA walks its tiles with three warp roles: twelve load warps
+// (three threads per tile row) read X from HBM and write the A tile, one thread issues
 // the tcgen05.mma chain into one of two TMEM accumulators and commits to
 // mbarriers, and four epilogue warps read TMEM back (tcgen05.ld) and write y,
 // so that loading tile t + 1, the MMAs of tile t and the epilogue of tile t - 1
@@ -27,9 +27,10 @@ namespace tca {
 namespace {
 
 constexpr int kM = 128;
-constexpr int kLoadWarps = 4, kEpiWarps = 4;
-constexpr int kMmaWarp = kLoadWarps;                                   // warp 4
-constexpr int kTcThreads = (kLoadWarps + 1 + kEpiWarps) * 32;          // 288
+constexpr int kLoadWarps = 12, kEpiWarps = 4;
+constexpr int kKParts = kLoadWarps / 4;                                // load threads per tile row
+constexpr int kMmaWarp = kLoadWarps;                                   // warp 12
+constexpr int kTcThreads = (kLoadWarps + 1 + kEpiWarps) * 32;          // 544
 constexpr long long kTcWaitLimit = 1ll << 26;
 constexpr int kChunk = 32;  // K values a load thread holds per step
 
@@ -87,14 +88,16 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, int parity, volatile int* 
 }
 
 // Warp roles (one CTA per SM, persistent over tiles of 128 positions):
-//   warps 0-3  load: thread r owns row r of the tile; it reads the row's n_in
-//              values from HBM (32 at a time, the next chunk in flight while
-//              the current one is written), splits them into TF32 head and
-//              tail (3xTF32) and writes the canonical K-major A tile;
-//   warp 4     MMA: one thread issues the tcgen05.mma chain of a tile into one
-//              of two TMEM accumulators and commits to two mbarriers (A free,
-//              accumulator full);
-//   warps 5-8  epilogue: TMEM -> registers (tcgen05.ld) -> y.
+//   warps 0-11  load: three threads per tile row, each owning a third of the
+//               row's n_in values; they read them from HBM (32 at a time, the
+//               next chunk in flight while the current one is written), split
+//               them into TF32 head and tail (3xTF32) and write the canonical
+//               K-major A tile (many loads in flight per SM: the reads are
+//               latency-bound otherwise);
+//   warp 12     MMA: one thread issues the tcgen05.mma chain of a tile into
+//               one of two TMEM accumulators and commits to two mbarriers (A
+//               free, accumulator full);
+//   warps 13-16 epilogue: TMEM -> registers (tcgen05.ld) -> y.
 // Loading tile t + 1 overlaps the MMAs of tile t and the epilogue of t - 1.
 __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(const float* __restrict__ x, float* __restrict__ y,
                                                                  const float* __restrict__ a, TcGeom g,
@@ -145,7 +148,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(const float* __
 
   if (warp < kLoadWarps) {
     // ---------------- load / split ----------------
-    const int r = tid;
+    const int r = tid % kM;
+    // K range of this thread: part kp of kKParts, a multiple of 4 wide.
+    const int kp = tid / kM;
+    const int kw = ((g.Kp / 4 + kKParts - 1) / kKParts) * 4;
+    const int kb = kp * kw, ke = min(g.Kp, kb + kw);
     const bool fibre = g.I == 1 && (g.n_in % 4) == 0;
     int k = 0;
     for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x, ++k) {
@@ -170,14 +177,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(const float* __
           }
         }
       };
-      load(0, cur);
+      if (kb < ke) load(kb, cur);
       if (k > 0 && !bar_wait(&bars[BAR_AEMPTY], (k - 1) & 1, abort)) break;  // MMAs of tile k-1 read A
-      for (int c0 = 0; c0 < g.Kp; c0 += kChunk) {
-        if (c0 + kChunk < g.Kp) load(c0 + kChunk, nxt);
+      for (int c0 = kb; c0 < ke; c0 += kChunk) {
+        if (c0 + kChunk < ke) load(c0 + kChunk, nxt);
 #pragma unroll
         for (int u = 0; u < kChunk / 4; ++u) {
           const int l = c0 + 4 * u;
-          if (l >= g.Kp) break;
+          if (l >= ke) break;
           const int off = (r >> 3) * sbo + (l >> 2) * 128 + (r & 7) * 16;
           float4 h = make_float4(cur[4 * u], cur[4 * u + 1], cur[4 * u + 2], cur[4 * u + 3]);
           if (nsplit == 2) {
