@@ -283,20 +283,28 @@ __global__ void __launch_bounds__(kThreads) conv32to32_kernel(const __nv_bfloat1
 // the A operand is the input rows (z + a - 1, y + b - 1) shifted by (e - 1) B
 // voxels, K = 32 input channels, N = 32 output channels:
 //   D[r][o] += sum_i in[v_r + off t][i] W[t][o][i]      (27 taps x 2 MMAs of K = 16)
-// A CTA walks a column of tiles along y for fixed (z, segment): input strips
+// A CTA walks columns of tiles along y for fixed (z, segment): input strips
 // (128 + 2B voxels x 32 channels of one row (z', y')) stay in a 5-row ring in
-// shared memory, each new y loads the three strips of row y + 2 (cp.async
-// with zero fill at the volume's edges), so every input row is read about
-// once per (z', segment) column.  Strip layout: [channel chunk c (4)][voxel
-// s][16 bytes] - the canonical no-swizzle K-major layout (8 voxel rows x
-// 16 bytes per core matrix), so a tap's shift is just a start address.  Two
-// TMEM accumulators alternate: the epilogue of tile y - 1 (bias + ReLU or the
-// ReLU mask, bfloat16, 64 bytes per voxel) overlaps the MMAs of tile y.
+// shared memory and each input row is loaded once per column.  Strip layout:
+// [channel chunk c (4)][voxel s][16 bytes] - the canonical no-swizzle K-major
+// layout (8 voxel rows x 16 bytes per core matrix), so a tap's shift is just
+// a start address.  Warp roles, connected by mbarriers (every wait bounded):
+//   warps 0-3  producer: cp.async of the three strips of the next row into a
+//              free ring slot (zero fill at the volume's faces); completion
+//              arrives on the slot's mbarrier (cp.async.mbarrier.arrive);
+//   warp 4     MMA: one thread issues the 54 MMAs of a tile into one of two
+//              TMEM accumulators, commits to the accumulator's mbarrier and,
+//              for the row no later tile reads, to that ring slot's mbarrier;
+//   warps 5-8  epilogue: TMEM -> registers, bias + ReLU (forward) or the ReLU
+//              mask of the layer below (input gradient), bfloat16, 64 bytes per
+//              voxel to HBM.
 namespace tc {
 
 constexpr int kTile = 128;
 constexpr int kRing = 5;
-constexpr int kThr = 128;
+constexpr int kProdWarps = 4, kEpiWarps = 4;
+constexpr int kMmaWarp = kProdWarps;
+constexpr int kThr = (kProdWarps + 1 + kEpiWarps) * 32;  // 288
 constexpr long long kWaitLimit = 1ll << 26;
 constexpr int kWBytes = T * C * C * 2;  // 55296
 
@@ -321,168 +329,269 @@ struct Args {
   int64_t items;
 };
 
-// Issue the three strips (z - 1 .. z + 1) of row yr for segment seg into ring slot.
-__device__ __forceinline__ void load_row(const Args& g, unsigned char* ring, int z, int yr, int seg, int tid) {
-  unsigned char* slot = ring + (size_t)(((yr % kRing) + kRing) % kRing) * 3 * 4 * g.S * 16;
-  const int n16 = 3 * 4 * g.S;
-  for (int idx = tid; idx < n16; idx += kThr) {
-    const int c = idx & 3;
-    const int s = (idx >> 2) % g.S;
-    const int dz = idx / (4 * g.S);
-    const int zz = z + dz - 1;
-    const int vl = seg * kTile - g.B + s;
-    const bool ok = zz >= 0 && zz < g.D && yr >= 0 && yr < g.H && vl >= 0 && vl < g.L;
-    const __nv_bfloat16* src = ok ? g.in + (((int64_t)zz * g.H + yr) * g.L + vl) * C + c * 8 : g.in;
-    unsigned char* dst = slot + ((size_t)dz * 4 + c) * g.S * 16 + (size_t)s * 16;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(ok ? 16 : 0)
-                 : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
+// barrier layout: full[kRing], empty[kRing], acc_full[2], acc_empty[2]
+enum { B_FULL = 0, B_EMPTY = kRing, B_ACCF = 2 * kRing, B_ACCE = 2 * kRing + 2, NBAR = 2 * kRing + 4 };
 
-__device__ __forceinline__ bool wait_bar(unsigned bar, int parity) {
+__device__ __forceinline__ void bar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, int parity, volatile int* abort) {
   for (long long it = 0; it < kWaitLimit; ++it) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(su32(b)), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 255) == 255 && *abort) return false;
   }
+  *abort = 1;
   return false;
 }
+
+// Per-CTA walk over (item, row) in a fixed order shared by every role: item
+// `it` covers tiles y0 .. y1 - 1 of column (z, seg) and input rows y0 - 1 .. y1.
+struct Walk {
+  int z, seg, y0, y1;
+  __device__ __forceinline__ void set(const Args& g, int64_t item) {
+    const int yc = (int)(item % g.ychunks);
+    seg = (int)((item / g.ychunks) % g.segs);
+    z = (int)(item / ((int64_t)g.ychunks * g.segs));
+    y0 = yc * g.ychunk;
+    y1 = min(g.H, y0 + g.ychunk);
+  }
+};
 
 __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  unsigned char* sw = base;                       // weights
-  unsigned char* ring = base + kWBytes;           // kRing x 3 x 4 x S x 16
+  unsigned char* sw = base;                                          // weights
+  unsigned char* ring = base + kWBytes;                              // kRing x 3 x 4 x S x 16
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kRing * 3 * 4 * g.S * 16);
-  unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2);
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + NBAR);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   float* sbias = reinterpret_cast<float*>(tslot + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned strip_bytes = 4u * g.S * 16u;
 
   for (int k = tid; k < kWBytes / 16; k += kThr)
     reinterpret_cast<uint4*>(sw)[k] = __ldg(reinterpret_cast<const uint4*>(g.w) + k);
   if (tid < C) sbias[tid] = g.bias ? g.bias[tid] : 0.f;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[1])));
+    for (int i = 0; i < kRing; ++i) {
+      bar_init(&bars[B_FULL + i], kProdWarps * 32);
+      bar_init(&bars[B_EMPTY + i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&bars[B_ACCF + i], 1);
+      bar_init(&bars[B_ACCE + i], kEpiWarps * 32);
+    }
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(64));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights -> tensor-core reads
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const unsigned tmem = *tslot;
-  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(C >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
-  const unsigned sw_a = su32(sw), ring_a = su32(ring);
-  const unsigned strip_bytes = 4u * g.S * 16u;
-  int parity[2] = {0, 0};
-  bool timed_out = false;
 
-  for (int64_t item = blockIdx.x; item < g.items && !timed_out; item += gridDim.x) {
-    const int yc = (int)(item % g.ychunks);
-    const int seg = (int)((item / g.ychunks) % g.segs);
-    const int z = (int)(item / ((int64_t)g.ychunks * g.segs));
-    const int y0 = yc * g.ychunk, y1 = min(g.H, y0 + g.ychunk);
-    // Prologue: rows y0 - 1 .. y0 + 2; iteration y issues row y + 3.
-    for (int r = y0 - 1; r <= y0 + 2; ++r) load_row(g, ring, z, r, seg, tid);
-    for (int y = y0; y <= y1; ++y) {
-      if (y < y1) {
-        // Rows <= y + 1 have landed; row y + 2 (the newest group) may still be in flight.
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-          const unsigned dtm = tmem + (unsigned)((y & 1) * C);
-          int first = 1;
+  if (warp < kProdWarps) {
+    // ---------------- producer ----------------
+    // The copy pattern of a row is the same for every row: per thread, up to
+    // kMaxCp 16-byte pieces (strip dz, channel chunk c, voxel sv) with their
+    // shared-memory offsets, precomputed once.
+    constexpr int kMaxCp = (3 * 4 * 176 + kProdWarps * 32 - 1) / (kProdWarps * 32);  // S <= 176
+    int cp_dst[kMaxCp], cp_sv[kMaxCp];
+    uint64_t cp_dz = 0;  // 2 bits per piece
+    const int n16 = 3 * 4 * g.S;
+#pragma unroll
+    for (int i = 0; i < kMaxCp; ++i) {
+      const int idx = tid + i * kProdWarps * 32;
+      cp_dst[i] = -1;
+      cp_sv[i] = 0;
+      if (idx < n16) {
+        const int c = idx & 3;
+        const int sv = (idx >> 2) % g.S;
+        const int dz = idx / (4 * g.S);
+        cp_dst[i] = (dz * 4 + c) * g.S * 16 + sv * 16;
+        cp_sv[i] = sv * C + c * 8;  // element offset within the strip's voxels (before the row base)
+        cp_dz |= (uint64_t)dz << (2 * i);
+      }
+    }
+    int64_t n = 0;  // row sequence number of this CTA
+    bool stop = false;
+    for (int64_t item = blockIdx.x; item < g.items && !stop; item += gridDim.x) {
+      Walk wk;
+      wk.set(g, item);
+      const int vl0 = wk.seg * kTile - g.B;  // voxel of strip position 0
+      for (int yr = wk.y0 - 1; yr <= wk.y1; ++yr, ++n) {
+        const int slot = (int)(n % kRing);
+        if (n >= kRing && !bar_wait(&bars[B_EMPTY + slot], (int)((n / kRing - 1) & 1), abort)) {
+          stop = true;
+          break;
+        }
+        const unsigned sp = su32(ring) + (unsigned)slot * 3u * strip_bytes;
+        // Element offset of strip position 0 in each strip's row (z - 1, z, z + 1)
+        // (negative for the first segment's halo) and whether that row exists.
+        int64_t rb[3];
+        unsigned rok = 0;
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+          const int zz = wk.z + dz - 1;
+          const bool in_vol = zz >= 0 && zz < g.D && yr >= 0 && yr < g.H;
+          rb[dz] = (((int64_t)(in_vol ? zz : 0) * g.H + (in_vol ? yr : 0)) * g.L + vl0) * C;
+          rok |= in_vol ? (1u << dz) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxCp; ++i) {
+          if (cp_dst[i] < 0) continue;
+          const int dz = (int)((cp_dz >> (2 * i)) & 3);
+          const int vl = vl0 + cp_sv[i] / C;
+          const bool ok = ((rok >> dz) & 1u) && vl >= 0 && vl < g.L;
+          const __nv_bfloat16* src = ok ? g.in + rb[dz] + cp_sv[i] : g.in;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sp + (unsigned)cp_dst[i]), "l"(src),
+                       "r"(ok ? 16 : 0)
+                       : "memory");
+        }
+        // The slot's barrier completes once every producer thread's copies have landed.
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&bars[B_FULL + slot]))
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == kMmaWarp) {
+    // ---------------- MMA ----------------
+    if (lane == 0) {
+      const unsigned idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(C >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
+      const unsigned sw_a = su32(sw), ring_a = su32(ring);
+      const unsigned lbo_a = (unsigned)g.S * 16u;
+      const uint64_t wd = desc(sw_a, 512u, 128u);  // + (t 2048 + ks 1024) / 16 per tap
+      int64_t nbase = 0;  // row sequence number of row y0 - 1 of the current item
+      int64_t k = 0;      // tile sequence number
+      bool stop = false;
+      for (int64_t item = blockIdx.x; item < g.items && !stop; item += gridDim.x) {
+        Walk wk;
+        wk.set(g, item);
+        for (int y = wk.y0; y < wk.y1; ++y, ++k) {
+          // rows y - 1, y, y + 1 have sequence numbers nbase + (y - y0) + {0, 1, 2}
+          const int64_t nr = nbase + (y - wk.y0);
+          bool ok = true;
+          for (int d = 0; d < 3 && ok; ++d) {
+            const int64_t m = nr + d;
+            // wait only for the newest row (the older two were waited for by earlier tiles)
+            if (d == 2 || y == wk.y0) ok = bar_wait(&bars[B_FULL + (int)(m % kRing)], (int)((m / kRing) & 1), abort);
+          }
+          const int as = (int)(k & 1);
+          if (ok && k >= 2) ok = bar_wait(&bars[B_ACCE + as], (int)(((k - 2) >> 1) & 1), abort);
+          if (!ok) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const unsigned dtm = tmem + (unsigned)(as * C);
+          // Descriptor of strip (row y - 1 + b, dz a); a tap adds its shift in
+          // 16-byte units to the address field (addresses stay below 256 KB).
+          uint64_t sd[3][3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const unsigned slot = (unsigned)((nr + b) % kRing);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sd[b][a] = desc(ring_a + (slot * 3u + a) * strip_bytes, lbo_a, 128u);
+          }
+#pragma unroll
           for (int t = 0; t < T; ++t) {
             const int a = t / 9, b = (t / 3) % 3, e = t % 3;
-            const unsigned strip = ring_a + (unsigned)((((y + b - 1) % kRing + kRing) % kRing) * 3 + a) * strip_bytes;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-              const uint64_t ad = desc(strip + (unsigned)(2 * ks) * g.S * 16u + (unsigned)(e * g.B) * 16u,
-                                       (unsigned)g.S * 16u, 128u);
-              const uint64_t bd = desc(sw_a + (unsigned)t * 2048u + (unsigned)(2 * ks) * 512u, 512u, 128u);
+              const uint64_t ad = sd[b][a] + (uint64_t)(2 * ks * g.S + e * g.B);
+              const uint64_t bd = wd + (uint64_t)(t * 128 + ks * 64);
               asm volatile(
                   "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0u : 1u));
-              first = 0;
+                  "l"(ad), "l"(bd), "r"(idesc), "r"((t | ks) ? 1u : 0u));
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bars[y & 1])));
+              su32(&bars[B_ACCF + as])));
+          // Rows whose last reader is this tile: y - 1, and at the column's end also y and y + 1.
+          const int nfree = (y == wk.y1 - 1) ? 3 : 1;
+          for (int d = 0; d < nfree; ++d)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&bars[B_EMPTY + (int)((nr + d) % kRing)])));
         }
-      }
-      if (y > y0) {
-        // Epilogue of tile y - 1.
-        const int yp = y - 1, sl = yp & 1;
-        const bool ok = __all_sync(0xffffffffu, wait_bar(su32(&bars[sl]), parity[sl]));
-        parity[sl] ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!ok) {
-          timed_out = true;
-        } else {
-          const int row = 32 * warp + lane;
-          const int vl = seg * kTile + row;
-          unsigned v[32];
-          const unsigned taddr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(sl * C);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-          if (vl < g.L) {
-            const int64_t vox = ((int64_t)z * g.H + yp) * g.L + vl;
-            float acc[C];
-            if (g.mask) {
-              float h[C];
-              load32(g.mask + vox * C, h);
-#pragma unroll
-              for (int c = 0; c < C; ++c) acc[c] = h[c] > 0.f ? __uint_as_float(v[c]) : 0.f;
-            } else {
-#pragma unroll
-              for (int c = 0; c < C; ++c) acc[c] = fmaxf(__uint_as_float(v[c]) + sbias[c], 0.f);
-            }
-            store32(g.out + vox * C, acc);
-          }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-      }
-      // Ring slot of row y - 2 is free for row y + 3: tile y - 1's MMAs (the
-      // last to read it) completed in the epilogue above, and at y0 the
-      // previous item's MMAs all completed before its end.
-      if (y < y1) load_row(g, ring, z, y + 3, seg, tid);
-      if (__syncthreads_or(timed_out)) {
-        timed_out = true;
-        break;
+        nbase += (wk.y1 - wk.y0) + 2;
       }
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int lq = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = 32 * lq + lane;
+    int64_t k = 0;
+    bool stop = false;
+    for (int64_t item = blockIdx.x; item < g.items && !stop; item += gridDim.x) {
+      Walk wk;
+      wk.set(g, item);
+      for (int y = wk.y0; y < wk.y1; ++y, ++k) {
+        const int as = (int)(k & 1);
+        const bool ok = __all_sync(0xffffffffu, bar_wait(&bars[B_ACCF + as], (int)((k >> 1) & 1), abort));
+        if (!ok) {
+          *abort = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        unsigned v[32];
+        const unsigned taddr = tmem + ((unsigned)(32 * lq) << 16) + (unsigned)(as * C);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        bar_arrive(&bars[B_ACCE + as]);  // the accumulator is free for tile k + 2
+        const int vl = wk.seg * kTile + row;
+        if (vl < g.L) {
+          const int64_t vox = ((int64_t)wk.z * g.H + y) * g.L + vl;
+          float acc[C];
+          if (g.mask) {
+            float h[C];
+            load32(g.mask + vox * C, h);
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = h[c] > 0.f ? __uint_as_float(v[c]) : 0.f;
+          } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = fmaxf(__uint_as_float(v[c]) + sbias[c], 0.f);
+          }
+          store32(g.out + vox * C, acc);
+        }
+      }
+    }
   }
-  if (timed_out && tid == 0 && timeout_flag) atomicExch(timeout_flag, 1);
   __syncthreads();
-  if (warp == 0) {
+  if (*abort && tid == 0 && timeout_flag) atomicExch(timeout_flag, 1);
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
   }
 }
 
-size_t smem_bytes(int S) { return 128 + (size_t)kWBytes + (size_t)kRing * 3 * 4 * S * 16 + 16 + 16 + C * 4; }
+size_t smem_bytes(int S) { return 128 + (size_t)kWBytes + (size_t)kRing * 3 * 4 * S * 16 + NBAR * 8 + 16 + C * 4; }
 
 }  // namespace tc
 
