@@ -65,6 +65,9 @@ struct Derived {
   __align__(16) __nv_bfloat16 w3f_tc[T * C * C];
   __align__(16) __nv_bfloat16 w2b_tc[T * C * C];
   __align__(16) __nv_bfloat16 w3b_tc[T * C * C];
+  // Layer 4 (32 -> 1) in the same layout with N padded to 16 rows (row 0 is
+  // the output channel, rows 1..15 zero): byte t 1024 + (i / 8) 256 + o 16 + (i % 8) 2.
+  __align__(16) __nv_bfloat16 w4f_tc[T * 16 * C];
 };
 
 // Address of a member of the device-resident Derived block.
@@ -306,7 +309,7 @@ constexpr int kProdWarps = 4, kEpiWarps = 4;
 constexpr int kMmaWarp = kProdWarps;
 constexpr int kThr = (kProdWarps + 1 + kEpiWarps) * 32;  // 288
 constexpr long long kWaitLimit = 1ll << 26;
-constexpr int kWBytes = T * C * C * 2;  // 55296
+constexpr int kWBytes = T * C * C * 2;  // 55296: weight tile of a 32 -> 32 layer (N = 32)
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -320,7 +323,9 @@ __device__ __forceinline__ uint64_t desc(unsigned saddr, unsigned lbo, unsigned 
 
 struct Args {
   const __nv_bfloat16* in;
-  __nv_bfloat16* out;
+  __nv_bfloat16* out;         // 32-channel output (N = 32)
+  float* out1;                // one-channel output (N = 16, row 0): (acc + bias[0]) * scale
+  const float* scale;         // device scalar or null
   const __nv_bfloat16* w;     // tensor-core layout, 27 x 2048 bytes
   const float* bias;          // forward: bias + ReLU; null: mask mode
   const __nv_bfloat16* mask;  // mask mode: out = acc * (mask > 0)
@@ -366,12 +371,15 @@ struct Walk {
   }
 };
 
+template <int NO>
 __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_flag) {
+  static_assert(NO == 32 || NO == 16, "output channels per MMA");
+  constexpr int kW = T * NO * C * 2;  // weight bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   unsigned char* sw = base;                                          // weights
-  unsigned char* ring = base + kWBytes;                              // kRing x 3 x 4 x S x 16
+  unsigned char* ring = base + kWBytes;                              // kRing x 3 x 4 x S x 16 (same offset for N = 16)
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kRing * 3 * 4 * g.S * 16);
   unsigned* tslot = reinterpret_cast<unsigned*>(bars + NBAR);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
@@ -379,7 +387,7 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned strip_bytes = 4u * g.S * 16u;
 
-  for (int k = tid; k < kWBytes / 16; k += kThr)
+  for (int k = tid; k < kW / 16; k += kThr)
     reinterpret_cast<uint4*>(sw)[k] = __ldg(reinterpret_cast<const uint4*>(g.w) + k);
   if (tid < C) sbias[tid] = g.bias ? g.bias[tid] : 0.f;
   if (tid == 0) {
@@ -395,7 +403,7 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(64));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(2 * NO));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     asm volatile("tcgen05.fence::before_thread_sync;");
   }
@@ -472,10 +480,10 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
     // ---------------- MMA ----------------
     if (lane == 0) {
       const unsigned idesc =
-          (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(C >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
+          (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NO >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
       const unsigned sw_a = su32(sw), ring_a = su32(ring);
       const unsigned lbo_a = (unsigned)g.S * 16u;
-      const uint64_t wd = desc(sw_a, 512u, 128u);  // + (t 2048 + ks 1024) / 16 per tap
+      const uint64_t wd = desc(sw_a, NO * 16u, 128u);  // + (t 64 NO + ks 32 NO) / 16 per tap
       int64_t nbase = 0;  // row sequence number of row y0 - 1 of the current item
       int64_t k = 0;      // tile sequence number
       bool stop = false;
@@ -498,7 +506,7 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const unsigned dtm = tmem + (unsigned)(as * C);
+          const unsigned dtm = tmem + (unsigned)(as * NO);
           // Descriptor of strip (row y - 1 + b, dz a); a tap adds its shift in
           // 16-byte units to the address field (addresses stay below 256 KB).
           uint64_t sd[3][3];
@@ -514,7 +522,7 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
               const uint64_t ad = sd[b][a] + (uint64_t)(2 * ks * g.S + e * g.B);
-              const uint64_t bd = wd + (uint64_t)(t * 128 + ks * 64);
+              const uint64_t bd = wd + (uint64_t)(t * 4 * NO + ks * 2 * NO);
               asm volatile(
                   "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
@@ -537,6 +545,7 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
     // ---------------- epilogue ----------------
     const int lq = warp & 3;  // TMEM lane quarter this warp may access
     const int row = 32 * lq + lane;
+    const float oscale = (NO == 16 && g.scale) ? *g.scale : 1.f;
     int64_t k = 0;
     bool stop = false;
     for (int64_t item = blockIdx.x; item < g.items && !stop; item += gridDim.x) {
@@ -551,8 +560,21 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
+        const unsigned taddr = tmem + ((unsigned)(32 * lq) << 16) + (unsigned)(as * NO);
+        if constexpr (NO == 16) {
+          unsigned v0;
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v0) : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          bar_arrive(&bars[B_ACCE + as]);
+          const int vl = wk.seg * kTile + row;
+          if (vl < g.L) {
+            const int64_t vox = ((int64_t)wk.z * g.H + y) * g.L + vl;
+            g.out1[vox] = (__uint_as_float(v0) + sbias[0]) * oscale;
+          }
+          continue;
+        }
         unsigned v[32];
-        const unsigned taddr = tmem + ((unsigned)(32 * lq) << 16) + (unsigned)(as * C);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -587,7 +609,7 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
   if (*abort && tid == 0 && timeout_flag) atomicExch(timeout_flag, 1);
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NO));
   }
 }
 
@@ -755,6 +777,11 @@ __global__ void prep_kernel(const float* __restrict__ p, Derived* __restrict__ d
     dw->w3f_tc[tc] = dw->w3f[k];
     dw->w2b_tc[tc] = dw->w2b[k];
     dw->w3b_tc[tc] = dw->w3b[k];
+  }
+  if (k < T * 16 * C) {
+    const int t = k / (16 * C), o = (k / C) % 16, i = k % C;
+    const float v = o == 0 ? p[kW4 + (int64_t)i * T + t] : 0.f;
+    dw->w4f_tc[t * 16 * C + (i / 8) * (8 * 16) + o * 8 + (i % 8)] = __float2bfloat16_rn(v);
   }
 }
 
@@ -924,11 +951,11 @@ tca_status conv32(tca_net_s* n, const __nv_bfloat16* in, const __nv_bfloat16* w,
     const size_t smem = tc::smem_bytes(g.S);
     static bool tc_attr = false;
     if (!tc_attr) {
-      cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(tc::conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       tc_attr = true;
     }
     const int grid = (int)std::min<int64_t>(g.items, (int64_t)std::max(1, n->num_sms));
-    tc::conv_tc_kernel<<<grid, tc::kThr, smem, s>>>(g, wait_timeout_flag());
+    tc::conv_tc_kernel<32><<<grid, tc::kThr, smem, s>>>(g, wait_timeout_flag());
     TCA_LAUNCH_CHECK();
     return TCA_OK;
   }
@@ -953,7 +980,24 @@ tca_status forward(tca_net_s* n, const float* u, float* y, const Dims& d, bool s
   TCA_LAUNCH_CHECK();
   TCA_TRY(conv32(n, n->h[0], DW(n, w2f), DW(n, w2f_tc), DW(n, b2), nullptr, n->h[1], d, s));
   TCA_TRY(conv32(n, n->h[1], DW(n, w3f), DW(n, w3f_tc), DW(n, b3), nullptr, n->h[2], d, s));
-  conv32to1_kernel<<<grid, kThreads, 0, s>>>(n->h[2], DW(n, w4f), DW(n, b4), scaled ? n->scale : nullptr, y, d);
+  if (tc_supported(d) && !n->force_cuda_cores) {
+    // Layer 4 on the tensor cores with N padded to 16 (one real output channel).
+    tc::Args g = tc_geometry(n, d);
+    g.in = n->h[2];
+    g.out1 = y;
+    g.scale = scaled ? n->scale : nullptr;
+    g.w = DW(n, w4f_tc);
+    g.bias = DW(n, b4);
+    static bool tc1_attr = false;
+    if (!tc1_attr) {
+      cudaFuncSetAttribute(tc::conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      tc1_attr = true;
+    }
+    const int tgrid = (int)std::min<int64_t>(g.items, (int64_t)std::max(1, n->num_sms));
+    tc::conv_tc_kernel<16><<<tgrid, tc::kThr, tc::smem_bytes(g.S), s>>>(g, wait_timeout_flag());
+  } else {
+    conv32to1_kernel<<<grid, kThreads, 0, s>>>(n->h[2], DW(n, w4f), DW(n, b4), scaled ? n->scale : nullptr, y, d);
+  }
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }
