@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) conv32to32_kernel(const __nv_bfloat1
 //   warps 0-3  producer: cp.async of the three strips of the next row into a
 //              free ring slot (zero fill at the volume's faces); completion
 //              arrives on the slot's mbarrier (cp.async.mbarrier.arrive);
-//   warp 4     MMA: one thread issues the 54 MMAs of a tile into one of two
+//   warp 4     MMA: an elected lane issues the 54 MMAs of a tile into one of two
 //              TMEM accumulators, commits to the accumulator's mbarrier and,
 //              for the row no later tile reads, to that ring slot's mbarrier;
 //   warps 5-8  epilogue: TMEM -> registers, bias + ReLU (forward) or the ReLU
@@ -356,6 +356,13 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, int parity, volatile int* 
   }
   *abort = 1;
   return false;
+}
+
+// tcgen05.commit of all prior MMAs to an mbarrier, issued by one elected lane.
+__device__ __forceinline__ void commit_elect(uint64_t* b) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\t"
+      "@p tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(su32(b)));
 }
 
 // Per-CTA walk over (item, row) in a fixed order shared by every role: item
@@ -450,22 +457,21 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
         const unsigned sp = su32(ring) + (unsigned)slot * 3u * strip_bytes;
         // Element offset of strip position 0 in each strip's row (z - 1, z, z + 1)
         // (negative for the first segment's halo) and whether that row exists.
-        int64_t rb[3];
-        unsigned rok = 0;
-#pragma unroll
-        for (int dz = 0; dz < 3; ++dz) {
-          const int zz = wk.z + dz - 1;
-          const bool in_vol = zz >= 0 && zz < g.D && yr >= 0 && yr < g.H;
-          rb[dz] = (((int64_t)(in_vol ? zz : 0) * g.H + (in_vol ? yr : 0)) * g.L + vl0) * C;
-          rok |= in_vol ? (1u << dz) : 0u;
-        }
+        // (Three named values, not an array: a runtime-indexed array would live in local memory.)
+        const bool yok = yr >= 0 && yr < g.H;
+        const bool ok0 = yok && wk.z >= 1, ok1 = yok, ok2 = yok && wk.z + 1 < g.D;
+        const int64_t rowb = ((int64_t)wk.z * g.H + (yok ? yr : 0)) * g.L + vl0;  // strip dz = 1
+        const int64_t zstep = (int64_t)g.H * g.L;
+        const int64_t rb0 = (rowb - zstep) * C, rb1 = rowb * C, rb2 = (rowb + zstep) * C;
 #pragma unroll
         for (int i = 0; i < kMaxCp; ++i) {
           if (cp_dst[i] < 0) continue;
           const int dz = (int)((cp_dz >> (2 * i)) & 3);
           const int vl = vl0 + cp_sv[i] / C;
-          const bool ok = ((rok >> dz) & 1u) && vl >= 0 && vl < g.L;
-          const __nv_bfloat16* src = ok ? g.in + rb[dz] + cp_sv[i] : g.in;
+          const bool rok = dz == 0 ? ok0 : (dz == 1 ? ok1 : ok2);
+          const int64_t rb = dz == 0 ? rb0 : (dz == 1 ? rb1 : rb2);
+          const bool ok = rok && vl >= 0 && vl < g.L;
+          const __nv_bfloat16* src = ok ? g.in + rb + cp_sv[i] : g.in;
           asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sp + (unsigned)cp_dst[i]), "l"(src),
                        "r"(ok ? 16 : 0)
                        : "memory");
@@ -478,7 +484,9 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kMmaWarp) {
     // ---------------- MMA ----------------
-    if (lane == 0) {
+    // The whole warp runs this loop so that the descriptors stay warp-uniform
+    // (uniform registers); one elected lane issues each tcgen05 instruction.
+    {
       const unsigned idesc =
           (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NO >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
       const unsigned sw_a = su32(sw), ring_a = su32(ring);
@@ -501,7 +509,8 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
           }
           const int as = (int)(k & 1);
           if (ok && k >= 2) ok = bar_wait(&bars[B_ACCE + as], (int)(((k - 2) >> 1) & 1), abort);
-          if (!ok) {
+          if (!__all_sync(0xffffffffu, ok)) {
+            *abort = 1;
             stop = true;
             break;
           }
@@ -524,18 +533,15 @@ __global__ void __launch_bounds__(kThr, 1) conv_tc_kernel(Args g, int* timeout_f
               const uint64_t ad = sd[b][a] + (uint64_t)(2 * ks * g.S + e * g.B);
               const uint64_t bd = wd + (uint64_t)(t * 4 * NO + ks * 2 * NO);
               asm volatile(
-                  "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+                  "{\n\t.reg .pred p, q;\n\telect.sync _|p, 0xffffffff;\n\tsetp.ne.u32 q, %4, 0;\n\t"
+                  "@p tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(dtm),
                   "l"(ad), "l"(bd), "r"(idesc), "r"((t | ks) ? 1u : 0u));
             }
           }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bars[B_ACCF + as])));
+          commit_elect(&bars[B_ACCF + as]);
           // Rows whose last reader is this tile: y - 1, and at the column's end also y and y + 1.
           const int nfree = (y == wk.y1 - 1) ? 3 : 1;
-          for (int d = 0; d < nfree; ++d)
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                su32(&bars[B_EMPTY + (int)((nr + d) % kRing)])));
+          for (int d = 0; d < nfree; ++d) commit_elect(&bars[B_EMPTY + (int)((nr + d) % kRing)]);
         }
         nbase += (wk.y1 - wk.y0) + 2;
       }
