@@ -144,48 +144,93 @@ constexpr int kThreads = 128;
 // ---- 1 -> 32 channels ------------------------------------------------------
 // Forward (layer 1): out = relu(sum_t w[t][co] * in[v + off t] * in_scale + b).
 // Input gradient of layer 4 (MASK): out = (sum_t w4b[t][ci] g[v + off t]) * (h3 > 0).
+// Register blocking: a thread owns four consecutive voxels and half of the 32
+// channels (64 accumulators), so each tap costs four input loads and four
+// 128-bit weight loads for 64 FMAs.
+constexpr int kV1 = 4;  // voxels per thread
+
 template <bool MASK>
 __global__ void __launch_bounds__(kThreads) conv1to32_kernel(const float* __restrict__ in,
                                                              const float* __restrict__ scale_dev,
                                                              const float* __restrict__ w, const float* __restrict__ bias,
                                                              const __nv_bfloat16* __restrict__ mask_src,
                                                              __nv_bfloat16* __restrict__ out, Dims d) {
-  __shared__ float sw[T * C];
+  __shared__ __align__(16) float sw[T * C];
   __shared__ float sb[C];
   for (int i = threadIdx.x; i < T * C; i += blockDim.x) sw[i] = w[i];
   if (threadIdx.x < C) sb[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
   __syncthreads();
   const float inv = scale_dev ? 1.f / *scale_dev : 1.f;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += (int64_t)gridDim.x * blockDim.x) {
-    int z, y, x;
-    decode(v, d, z, y, x);
-    const unsigned m = tap_mask(z, y, x, d);
-    float acc[C];
+  const int64_t nq = (d.V + kV1 - 1) / kV1;  // voxel quads
+  for (int64_t job = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; job < 2 * nq;
+       job += (int64_t)gridDim.x * blockDim.x) {
+    const int half = (int)(job & 1);  // channels 16 half .. 16 half + 15
+    const int64_t v0 = (job >> 1) * kV1;
+    unsigned m[kV1];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = sb[c];
-    for (int t = 0; t < T; ++t) {
-      if (!(m >> t & 1u)) continue;
-      const float val = __ldg(in + v + tap_offset(t, d)) * inv;
-      const float4* w4 = reinterpret_cast<const float4*>(sw + t * C);
-#pragma unroll
-      for (int q = 0; q < C / 4; ++q) {
-        const float4 ww = w4[q];
-        acc[4 * q + 0] = fmaf(ww.x, val, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(ww.y, val, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(ww.z, val, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(ww.w, val, acc[4 * q + 3]);
+    for (int u = 0; u < kV1; ++u) {
+      m[u] = 0u;
+      if (v0 + u < d.V) {
+        int z, y, x;
+        decode(v0 + u, d, z, y, x);
+        m[u] = tap_mask(z, y, x, d);
       }
     }
-    if constexpr (MASK) {
-      float h[C];
-      load32(mask_src + v * C, h);
+    float acc[kV1][16];
 #pragma unroll
-      for (int c = 0; c < C; ++c) acc[c] = h[c] > 0.f ? acc[c] : 0.f;
-    } else {
+    for (int u = 0; u < kV1; ++u)
 #pragma unroll
-      for (int c = 0; c < C; ++c) acc[c] = fmaxf(acc[c], 0.f);
+      for (int c = 0; c < 16; ++c) acc[u][c] = sb[16 * half + c];
+#pragma unroll 1
+    for (int t = 0; t < T; ++t) {
+      const int64_t off = tap_offset(t, d);
+      float val[kV1];
+#pragma unroll
+      for (int u = 0; u < kV1; ++u) val[u] = (m[u] >> t & 1u) ? __ldg(in + v0 + u + off) * inv : 0.f;
+      const float4* w4 = reinterpret_cast<const float4*>(sw + t * C + 16 * half);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 ww = w4[q];
+#pragma unroll
+        for (int u = 0; u < kV1; ++u) {
+          acc[u][4 * q + 0] = fmaf(ww.x, val[u], acc[u][4 * q + 0]);
+          acc[u][4 * q + 1] = fmaf(ww.y, val[u], acc[u][4 * q + 1]);
+          acc[u][4 * q + 2] = fmaf(ww.z, val[u], acc[u][4 * q + 2]);
+          acc[u][4 * q + 3] = fmaf(ww.w, val[u], acc[u][4 * q + 3]);
+        }
+      }
     }
-    store32(out + v * C, acc);
+#pragma unroll
+    for (int u = 0; u < kV1; ++u) {
+      if (v0 + u >= d.V) break;
+      const int64_t v = v0 + u;
+      if constexpr (MASK) {
+        const uint4* hs = reinterpret_cast<const uint4*>(mask_src + v * C + 16 * half);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint4 hw = __ldg(hs + q);
+          const uint32_t hv[4] = {hw.x, hw.y, hw.z, hw.w};
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if (!(bf_lo(hv[r]) > 0.f)) acc[u][8 * q + 2 * r] = 0.f;
+            if (!(bf_hi(hv[r]) > 0.f)) acc[u][8 * q + 2 * r + 1] = 0.f;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[u][c] = fmaxf(acc[u][c], 0.f);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(out + v * C + 16 * half);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint4 o;
+        o.x = pack2(acc[u][8 * q + 0], acc[u][8 * q + 1]);
+        o.y = pack2(acc[u][8 * q + 2], acc[u][8 * q + 3]);
+        o.z = pack2(acc[u][8 * q + 4], acc[u][8 * q + 5]);
+        o.w = pack2(acc[u][8 * q + 6], acc[u][8 * q + 7]);
+        dst[q] = o;
+      }
+    }
   }
 }
 
