@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) conv1to32_kernel(const float* __rest
     for (int u = 0; u < kV1; ++u)
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc[u][c] = sb[16 * half + c];
-#pragma unroll 1
+#pragma unroll 9
     for (int t = 0; t < T; ++t) {
       const int64_t off = tap_offset(t, d);
       float val[kV1];
