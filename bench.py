@@ -31,6 +31,10 @@ SHAPE = (160, 160, 160, 8)
 SEED = 2
 LAM = 1e-3
 RTOL = 1e-6
+# DRAM bytes (read + written) of one launch of the CG sweep kernel at this workload,
+# counted by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the current kernel;
+# to be re-measured (or set to None) whenever that kernel changes.
+K2_TRAFFIC_BYTES = 512_350_000
 SUBVOL = (40, 40, 40, 8)  # iteration-count probe for the oracle arm (same generator)
 WORKLOAD = ("bspline4d: unknowns 160x160x160x8 (32.8M) FP32, cubic B-spline factors on 240x240x240x12 "
             "jittered samples, lambda 1e-3, noise 0.01, CG to true rel. residual 1e-6")
@@ -591,7 +595,8 @@ def run_tca(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "fused normal-operator CG sweep (p = r + beta p; q = K p; <p,q>)",
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": K2_TRAFFIC_BYTES if not args.small else None,
                      "peak_source": peak_src, "avg_launch_ms": round(k2_ms, 5),
                      "algorithmic_bytes": k2_bytes, "launches": sweep_n},
         "sweeps": sweeps,
