@@ -73,9 +73,40 @@ __device__ __forceinline__ float* align128(unsigned char* p) {
 struct RowGeom {
   int64_t O, I, i_chunks, tiles;
   int n_in, n_out, W, Ti, To, RB, j_chunks, stage_floats, stages;
+  int unit;  // 7-wide band with start[j] = start[0] + j: sliding-window path
 };
 
-__global__ void __launch_bounds__(kThreads) band_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+// Sliding window over consecutive outputs of a unit-step 7-wide band: the JPG
+// outputs j0 .. j0 + JPG - 1 of a thread read rows rs .. rs + JPG + 5 of the
+// tile once (JPG + 6 loads instead of 7 JPG).
+template <int JPG>
+__device__ __forceinline__ void rows_window7(const float* ts, int Ti, int RB, int rs, int j0, int n_out,
+                                             const float* __restrict__ w, float* yo, int64_t I, bool ok) {
+  float4 win[JPG + 6];
+  // Rows past the tile (RB rows) only feed outputs past n_out: never read them.
+#pragma unroll
+  for (int q = 0; q < JPG + 6; ++q)
+    win[q] = rs + q < RB ? *reinterpret_cast<const float4*>(ts + (size_t)(rs + q) * Ti) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < JPG; ++q) {
+    const int j = j0 + q;
+    if (j >= n_out) break;
+    const float* wj = w + (int64_t)j * 7;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < 7; ++e) {
+      const float c = __ldg(wj + e);
+      acc.x = fmaf(c, win[q + e].x, acc.x);
+      acc.y = fmaf(c, win[q + e].y, acc.y);
+      acc.z = fmaf(c, win[q + e].z, acc.z);
+      acc.w = fmaf(c, win[q + e].w, acc.w);
+    }
+    if (ok) *reinterpret_cast<float4*>(yo + (int64_t)j * I) = acc;
+  }
+}
+
+template <bool UNIT>
+__global__ void __launch_bounds__(kThreads, 3) band_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              float* __restrict__ y, RowGeom g,
                                                              const int32_t* __restrict__ start,
                                                              const float* __restrict__ w) {
@@ -127,7 +158,16 @@ __global__ void __launch_bounds__(kThreads) band_rows_kernel(const __grid_consta
     const bool ok = arrived && grp < groups && o < g.O && i < g.I;
     const float* ts = base + buf * g.stage_floats + (size_t)oo * g.RB * g.Ti + 4 * v;
     float* yo = y + o * (int64_t)g.n_out * g.I + i;
-    if (grp < groups) {
+    if (UNIT && grp < groups && (groups == 8 || groups == 4)) {
+      // Contiguous outputs per thread group (kJB / groups = 4 or 8 of them).
+      const int jpg = kJB / groups;
+      const int jg = j0 + grp * jpg;
+      const int rs = start[min(jg, g.n_out - 1)] - r0;
+      if (jg < g.n_out) {
+        if (jpg == 4) rows_window7<4>(ts, g.Ti, g.RB, rs, jg, g.n_out, w, yo, g.I, ok);
+        else rows_window7<8>(ts, g.Ti, g.RB, rs, jg, g.n_out, w, yo, g.I, ok);
+      }
+    } else if (grp < groups) {
       for (int jj = grp; jj < kJB; jj += groups) {
         const int j = j0 + jj;
         if (j >= g.n_out) break;
@@ -313,6 +353,7 @@ tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t 
   g.j_chunks = (n_out + kJB - 1) / kJB;
   g.tiles = ((O + To - 1) / To) * g.i_chunks * g.j_chunks;
   g.stage_floats = ((Ti * RB * To + 31) / 32) * 32;
+  g.unit = band.unit && W == 7;
   // Measured on GB300 (160^3 x 8 Gram and collocation sweeps): three persistent
   // CTAs per SM with a 3-deep ring beat one tile per CTA and deeper rings.
   static const int per_sm = env_int("TCA_ROWS_CTAS_PER_SM", 3);
@@ -325,10 +366,14 @@ tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t 
   const size_t sm = sizeof(float) * (size_t)g.stages * g.stage_floats + 128 + 8 * g.stages;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(band_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(band_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(band_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  band_rows_kernel<<<(unsigned)grid, kThreads, sm, s>>>(tmap, y, g, band.start, band.w32);
+  if (g.unit)
+    band_rows_kernel<true><<<(unsigned)grid, kThreads, sm, s>>>(tmap, y, g, band.start, band.w32);
+  else
+    band_rows_kernel<false><<<(unsigned)grid, kThreads, sm, s>>>(tmap, y, g, band.start, band.w32);
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }

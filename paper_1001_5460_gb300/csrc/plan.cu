@@ -232,6 +232,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     gb.n_in = n;
     gb.W = 2 * kGramHalf + 1;
     gb.rows32 = (int)std::min<int64_t>(n, 32) - 1 + gb.W;
+    gb.unit = true;
     TCA_TRY(dmalloc(&gb.start, n));
     TCA_TRY(dmalloc(&gb.w64, n * 7));
     TCA_TRY(dmalloc(&gb.w32, n * 7));
@@ -281,6 +282,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
   lb.n_in = n;
   lb.W = 2 * kLapHalf + 1;
   lb.rows32 = (int)std::min<int64_t>(n, 32) - 1 + lb.W;
+  lb.unit = true;
   TCA_TRY(dmalloc(&lb.start, n));
   TCA_TRY(dmalloc(&lb.w64, n * 5));
   TCA_TRY(dmalloc(&lb.w32, n * 5));

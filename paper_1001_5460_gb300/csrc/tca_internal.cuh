@@ -27,6 +27,7 @@ struct Band {
   double* w64 = nullptr;     // device, n_out * W
   float2* wff = nullptr;     // device, n_out * W: w64 split into (hi, lo) floats
   int rows32 = 0;            // input rows spanned by any 32 consecutive outputs (TMA tile height)
+  bool unit = false;         // start[j] = start[0] + j (Gram and regulariser bands)
 };
 
 // Row-major n_out x n_in matrix.
