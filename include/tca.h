@@ -155,7 +155,7 @@ typedef struct {
   int32_t x0_given;     /* 1: x holds the initial guess; 0: start from x = 0 */
   double inner_rtol;    /* _IR plans: relative tolerance of each inner solve (0: default 1e-3) */
   int32_t max_refine;   /* _IR plans: cap on refinement steps (0: default 30) */
-  int32_t check_every;  /* iterations between host convergence reads (0: default 16) */
+  int32_t check_every;  /* iterations between host convergence reads (0: default 16; rounded up to a multiple of 4) */
   int32_t profile;      /* 1: time every normal-operator sweep with CUDA events (info->sweep_*) */
 } tca_solve_opts;
 
@@ -178,7 +178,11 @@ typedef struct {
  * from the current x.  b: m-shaped data, x: n-shaped solution (in: initial
  * guess when opts->x0_given).  Scalars alpha, beta and all inner products are
  * kept in FP64 on the device; the host reads the convergence flag every
- * check_every iterations.  Returns TCA_ERR_NOT_CONVERGED (x and info still
+ * check_every iterations.  The update C += alpha P is applied once per four
+ * iterations from the four directions kept meanwhile (the same terms in the
+ * same order and rounding as one update per iteration; a group cut short by
+ * the stop test is completed before the true residual is formed), so x is
+ * read and written a quarter as often.  Returns TCA_ERR_NOT_CONVERGED (x and info still
  * filled) when max_iter is reached, TCA_ERR_BREAKDOWN when <P, Q> <= 0 or a
  * scalar is not finite.  info may be NULL.  Synchronises the stream. */
 TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,

@@ -29,11 +29,30 @@ template <typename T> struct V2;
 template <> struct V2<float> { using t = float4; static constexpr int n = 4; };
 template <> struct V2<double> { using t = double2; static constexpr int n = 2; };
 
-// x += alpha p;  r -= alpha q;  rho1 = <r, r>  (Fig. 2 update block) -> beta, stop test.
+// r -= alpha q;  rho1 = <r, r>  (Fig. 2 update block) -> beta, stop test, and
+// the solution update x += alpha p grouped over kDirBufs iterations: the
+// iterations at group positions 0 .. kDirBufs - 2 only record alpha (their
+// directions stay in their own buffers); the last position applies
+//   x += alpha_0 p_0;  x += alpha_1 p_1;  ...;  x += alpha p
+// in iteration order, one rounding per term, the same values as one update
+// per iteration, for a quarter of the x traffic.
 template <typename T>
+struct DirBufs {
+  const T* p[kDirBufs];  // direction written at group position i: p[(i + 1) % kDirBufs]
+};
+
+template <typename T>
+__device__ __forceinline__ T group_x_update(T x, const T* __restrict__ const* pb, const double* ah, T alpha, T pnew,
+                                            int64_t i, int npend) {
+  for (int k = 0; k < npend; ++k) x = fma((T)ah[k], pb[k + 1][i], x);
+  return fma(alpha, pnew, x);
+}
+
+template <typename T, bool XUPD>
 __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
                                                                 const T* __restrict__ p, const T* __restrict__ q,
-                                                                int64_t n, Scalars* sc, Reduce red) {
+                                                                int64_t n, Scalars* sc, Reduce red, DirBufs<T> pb,
+                                                                int pos) {
   __shared__ double sh[kVecThreads / 32];
   if (cg_done(sc)) return;
   const double alpha_d = sc->alpha;
@@ -41,24 +60,40 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ 
   using VT = typename V2<T>::t;
   constexpr int VN = V2<T>::n;
   const int64_t nv = n / VN;
+  T ah[kDirBufs - 1];
+  if constexpr (XUPD) {
+#pragma unroll
+    for (int k = 0; k < kDirBufs - 1; ++k) ah[k] = (T)sc->alpha_hist[k];
+  }
   T part = T(0);
   double acc = 0.0;
   int cnt = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-    VT xv = reinterpret_cast<VT*>(x)[i];
     VT rv = reinterpret_cast<VT*>(r)[i];
-    const VT pv = reinterpret_cast<const VT*>(p)[i];
     const VT qv = reinterpret_cast<const VT*>(q)[i];
+    if constexpr (XUPD) {
+      VT xv = reinterpret_cast<VT*>(x)[i];
+      T* xs = reinterpret_cast<T*>(&xv);
+#pragma unroll
+      for (int k = 0; k < kDirBufs - 1; ++k) {
+        const VT pv = reinterpret_cast<const VT*>(pb.p[k + 1])[i];
+        const T* ps = reinterpret_cast<const T*>(&pv);
+#pragma unroll
+        for (int c = 0; c < VN; ++c) xs[c] = fma(ah[k], ps[c], xs[c]);
+      }
+      const VT pv = reinterpret_cast<const VT*>(p)[i];
+      const T* ps = reinterpret_cast<const T*>(&pv);
+#pragma unroll
+      for (int c = 0; c < VN; ++c) xs[c] = fma(alpha, ps[c], xs[c]);
+      reinterpret_cast<VT*>(x)[i] = xv;
+    }
     if constexpr (VN == 4) {
-      xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
       rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
       part += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
     } else {
-      xv.x += alpha * pv.x; xv.y += alpha * pv.y;
       rv.x -= alpha * qv.x; rv.y -= alpha * qv.y;
       part += rv.x * rv.x + rv.y * rv.y;
     }
-    reinterpret_cast<VT*>(x)[i] = xv;
     reinterpret_cast<VT*>(r)[i] = rv;
     if (++cnt == 8) {  // short FP32 runs, FP64 beyond
       acc += (double)part;
@@ -68,7 +103,7 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ 
   }
   if (blockIdx.x == 0) {
     for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) {
-      x[i] += alpha * p[i];
+      if constexpr (XUPD) x[i] = group_x_update<T>(x[i], pb.p, sc->alpha_hist, alpha, p[i], i, kDirBufs - 1);
       r[i] -= alpha * q[i];
       part += r[i] * r[i];
     }
@@ -81,9 +116,34 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ 
     sc->beta = total / rho;
     sc->rho = total;
     sc->iters += 1;
+    if constexpr (XUPD) {
+      sc->npend = 0;
+    } else {
+      sc->alpha_hist[pos] = alpha_d;
+      sc->npend = pos + 1;
+    }
     if (!isfinite(total)) sc->breakdown = 1;
     if (sqrt(total) <= sc->rtol * sc->bnorm) sc->converged = 1;
   }
+}
+
+// The part of a group's solution update still pending when the iteration loop
+// stops (converged, broken down or out of iterations part-way through a group):
+// x += alpha_k p_k for the npend recorded positions, then npend = 0.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cg_flush_x_kernel(T* __restrict__ x, int64_t n, Scalars* sc,
+                                                                 Reduce red, DirBufs<T> pb) {
+  __shared__ double sh[kVecThreads / 32];
+  const int np = sc->npend;
+  if (np > 0) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      T xv = x[i];
+      for (int k = 0; k < np; ++k) xv = fma((T)sc->alpha_hist[k], pb.p[k + 1][i], xv);
+      x[i] = xv;
+    }
+  }
+  double total;
+  if (dev::grid_sum_last(0.0, red, &total, sh)) sc->npend = 0;
 }
 
 // P_new = R + beta P_old (used when the normal operator is not the fused sweep).
@@ -178,6 +238,7 @@ __global__ void cg_setup_kernel(Scalars* sc, double rtol, int max_iter) {
   sc->breakdown = 0;
   sc->beta = 0.0;
   sc->alpha = 0.0;
+  sc->npend = 0;
 }
 
 }  // namespace
@@ -196,12 +257,24 @@ static Reduce first_reduce(const tca_plan_s* p) {
   return r;
 }
 
-// One CG iteration.  ev_begin/ev_end (may be null) bracket the normal-operator
-// sweep so that a profiled solve can time it on the device.
 template <typename T>
-static tca_status enqueue_iteration(tca_plan_s* p, T* x, const T* pold, T* pnew, cudaStream_t s,
-                                    cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+static DirBufs<T> dir_bufs(const tca_plan_s* p) {
+  DirBufs<T> d;
+  for (int k = 0; k < kDirBufs; ++k) d.p[k] = (const T*)p->p[k];
+  return d;
+}
+
+// One CG iteration at position `it` of a graph replay (replays hold a multiple
+// of kDirBufs iterations, so it % kDirBufs is the position in the update
+// group).  ev_begin/ev_end (may be null) bracket the normal-operator sweep so
+// that a profiled solve can time it on the device.
+template <typename T>
+static tca_status enqueue_iteration(tca_plan_s* p, T* x, int it, cudaStream_t s, cudaEvent_t ev_begin,
+                                    cudaEvent_t ev_end) {
   const int64_t N = p->N;
+  const int pos = it % kDirBufs;
+  const T* pold = (const T*)p->p[pos];
+  T* pnew = (T*)p->p[(pos + 1) % kDirBufs];
   T* r = (T*)p->r;
   T* q = (T*)p->q;
   const int grid = std::min(vector_grid(p, N), first_reduce(p).max_blocks);
@@ -218,7 +291,22 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, const T* pold, T* pnew,
     TCA_LAUNCH_CHECK();
   }
   if (ev_end) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_end, s, cudaEventRecordExternal));
-  cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p));
+  if (pos == kDirBufs - 1)
+    cg_update_kernel<T, true><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p), dir_bufs<T>(p),
+                                                           pos);
+  else
+    cg_update_kernel<T, false><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p),
+                                                            dir_bufs<T>(p), pos);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+// Apply the part of the grouped solution update still pending after the
+// iteration loop.
+template <typename T>
+static tca_status flush_pending_x(tca_plan_s* p, T* x, cudaStream_t s) {
+  const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
+  cg_flush_x_kernel<T><<<grid, kVecThreads, 0, s>>>(x, p->N, p->scal, first_reduce(p), dir_bufs<T>(p));
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }
@@ -229,8 +317,7 @@ static tca_status ensure_solver_buffers(tca_plan_s* p) {
   const size_t bytes = sizeof(T) * (size_t)p->N;
   cudaError_t e = cudaMalloc(&p->rhs, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->r, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->p[0], bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->p[1], bytes);
+  for (int k = 0; k < kDirBufs && e == cudaSuccess; ++k) e = cudaMalloc(&p->p[k], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->q, bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->res64, sizeof(double) * (size_t)p->N);
   if (e == cudaSuccess && sizeof(T) == 4) e = cudaMalloc((void**)&p->rhs64, sizeof(double) * (size_t)p->N);
@@ -241,8 +328,8 @@ static tca_status ensure_solver_buffers(tca_plan_s* p) {
   return TCA_OK;
 }
 
-// Build (or reuse) the graph of `iters` iterations (an even count: the two
-// direction buffers alternate) for this x buffer.
+// Build (or reuse) the graph of `iters` iterations (a multiple of kDirBufs:
+// the direction buffers rotate) for this x buffer.
 template <typename T>
 static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaStream_t s) {
   if (p->graph_exec && p->graph_x == x && p->graph_iters == iters && p->graph_profiled == profile) return TCA_OK;
@@ -261,9 +348,7 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
   tca_status st = TCA_OK;
   if (e == cudaSuccess) {
     for (int it = 0; it < iters && st == TCA_OK; ++it) {
-      const T* pold = (const T*)p->p[it & 1];
-      T* pnew = (T*)p->p[(it + 1) & 1];
-      st = enqueue_iteration<T>(p, x, pold, pnew, cs, profile ? p->sweep_ev[2 * it] : nullptr,
+      st = enqueue_iteration<T>(p, x, it, cs, profile ? p->sweep_ev[2 * it] : nullptr,
                                 profile ? p->sweep_ev[2 * it + 1] : nullptr);
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -374,7 +459,7 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
   const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
   const int max_refine = (o && o->max_refine > 0) ? o->max_refine : 30;
   int every = (o && o->check_every > 0) ? o->check_every : 16;
-  every = std::max(2, (every + 1) / 2 * 2);
+  every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
   const bool profile = o && o->profile;
   if (profile) every = std::min(every, kMaxProfiledIters);
   if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
@@ -413,6 +498,7 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
                                                           first_reduce(p), 1, second_reduce(p));
     TCA_LAUNCH_CHECK();
     TCA_TRY(cg_iterate(p, inner, max_iter - total, every, profile, &sweep_ms, &sweep_n, s));
+    TCA_TRY(flush_pending_x<float>(p, d, s));
     total += hs->iters;
     rec = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho, 0.0)) / hs->bnorm : 0.0;
     if (hs->breakdown) {
@@ -445,7 +531,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
   const bool x0 = o && o->x0_given;
   int every = (o && o->check_every > 0) ? o->check_every : 16;
-  every = std::max(2, (every + 1) / 2 * 2);
+  every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
   const bool profile = o && o->profile;
   if (profile) every = std::min(every, kMaxProfiledIters);
   if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
@@ -489,6 +575,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   Scalars* hs = p->scal_host;
   for (;;) {
     TCA_TRY(cg_iterate(p, rtol, max_iter, every, profile, &sweep_ms, &sweep_n, s));
+    TCA_TRY(flush_pending_x<T>(p, x, s));
     if (hs->breakdown) {
       status = TCA_ERR_BREAKDOWN;
       break;
@@ -722,6 +809,7 @@ tca_status build_batch(int count, tca_plan_s** plans, const float* const* b, flo
       TCA_LAUNCH_CHECK();
       TCA_TRY(capture_while(s, hi, &inner));
       const uint64_t l0 = tca_kernel_launches(0);
+      TCA_TRY(flush_pending_x<float>(p, x[i], s));
       TCA_TRY(residual_ff(p, x[i], reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
                           (float*)p->r, first_reduce(p), second_reduce(p), s));
       const int vgrid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
@@ -736,8 +824,7 @@ tca_status build_batch(int count, tca_plan_s** plans, const float* const* b, flo
     st = capture_into(inner, cs, [&](cudaStream_t s) -> tca_status {
       const uint64_t l0 = tca_kernel_launches(0);
       for (int it = 0; it < every; ++it)
-        TCA_TRY(enqueue_iteration<float>(p, x[i], (const float*)p->p[it & 1], (float*)p->p[(it + 1) & 1], s,
-                                         nullptr, nullptr));
+        TCA_TRY(enqueue_iteration<float>(p, x[i], it, s, nullptr, nullptr));
       bg->l_iter[i] = (tca_kernel_launches(0) - l0) / every;
       cond_running_kernel<<<1, 1, 0, s>>>(p->scal, hi);
       TCA_LAUNCH_CHECK();
@@ -766,7 +853,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
   const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
   const bool x0 = o && o->x0_given;
   int every = (o && o->check_every > 0) ? o->check_every : 16;
-  every = std::max(2, (every + 1) / 2 * 2);
+  every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
   if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     TCA_TRY(ensure_solver_buffers<float>(plans[i]));

@@ -323,8 +323,7 @@ static void destroy_plan(tca_plan_s* p) {
   cudaFree(p->ws64[1]);
   cudaFree(p->rhs);
   cudaFree(p->r);
-  cudaFree(p->p[0]);
-  cudaFree(p->p[1]);
+  for (int k = 0; k < kDirBufs; ++k) cudaFree(p->p[k]);
   cudaFree(p->q);
   cudaFree(p->rhs64);
   cudaFree(p->res64);

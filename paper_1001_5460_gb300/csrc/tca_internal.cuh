@@ -16,6 +16,7 @@ constexpr int kGramHalf = 3;  // G_k = A_k^T A_k of a 4-wide band is 7-banded
 constexpr int kLapHalf = 2;   // D2^T D2 is 5-banded
 constexpr int kMaxBandW = 16; // widest transposed ELL4 band accepted
 constexpr int kMaxProfiledIters = 64;  // iterations per graph replay when sweeps are timed
+constexpr int kDirBufs = 4;            // CG direction buffers; x is updated once per kDirBufs iterations
 
 // y[o] = sum_{e < W} w[o*W + e] * x[start[o] + e]; indices outside [0, n_in)
 // carry weight 0 in w and are skipped by the kernels.
@@ -76,6 +77,11 @@ struct Scalars {
   int32_t max_iter;  // kernels of an iteration skip their work once iters reaches it
   int32_t restarts;  // device-side restarts from the true residual (batched solve)
   int32_t pad;
+  // Grouped solution update: alpha of the first npend positions of the
+  // current group of kDirBufs iterations, whose x += alpha p is still pending.
+  double alpha_hist[kDirBufs - 1];
+  int32_t npend;
+  int32_t pad2;
 };
 
 // True once the iteration loop must stop doing work (converged, broken down or
@@ -116,7 +122,7 @@ struct tca_plan_s {
   // Solver vectors (element type of the plan), allocated on first solve.
   void* rhs = nullptr;
   void* r = nullptr;
-  void* p[2] = {nullptr, nullptr};
+  void* p[tca::kDirBufs] = {};
   void* q = nullptr;
   double* rhs64 = nullptr;
   double* res64 = nullptr;

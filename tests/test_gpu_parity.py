@@ -201,6 +201,29 @@ def test_solve_with_initial_guess_and_max_iter():
     assert full_iters > 5
 
 
+@pytest.mark.parametrize("shape,prec,tol", [((20, 18, 16, 8), "f32", 1e-4),   # fused sweep
+                                             ((19, 12, 15, 4), "f32", 1e-4),   # fused sweep, n4 = 4
+                                             ((17, 14, 19, 3), "f64", 1e-10)])  # generic FP64 path
+def test_partial_iterates_match_oracle(shape, prec, tol):
+    """x after k CG iterations (max_iter = k) equals the oracle's k-th iterate.
+
+    The solution update is applied once per group of four iterations; k = 1 .. 9
+    stops at every position of a group, so a term left out, applied twice or
+    taken with the wrong direction shows as an O(1) error here."""
+    tca = lib()
+    dt = np.float32 if prec == "f32" else np.float64
+    inst = synth.instance_bspline(shape, seed=650, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(dt)
+    plan = tca.plan_from_instance(inst, precision=prec)
+    for k in range(1, 10):
+        x = empty_dev(inst.shape, dt)
+        st, info = plan.solve(to_dev(b, dt), x, rtol=1e-14, max_iter=k, raise_on_error=False)
+        assert st == tca.ERR_NOT_CONVERGED and info["iters"] == k
+        ref = O.solve(b.astype(np.float64), mats, inst.lam, rtol=0.0, max_iter=k).x
+        assert rel_l2(x.cpu().numpy(), ref) < tol, k
+
+
 def test_zero_rhs():
     tca = lib()
     inst = synth.instance_bspline((10, 9, 8, 4), seed=700, with_truth=False)
