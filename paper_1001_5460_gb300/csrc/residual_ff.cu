@@ -47,7 +47,8 @@ template <> __device__ __forceinline__ float2 as_ff<float>(float v) { return mak
 template <> __device__ __forceinline__ float2 as_ff<float2>(float2 v) { return v; }
 
 // Mode product on the inner layout (I >= 32): lanes along the contiguous inner
-// index, 8 outputs along the mode per thread.
+// index, JT outputs along the mode per thread, their accumulators advanced
+// together so that each tap step has JT independent loads in flight.
 template <typename Tin>
 __global__ void __launch_bounds__(256) band_ff_inner_kernel(const Tin* __restrict__ x, float2* __restrict__ y,
                                                             float* __restrict__ y32, int64_t O, int n_in, int n_out,
@@ -63,62 +64,251 @@ __global__ void __launch_bounds__(256) band_ff_inner_kernel(const Tin* __restric
   const int64_t i = ic * 64 + threadIdx.x;
   if (i >= I) return;
   const Tin* xo = x + o * (int64_t)n_in * I + i;
-#pragma unroll 1
+  int s0[JT];
+  bool jv[JT];
+#pragma unroll
   for (int t = 0; t < JT; ++t) {
     const int j = jc * (4 * JT) + threadIdx.y + 4 * t;
-    if (j >= n_out) break;
-    Acc2 acc;
-    const int s0 = start[j];
-    for (int e = 0; e < W; ++e) {
-      const int l = s0 + e;
-      if (l < 0 || l >= n_in) continue;
-      const float2 c = w[(int64_t)j * W + e];
-      const float2 v = as_ff(xo[(int64_t)l * I]);
-      acc.add(c.x, c.y, v.x, v.y);
+    jv[t] = j < n_out;
+    s0[t] = jv[t] ? start[j] : 0;
+  }
+  Acc2 acc[JT];
+#pragma unroll 1
+  for (int e = 0; e < W; ++e) {
+#pragma unroll
+    for (int t = 0; t < JT; ++t) {
+      const int j = jc * (4 * JT) + threadIdx.y + 4 * t;
+      const int l = s0[t] + e;
+      const bool ok = jv[t] && l >= 0 && l < n_in;
+      // A zero coefficient leaves the accumulator exactly unchanged.
+      const float2 c = ok ? w[(int64_t)j * W + e] : make_float2(0.f, 0.f);
+      const float2 v = ok ? as_ff(xo[(int64_t)l * I]) : make_float2(0.f, 0.f);
+      acc[t].add(c.x, c.y, v.x, v.y);
     }
-    const float2 r = acc.result();
+  }
+#pragma unroll
+  for (int t = 0; t < JT; ++t) {
+    if (!jv[t]) continue;
+    const int j = jc * (4 * JT) + threadIdx.y + 4 * t;
+    const float2 r = acc[t].result();
     const int64_t oi = (o * (int64_t)n_out + j) * I + i;
     y[oi] = r;
     if (y32) y32[oi] = r.x;
   }
 }
 
-// Mode product on the outer layout (I < 32): whole (n_in x I) slabs staged in
-// shared memory.
+// Four consecutive elements (16-byte aligned) as double-float pairs.
+__device__ __forceinline__ void load4_ff(const float* p, float2 (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = make_float2(a.x, 0.f); v[1] = make_float2(a.y, 0.f);
+  v[2] = make_float2(a.z, 0.f); v[3] = make_float2(a.w, 0.f);
+}
+__device__ __forceinline__ void load4_ff(const float2* p, float2 (&v)[4]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0];
+  const float4 b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+}
+
+// One output row j over four lanes: acc[q] += sum_e w[j][e] x[start[j] + e][q],
+// x given by a row pointer and a row pitch.  Rows outside [0, n_in) are
+// skipped; a window wholly inside (the common case) runs unpredicated.
 template <typename Tin>
-__global__ void __launch_bounds__(256) band_ff_outer_kernel(const Tin* __restrict__ x, float2* __restrict__ y,
-                                                            float* __restrict__ y32, int64_t O, int n_in, int n_out,
-                                                            int I, const int32_t* __restrict__ start,
-                                                            const float2* __restrict__ w, int W, int To) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* xs = reinterpret_cast<float2*>(smem_raw);
-  const int64_t o0 = (int64_t)blockIdx.x * To;
-  const int to = (int)((O - o0) < (int64_t)To ? (O - o0) : (int64_t)To);
-  const int sin = n_in * I, sout = n_out * I;
-  const Tin* xsrc = x + o0 * sin;
-  for (int t = threadIdx.x; t < to * sin; t += blockDim.x) xs[t] = as_ff(xsrc[t]);
-  __syncthreads();
-  const int lanes = to * I;
-  for (int t = threadIdx.x; t < lanes * n_out; t += blockDim.x) {
-    const int j = t / lanes;
-    const int lane = t - j * lanes;
-    const int oo = lane / I;
-    const int ii = lane - oo * I;
-    const float2* xf = xs + oo * sin + ii;
-    Acc2 acc;
-    const int s0 = start[j];
+__device__ __forceinline__ void taps4(Acc2 (&acc)[4], const Tin* x0, int64_t pitch, int s0, int W, int n_in,
+                                      const float2* __restrict__ wj) {
+  if (s0 >= 0 && s0 + W <= n_in) {
+    const Tin* xr = x0 + (int64_t)s0 * pitch;
+#pragma unroll 2
+    for (int e = 0; e < W; ++e) {
+      const float2 c = wj[e];
+      float2 v[4];
+      load4_ff(xr + (int64_t)e * pitch, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q].add(c.x, c.y, v[q].x, v[q].y);
+    }
+  } else {
     for (int e = 0; e < W; ++e) {
       const int l = s0 + e;
       if (l < 0 || l >= n_in) continue;
-      const float2 c = w[(int64_t)j * W + e];
-      const float2 v = xf[l * I];
-      acc.add(c.x, c.y, v.x, v.y);
+      const float2 c = wj[e];
+      float2 v[4];
+      load4_ff(x0 + (int64_t)l * pitch, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q].add(c.x, c.y, v[q].x, v[q].y);
     }
-    const float2 r = acc.result();
-    const int64_t oi = (o0 + oo) * (int64_t)sout + j * I + ii;
-    y[oi] = r;
-    if (y32) y32[oi] = r.x;
   }
+}
+
+__device__ __forceinline__ void store4_ff(float2* y, float* y32, int64_t oi, const Acc2 (&acc)[4]) {
+  float2 r[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) r[q] = acc[q].result();
+  reinterpret_cast<float4*>(y + oi)[0] = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+  reinterpret_cast<float4*>(y + oi)[1] = make_float4(r[2].x, r[2].y, r[3].x, r[3].y);
+  if (y32) *reinterpret_cast<float4*>(y32 + oi) = make_float4(r[0].x, r[1].x, r[2].x, r[3].x);
+}
+
+// Mode product on the inner layout with I a multiple of 4 (16-byte aligned
+// buffers): a thread owns four consecutive inner lanes and JT outputs along
+// the mode, so each coefficient load, bounds test and address step serves four
+// Dot2 accumulations and each input row arrives in one or two 16-byte loads.
+template <typename Tin>
+__global__ void __launch_bounds__(256) band_ff_inner4_kernel(const Tin* __restrict__ x, float2* __restrict__ y,
+                                                             float* __restrict__ y32, int n_in, int n_out, int64_t I,
+                                                             const int32_t* __restrict__ start,
+                                                             const float2* __restrict__ w, int W, int64_t i_chunks,
+                                                             int j_chunks) {
+  constexpr int JT = 4;
+  const int64_t b = blockIdx.x;
+  const int jc = (int)(b % j_chunks);
+  const int64_t rest = b / j_chunks;
+  const int64_t ic = rest % i_chunks;
+  const int64_t o = rest / i_chunks;
+  const int64_t i = (ic * 64 + threadIdx.x) * 4;
+  if (i >= I) return;
+  const Tin* xo = x + o * (int64_t)n_in * I + i;
+#pragma unroll 1
+  for (int t = 0; t < JT; ++t) {
+    const int j = jc * (4 * JT) + threadIdx.y + 4 * t;
+    if (j >= n_out) break;
+    Acc2 acc[4];
+    taps4<Tin>(acc, xo, I, start[j], W, n_in, w + (int64_t)j * W);
+    store4_ff(y, y32, (o * (int64_t)n_out + j) * I + i, acc);
+  }
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Mode product on the outer layout (I < 32): a persistent CTA walks tiles of
+// To consecutive (n_in x I) slabs, each one contiguous range of the input,
+// staged in shared memory by cp.async (16-byte copies when VEC, element copies
+// otherwise) through a ring of `stages` buffers, so the next tile's copy runs
+// under the current tile's arithmetic.  Thread t of a tile computes output
+// t, t + 256, ... in memory order: the stores are coalesced.
+// MODE 0: one output per step (any I); 1: four consecutive inner lanes
+// (I % 4 == 0); 2: four consecutive slabs of the same output row (I == 1).
+template <typename Tin, bool VEC, int MODE>
+__global__ void __launch_bounds__(256) band_ff_outer_kernel(const Tin* __restrict__ x, float2* __restrict__ y,
+                                                            float* __restrict__ y32, int64_t O, int n_in, int n_out,
+                                                            int I, const int32_t* __restrict__ start,
+                                                            const float2* __restrict__ w, int W, int To, int stages) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int sin = n_in * I, sout = n_out * I;
+  const int64_t tiles = (O + To - 1) / To;
+  const int buf_elems = ((To * sin * (int)sizeof(Tin) + 15) / 16) * 16 / (int)sizeof(Tin);
+  auto issue = [&](int64_t tile, int buf) {
+    const int64_t o0 = tile * To;
+    const int to = (int)((O - o0) < (int64_t)To ? (O - o0) : (int64_t)To);
+    Tin* dst = reinterpret_cast<Tin*>(smem_raw) + (size_t)buf * buf_elems;
+    const Tin* src = x + o0 * sin;
+    if constexpr (VEC) {
+      const int n16 = to * sin * (int)sizeof(Tin) / 16;
+      for (int t = threadIdx.x; t < n16; t += blockDim.x)
+        cp_async<16>(reinterpret_cast<unsigned char*>(dst) + 16 * t, reinterpret_cast<const unsigned char*>(src) + 16 * t);
+    } else {
+      for (int t = threadIdx.x; t < to * sin; t += blockDim.x) cp_async<(int)sizeof(Tin)>(dst + t, src + t);
+    }
+  };
+  int64_t tile = blockIdx.x;
+  for (int st = 0; st < stages - 1; ++st) {
+    const int64_t tt = tile + (int64_t)st * gridDim.x;
+    if (tt < tiles) issue(tt, st);
+    cp_async_commit();
+  }
+  for (int64_t k = 0; tile < tiles; ++k, tile += gridDim.x) {
+    if (stages > 1) {
+      const int64_t tn = tile + (int64_t)(stages - 1) * gridDim.x;
+      if (tn < tiles) issue(tn, (int)((k + stages - 1) % stages));
+      cp_async_commit();
+      cp_async_wait<1>();  // all but the newest group complete: this tile has landed
+    } else {
+      issue(tile, 0);
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const Tin* xs = reinterpret_cast<const Tin*>(smem_raw) + (size_t)(k % stages) * buf_elems;
+    const int64_t o0 = tile * To;
+    const int to = (int)((O - o0) < (int64_t)To ? (O - o0) : (int64_t)To);
+    if constexpr (MODE == 1) {
+      // Groups of four inner lanes in output memory order (coalesced stores).
+      const int gi = I / 4;
+      for (int t = threadIdx.x; t < to * n_out * gi; t += blockDim.x) {
+        const int oo = t / (n_out * gi);
+        const int rem = t - oo * (n_out * gi);
+        const int j = rem / gi;
+        const int ii = 4 * (rem - j * gi);
+        Acc2 acc[4];
+        taps4<Tin>(acc, xs + oo * sin + ii, I, start[j], W, n_in, w + (int64_t)j * W);
+        store4_ff(y, y32, o0 * sout + (int64_t)oo * sout + j * I + ii, acc);
+      }
+    } else if constexpr (MODE == 2) {
+      // Four slabs (fibres) per thread for one output row j; j fastest across
+      // threads, so each store instruction writes consecutive outputs.
+      const int groups = (to + 3) / 4;
+      for (int t = threadIdx.x; t < groups * n_out; t += blockDim.x) {
+        const int g = t / n_out;
+        const int j = t - g * n_out;
+        const int s0 = start[j];
+        const float2* wj = w + (int64_t)j * W;
+        const int nq = min(4, to - 4 * g);
+        const Tin* xf = xs + (4 * g) * sin;
+        Acc2 acc[4];
+        for (int e = 0; e < W; ++e) {
+          const int l = s0 + e;
+          if (l < 0 || l >= n_in) continue;
+          const float2 c = wj[e];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = q < nq ? as_ff(xf[q * sin + l]) : make_float2(0.f, 0.f);
+            acc[q].add(c.x, c.y, v.x, v.y);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (q >= nq) break;
+          const float2 r = acc[q].result();
+          const int64_t oi = (o0 + 4 * g + q) * (int64_t)n_out + j;
+          y[oi] = r;
+          if (y32) y32[oi] = r.x;
+        }
+      }
+    } else {
+      for (int t = threadIdx.x; t < to * sout; t += blockDim.x) {
+        const int oo = t / sout;
+        const int rem = t - oo * sout;
+        const int j = rem / I;
+        const int ii = rem - j * I;
+        const Tin* xf = xs + oo * sin + ii;
+        Acc2 acc;
+        const int s0 = start[j];
+#pragma unroll 4
+        for (int e = 0; e < W; ++e) {
+          const int l = s0 + e;
+          const bool ok = l >= 0 && l < n_in;
+          const float2 c = ok ? w[(int64_t)j * W + e] : make_float2(0.f, 0.f);
+          const float2 v = ok ? as_ff(xf[l * I]) : make_float2(0.f, 0.f);
+          acc.add(c.x, c.y, v.x, v.y);
+        }
+        const float2 r = acc.result();
+        const int64_t oi = o0 * sout + t;
+        y[oi] = r;
+        if (y32) y32[oi] = r.x;
+      }
+    }
+    __syncthreads();  // the buffer is refilled by the next iteration's copy
+  }
+  cp_async_wait<0>();
 }
 
 struct RegFF {
@@ -176,6 +366,108 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(const float2* __restri
   }
 }
 
+// The same residual for runs of four consecutive elements along the
+// innermost mode L (n_L a multiple of 4, 16-byte aligned vectors): one index
+// decode and one 16-byte load per neighbouring run instead of one scalar load
+// per tap, and the taps of each element accumulated in the order of
+// residual_ff_kernel (so the two give the same values).
+template <int L>
+__global__ void __launch_bounds__(256) residual_ff_vec_kernel(const float2* __restrict__ rhs,
+                                                              const float2* __restrict__ kx,
+                                                              const float* __restrict__ x, float* __restrict__ r_out,
+                                                              int64_t total, RegFF reg, Scalars* sc, Reduce red,
+                                                              Reduce red2) {
+  __shared__ double sh[8];
+  double a_rr = 0.0, a_bb = 0.0;
+  const int64_t runs = total / 4;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < runs; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = 4 * v;
+    int im[kMaxModes];
+    unsigned rem = (unsigned)idx;  // the host keeps total below 2^32
+#pragma unroll
+    for (int m = kMaxModes - 1; m >= 0; --m) {
+      im[m] = (int)(rem % (unsigned)reg.n[m]);
+      rem /= (unsigned)reg.n[m];
+    }
+    const float4 b01 = reinterpret_cast<const float4*>(rhs + idx)[0];
+    const float4 b23 = reinterpret_cast<const float4*>(rhs + idx)[1];
+    const float4 k01 = reinterpret_cast<const float4*>(kx + idx)[0];
+    const float4 k23 = reinterpret_cast<const float4*>(kx + idx)[1];
+    const float2 bv[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
+    const float2 kv[4] = {{k01.x, k01.y}, {k01.z, k01.w}, {k23.x, k23.y}, {k23.z, k23.w}};
+    Acc2 acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[i].add(1.f, 0.f, bv[i].x, bv[i].y);
+      acc[i].add(-1.f, 0.f, kv[i].x, kv[i].y);
+    }
+    const float4 xc4 = *reinterpret_cast<const float4*>(x + idx);
+    const float xc[4] = {xc4.x, xc4.y, xc4.z, xc4.w};
+#pragma unroll
+    for (int m = kMaxModes - 1; m >= 0; --m) {
+      if (!reg.w[m]) continue;
+      if (m == L) {
+        // Window x[idx - 4 .. idx + 8) along the run's own fibre.
+        const int nL = (int)reg.n[m];
+        const float4 lf = im[m] >= 4 ? *reinterpret_cast<const float4*>(x + idx - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 rf = im[m] + 4 < nL ? *reinterpret_cast<const float4*>(x + idx + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float win[12] = {lf.x, lf.y, lf.z, lf.w, xc[0], xc[1], xc[2], xc[3], rf.x, rf.y, rf.z, rf.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int row = im[m] + i;
+          const float2* wm = reg.w[m] + (int64_t)row * 5;
+#pragma unroll
+          for (int e = 0; e < 5; ++e) {
+            const int c = row - 2 + e;
+            if (c >= 0 && c < nL) {
+              const float2 cf = wm[e];
+              acc[i].add(-cf.x, -cf.y, win[i + 2 + e], 0.f);
+            }
+          }
+        }
+      } else {
+        const float2* wm = reg.w[m] + (int64_t)im[m] * 5;
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+          const int c = im[m] - 2 + e;
+          if (c >= 0 && c < reg.n[m]) {
+            const float2 cf = wm[e];
+            float xv[4];
+            if (e == 2) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) xv[i] = xc[i];
+            } else {
+              const float4 t = __ldg(reinterpret_cast<const float4*>(x + idx + (int64_t)(e - 2) * reg.stride[m]));
+              xv[0] = t.x; xv[1] = t.y; xv[2] = t.z; xv[3] = t.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i].add(-cf.x, -cf.y, xv[i], 0.f);
+          }
+        }
+      }
+    }
+    float ro[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 rv = acc[i].result();
+      ro[i] = rv.x;
+      const double rd = (double)rv.x + (double)rv.y;
+      a_rr += rd * rd;
+      const double bd = (double)bv[i].x + (double)bv[i].y;
+      a_bb += bd * bd;
+    }
+    if (r_out) *reinterpret_cast<float4*>(r_out + idx) = make_float4(ro[0], ro[1], ro[2], ro[3]);
+  }
+  double t_rr, t_bb;
+  const bool l1 = dev::grid_sum_last(a_rr, red, &t_rr, sh);
+  if (l1) red2.partials[red2.max_blocks - 1] = t_rr;  // park the first total past the used slots
+  const bool l2 = dev::grid_sum_last(a_bb, red2, &t_bb, sh);
+  if (l2) {
+    __threadfence();
+    sc->aux = sqrt(((volatile double*)red2.partials)[red2.max_blocks - 1]) / sqrt(t_bb);
+  }
+}
+
 // Split FP64 values into (hi, lo) float pairs.
 __global__ void split_ff_kernel(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,21 +491,43 @@ template <typename Tin>
 static tca_status launch_ff(const int32_t* start, const float2* w, int W, int n_in, int n_out, const Tin* x, float2* y,
                             float* y32, int64_t O, int64_t I, cudaStream_t s) {
   if (O <= 0 || I <= 0) return TCA_OK;
-  if (I >= 32) {
+  const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
+  const bool aligned = al16(x) && al16(y) && (!y32 || al16(y32));
+  if (I >= 32 && I % 4 == 0 && aligned) {
+    const int64_t ich = (I / 4 + 63) / 64;
+    const int jch = (n_out + 15) / 16;
+    band_ff_inner4_kernel<Tin><<<(unsigned)(O * ich * jch), dim3(64, 4), 0, s>>>(x, y, y32, n_in, n_out, I, start,
+                                                                                 w, W, ich, jch);
+  } else if (I >= 32) {
     const int64_t ich = (I + 63) / 64;
     const int jch = (n_out + 31) / 32;
     band_ff_inner_kernel<Tin><<<(unsigned)(O * ich * jch), dim3(64, 4), 0, s>>>(x, y, y32, O, n_in, n_out, I, start,
                                                                                 w, W, ich, jch);
   } else {
-    const size_t per = sizeof(float2) * (size_t)n_in * (size_t)I;
-    int To = (int)std::max<size_t>(1, std::min<size_t>(256, (64 * 1024) / per));
+    const size_t per = sizeof(Tin) * (size_t)n_in * (size_t)I;
+    if (per > 200 * 1024) return TCA_ERR_UNSUPPORTED;
+    int To = (int)std::max<size_t>(1, std::min<size_t>(256, (32 * 1024) / per));
     if ((int64_t)To > O) To = (int)O;
-    const size_t sm = per * To;
-    if (sm > 200 * 1024) return TCA_ERR_UNSUPPORTED;
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(band_ff_outer_kernel<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    band_ff_outer_kernel<Tin><<<(unsigned)((O + To - 1) / To), 256, sm, s>>>(x, y, y32, O, n_in, n_out, (int)I,
-                                                                             start, w, W, To);
+    const size_t buf = (per * To + 15) / 16 * 16;
+    const int stages = 2 * buf <= 200 * 1024 ? 2 : 1;
+    const size_t sm = buf * stages;
+    const bool vec = (per % 16) == 0 && (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+    const int64_t tiles = (O + To - 1) / To;
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
+    }
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)sms * 3);
+    // Four-lane modes need 16-byte aligned rows in shared memory and output.
+    const int mode = (I % 4 == 0 && vec && aligned) ? 1 : (I == 1 ? 2 : 0);
+    auto k = mode == 1 ? band_ff_outer_kernel<Tin, true, 1>
+                       : (mode == 2 ? (vec ? band_ff_outer_kernel<Tin, true, 2> : band_ff_outer_kernel<Tin, false, 2>)
+                                    : (vec ? band_ff_outer_kernel<Tin, true, 0> : band_ff_outer_kernel<Tin, false, 0>));
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<(unsigned)grid, 256, sm, s>>>(x, y, y32, O, n_in, n_out, (int)I, start, w, W, To, stages);
   }
   TCA_LAUNCH_CHECK();
   return TCA_OK;
@@ -280,7 +594,15 @@ tca_status residual_ff(tca_plan_s* p, const float* x, const float2* rhs_ff, floa
   }
   if (p->N >= (int64_t)1 << 32) return TCA_ERR_UNSUPPORTED;
   const int grid = std::min(vector_grid(p, p->N), red.max_blocks - 1);
-  residual_ff_kernel<<<grid, 256, 0, s>>>(rhs_ff, kx_ff, x, r_out, p->N, reg, p->scal, red, red2);
+  const int L = p->d - 1;
+  const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
+  if (p->n[L] % 4 == 0 && al16(x) && al16(rhs_ff) && al16(kx_ff) && (!r_out || al16(r_out))) {
+    auto k = L == 3 ? residual_ff_vec_kernel<3>
+                    : (L == 2 ? residual_ff_vec_kernel<2> : (L == 1 ? residual_ff_vec_kernel<1> : residual_ff_vec_kernel<0>));
+    k<<<grid, 256, 0, s>>>(rhs_ff, kx_ff, x, r_out, p->N, reg, p->scal, red, red2);
+  } else {
+    residual_ff_kernel<<<grid, 256, 0, s>>>(rhs_ff, kx_ff, x, r_out, p->N, reg, p->scal, red, red2);
+  }
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }

@@ -224,6 +224,30 @@ def test_partial_iterates_match_oracle(shape, prec, tol):
         assert rel_l2(x.cpu().numpy(), ref) < tol, k
 
 
+@pytest.mark.parametrize("kind,shape", [("bspline", (20, 18, 16, 8)), ("bspline", (19, 12, 15, 4)),
+                                        ("bspline", (33, 41, 70)), ("bspline", (12, 13, 11, 16)),
+                                        ("bspline", (9, 10, 7, 5)), ("dense", (13, 11, 9, 4))])
+def test_true_residual_is_fp64_accurate(kind, shape):
+    """The reported true residual of an FP32 solve (A^T b and K x in double-float)
+    equals the oracle's FP64 residual of the same x to ~1e-9 relative.
+
+    Stopped after 3 iterations the residual is ~1e-2 of ||A^T b||; an FP32
+    evaluation would be off by ~1e-5 relative there, so this pins the
+    double-float products (every layout of the mode kernels and both
+    residual kernels) rather than the iteration."""
+    tca = lib()
+    inst = _inst(kind, shape, 660)
+    mats = [f.dense() for f in inst.factors]
+    rng = np.random.default_rng(661)
+    b = rng.standard_normal(inst.sample_shape).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-14, max_iter=3, raise_on_error=False)
+    assert st == tca.ERR_NOT_CONVERGED
+    ref = O.rel_residual(x.cpu().numpy().astype(np.float64), b.astype(np.float64), mats, inst.lam)
+    assert abs(info["rel_res_true"] - ref) <= 1e-9 * ref + 1e-15, (info["rel_res_true"], ref)
+
+
 def test_zero_rhs():
     tca = lib()
     inst = synth.instance_bspline((10, 9, 8, 4), seed=700, with_truth=False)
