@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
 namespace ws {
 
 constexpr int NA = 256, NB = 256, NT = NA + NB;
-constexpr int REG_A = 104, REG_B = 152;  // 256 x 104 + 256 x 152 = 65536 = 512 x 128 at launch
+constexpr int REG_A = 112, REG_B = 144;  // 256 x 112 + 256 x 144 = 65536 = 512 x 128 at launch
 constexpr int BAR_A = 1, BAR_FULL = 2, BAR_EMPTY = 4;
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
@@ -844,31 +844,41 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
     for (int it = max(0, nplanes - 2); it < nplanes; ++it) bar_sync(BAR_EMPTY + (it & 1), NT);
   } else {
     // ======================= B: columns, ring, outputs =======================
+    // Thread = two adjacent core rows x four consecutive mode-4 lanes of one
+    // column: every shared-memory read and global store is 16 bytes wide and
+    // every tap is a packed pair FMA across lanes.  A warp covers all 16
+    // columns of one row pair (512 contiguous bytes per row).
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_B));
+    static_assert(NB == 2 * T3 * (T2 / 2), "B mapping: 2 lane quads x T3 columns x T2/2 row pairs");
     const int tb = tid - NA;
-    const int i4b = tb % N4;
-    const int bcol = (tb / N4) % T3;
-    const int a0 = (tb / (N4 * T3)) * P;
+    const int lq = tb & 1;
+    const int bcol = (tb >> 1) % T3;
+    const int a0 = 2 * (tb / (2 * T3));
     const bool col_ok = (i3_0 + bcol) < n3;
-    const int64_t out_base = ((int64_t)(i2_0 + a0) * n3 + i3_0 + bcol) * N4 + i4b;
+    const int64_t out_base = ((int64_t)(i2_0 + a0) * n3 + i3_0 + bcol) * N4 + 4 * lq;
     const int64_t row_step = (int64_t)n3 * N4;
-    unsigned row_ok = 0;
-#pragma unroll
-    for (int k = 0; k < P; ++k) row_ok |= (col_ok && (i2_0 + a0 + k) < n2) ? (1u << k) : 0u;
+    const bool ok0 = col_ok && (i2_0 + a0) < n2;
+    const bool ok1 = col_ok && (i2_0 + a0 + 1) < n2;
 
-    float2 acc[P / 2][7];
+    // Ring of accumulators along mode 1: [row][lane pair][slot].
+    float2 acc[2][2][7];
 #pragma unroll
-    for (int k = 0; k < P / 2; ++k)
+    for (int k = 0; k < 2; ++k)
 #pragma unroll
-      for (int e = 0; e < 7; ++e) acc[k][e] = make_float2(0.f, 0.f);
-    float2 w2[P / 2], lin2[P / 2], pc2[P / 2];
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 7; ++e) acc[k][h][e] = make_float2(0.f, 0.f);
+    float2 w2[2][2], lin2[2][2], pc2[2][2];
     float g1r[7], l1r[5];
 #pragma unroll
-    for (int k2 = 0; k2 < P / 2; ++k2) w2[k2] = lin2[k2] = pc2[k2] = make_float2(0.f, 0.f);
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) w2[k][h] = lin2[k][h] = pc2[k][h] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int e = 0; e < 7; ++e) g1r[e] = 0.f;
 #pragma unroll
     for (int e = 0; e < 5; ++e) l1r[e] = 0.f;
+    const int c_off = bcol * N4 + 4 * lq;
 
 #pragma unroll 1
     for (int j = jb; j < c1 + kGramHalf; ++j) {
@@ -880,21 +890,16 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
         const float* src = sm + C::OFF_P + par * C::TILE;
         const float* s_s1 = sm + C::OFF_S1 + par * C::S1N;
         const float* s_sl = sm + C::OFF_SL + par * C::SLN;
-        // Column values as register pairs (rows 2i, 2i + 1): a tap whose rows
-        // pair up evenly uses one packed FMA, an odd tap two scalar FMAs.
-        float2 s1p[(P + 6) / 2];
+        // S1 rows a0 .. a0 + 7 (G2 taps of both rows), P rows a0 + 1 .. a0 + 6
+        // of the core column (lambda L2 taps and centres), SL rows a0, a0 + 1.
+        float4 s1v[8], s0v[6], slv[2];
 #pragma unroll
-        for (int i = 0; i < (P + 6) / 2; ++i)
-          s1p[i] = make_float2(s_s1[(a0 + 2 * i) * ROW1 + bcol * N4 + i4b], s_s1[(a0 + 2 * i + 1) * ROW1 + bcol * N4 + i4b]);
-        float2 s0p[(P + 4) / 2];
+        for (int r = 0; r < 8; ++r) s1v[r] = *reinterpret_cast<const float4*>(s_s1 + (a0 + r) * ROW1 + c_off);
 #pragma unroll
-        for (int i = 0; i < (P + 4) / 2; ++i)
-          s0p[i] = make_float2(src[(a0 + 1 + 2 * i) * ROW + (bcol + 3) * N4 + i4b],
-                               src[(a0 + 2 + 2 * i) * ROW + (bcol + 3) * N4 + i4b]);
-        float2 slp[P / 2];
+        for (int r = 0; r < 6; ++r)
+          s0v[r] = *reinterpret_cast<const float4*>(src + (a0 + 1 + r) * ROW + 3 * N4 + c_off);
 #pragma unroll
-        for (int i = 0; i < P / 2; ++i)
-          slp[i] = make_float2(s_sl[(a0 + 2 * i) * ROW1 + bcol * N4 + i4b], s_sl[(a0 + 2 * i + 1) * ROW1 + bcol * N4 + i4b]);
+        for (int r = 0; r < 2; ++r) slv[r] = *reinterpret_cast<const float4*>(s_sl + (a0 + r) * ROW1 + c_off);
         __threadfence_block();
         bar_arrive(BAR_EMPTY + par, NT);  // everything B reads of plane j is in registers
 #pragma unroll
@@ -902,51 +907,40 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 #pragma unroll
         for (int e = 0; e < 5; ++e) l1r[e] = __ldg(a.l[0] + (int64_t)j * 5 + e);
         const bool own_plane = (j >= c0) && (j < c1);
-        float* pn = CG ? a.pnew + (int64_t)j * plane + out_base : nullptr;
+        float2 g2c[7], l2c[5];  // (row a0, row a0 + 1) coefficient pairs
 #pragma unroll
-        for (int h = 0; h < P / 4; ++h) {
-          float4 g2f[7], l2f[5];
+        for (int e = 0; e < 7; ++e) g2c[e] = *reinterpret_cast<const float2*>(g2s + e * T2 + a0);
 #pragma unroll
-          for (int e = 0; e < 7; ++e) g2f[e] = *reinterpret_cast<const float4*>(g2s + e * T2 + a0 + 4 * h);
+        for (int e = 0; e < 5; ++e) l2c[e] = *reinterpret_cast<const float2*>(l2s + e * T2 + a0);
 #pragma unroll
-          for (int e = 0; e < 5; ++e) l2f[e] = *reinterpret_cast<const float4*>(l2s + e * T2 + a0 + 4 * h);
+        for (int k = 0; k < 2; ++k) {
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int k2 = 2 * h + hh;
-            const int k = 2 * k2;
+          for (int h = 0; h < 2; ++h) {
             float2 w = make_float2(0.f, 0.f);
 #pragma unroll
             for (int e = 0; e < 7; ++e) {
-              const float2 cf = hh ? make_float2(g2f[e].z, g2f[e].w) : make_float2(g2f[e].x, g2f[e].y);
-              if ((e & 1) == 0) {
-                w = ffma2(cf, s1p[(k + e) / 2], w);
-              } else {
-                w.x = fmaf(cf.x, s1p[(k + e) / 2].y, w.x);
-                w.y = fmaf(cf.y, s1p[(k + e + 1) / 2].x, w.y);
-              }
+              const float cf = k ? g2c[e].y : g2c[e].x;
+              const float4 v = s1v[k + e];
+              w = ffma2(bc2(cf), h ? make_float2(v.z, v.w) : make_float2(v.x, v.y), w);
             }
-            float2 lin = slp[k2];
+            float2 lin = h ? make_float2(slv[k].z, slv[k].w) : make_float2(slv[k].x, slv[k].y);
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
-              const float2 cf = hh ? make_float2(l2f[e].z, l2f[e].w) : make_float2(l2f[e].x, l2f[e].y);
-              if ((e & 1) == 0) {
-                lin = ffma2(cf, s0p[(k + e) / 2], lin);
-              } else {
-                lin.x = fmaf(cf.x, s0p[(k + e) / 2].y, lin.x);
-                lin.y = fmaf(cf.y, s0p[(k + e + 1) / 2].x, lin.y);
-              }
+              const float cf = k ? l2c[e].y : l2c[e].x;
+              const float4 v = s0v[k + e];
+              lin = ffma2(bc2(cf), h ? make_float2(v.z, v.w) : make_float2(v.x, v.y), lin);
             }
-            const float2 pcv = s0p[(k + 2) / 2];
-            w2[k2] = w;
-            lin2[k2] = lin;
-            pc2[k2] = pcv;
-            if constexpr (CG) {
-              float* ring = s_ring + (j & 3) * C::CORE;
-              ring[(k) * NB + tb] = pcv.x;
-              ring[(k + 1) * NB + tb] = pcv.y;
-              if (own_plane && ((row_ok >> k) & 1u)) pn[k * row_step] = pcv.x;
-              if (own_plane && ((row_ok >> (k + 1)) & 1u)) pn[(k + 1) * row_step] = pcv.y;
-            }
+            const float4 pv = s0v[k + 2];
+            w2[k][h] = w;
+            lin2[k][h] = lin;
+            pc2[k][h] = h ? make_float2(pv.z, pv.w) : make_float2(pv.x, pv.y);
+          }
+          if constexpr (CG) {
+            const float4 pc4 = make_float4(pc2[k][0].x, pc2[k][0].y, pc2[k][1].x, pc2[k][1].y);
+            float* ring = s_ring + (j & 3) * C::CORE;
+            reinterpret_cast<float4*>(ring)[k * NB + tb] = pc4;
+            if (own_plane && (k ? ok1 : ok0))
+              *reinterpret_cast<float4*>(a.pnew + (int64_t)j * plane + out_base + k * row_step) = pc4;
           }
         }
       }
@@ -955,38 +949,45 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
         constexpr int S = decltype(tag)::value;
         if (have) {
 #pragma unroll
-          for (int k2 = 0; k2 < P / 2; ++k2) {
+          for (int k = 0; k < 2; ++k) {
 #pragma unroll
-            for (int d = -3; d <= 3; ++d)
-              acc[k2][(S + d + 7) % 7] = ffma2(bc2(g1r[3 + d]), w2[k2], acc[k2][(S + d + 7) % 7]);
+            for (int h = 0; h < 2; ++h) {
 #pragma unroll
-            for (int d = -2; d <= 2; ++d)
-              acc[k2][(S + d + 7) % 7] = ffma2(bc2(l1r[2 + d]), pc2[k2], acc[k2][(S + d + 7) % 7]);
-            acc[k2][S].x += lin2[k2].x;
-            acc[k2][S].y += lin2[k2].y;
+              for (int d = -3; d <= 3; ++d)
+                acc[k][h][(S + d + 7) % 7] = ffma2(bc2(g1r[3 + d]), w2[k][h], acc[k][h][(S + d + 7) % 7]);
+#pragma unroll
+              for (int d = -2; d <= 2; ++d)
+                acc[k][h][(S + d + 7) % 7] = ffma2(bc2(l1r[2 + d]), pc2[k][h], acc[k][h][(S + d + 7) % 7]);
+              acc[k][h][S].x += lin2[k][h].x;
+              acc[k][h][S].y += lin2[k][h].y;
+            }
           }
         }
         constexpr int E = (S + 4) % 7;
         if (c >= c0) {
           float part = 0.f;
           float* qo = a.q + (int64_t)c * plane + out_base;
-          const float* ring = s_ring + (c & 3) * C::CORE + tb;
+          const float4* ring = reinterpret_cast<const float4*>(s_ring + (c & 3) * C::CORE);
 #pragma unroll
-          for (int k2 = 0; k2 < P / 2; ++k2) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int k = 2 * k2 + h;
-              if ((row_ok >> k) & 1u) {
-                const float qv = h ? acc[k2][E].y : acc[k2][E].x;
-                qo[k * row_step] = qv;
-                if constexpr (CG) part = fmaf(qv, ring[k * NB], part);
+          for (int k = 0; k < 2; ++k) {
+            if (k ? ok1 : ok0) {
+              const float4 qv = make_float4(acc[k][0][E].x, acc[k][0][E].y, acc[k][1][E].x, acc[k][1][E].y);
+              *reinterpret_cast<float4*>(qo + k * row_step) = qv;
+              if constexpr (CG) {
+                const float4 pv = ring[k * NB + tb];
+                part = fmaf(qv.x, pv.x, part);
+                part = fmaf(qv.y, pv.y, part);
+                part = fmaf(qv.z, pv.z, part);
+                part = fmaf(qv.w, pv.w, part);
               }
             }
           }
           dot += (double)part;
         }
 #pragma unroll
-        for (int k2 = 0; k2 < P / 2; ++k2) acc[k2][E] = make_float2(0.f, 0.f);
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) acc[k][h][E] = make_float2(0.f, 0.f);
       };
       switch (j % 7) {
         case 0: step(std::integral_constant<int, 0>{}); break;
