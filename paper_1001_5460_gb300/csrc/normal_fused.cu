@@ -714,9 +714,24 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
       float* s_s1 = sm + C::OFF_S1 + par * C::S1N;
       float* s_sl = sm + C::OFF_SL + par * C::SLN;
       // ---- stage A (one halo row, two columns, eight lanes per thread) ----
-      for (int slot = tid; slot < H2 * C::NBQ; slot += NA) {
-        const int ar = slot % H2;
-        const int bq = slot / H2;
+      // Slots of core rows (G3, G4 and lambda (L3 + L4)) fill warps 0-3, one
+      // per scheduler; the lighter halo-row slots (G3, G4 only) fill warp 4
+      // and half of warp 5.  No warp mixes the two kinds, and the fewest
+      // warps issue the light work (issue slots, not lanes, are the limit).
+      static_assert(H2 == 22 && T2 == 16 && C::NBQ == 8 && NA == 256, "stage-A slot map");
+      int slot_ar = -1, slot_bq = 0;
+      if (tid < 128) {
+        slot_ar = 3 + (tid & 15);
+        slot_bq = tid >> 4;
+      } else if (tid < 176) {
+        const int h = tid - 128;  // 0 .. 47
+        const int hr = h % 6;
+        slot_ar = hr < 3 ? hr : hr + T2;
+        slot_bq = h / 6;
+      }
+      if (slot_ar >= 0) {
+        const int ar = slot_ar;
+        const int bq = slot_bq;
         const int b0 = bq * T3P;
         constexpr int NV = 4;
         float2 v[T3P + 6][NV];
