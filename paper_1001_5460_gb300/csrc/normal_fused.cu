@@ -51,6 +51,10 @@ struct FusedArgs {
   int nchunks;
   Scalars* scal;
   Reduce red;
+  // Warp-specialised sweep (n4 = 8): G_4 and lambda L_4 by tap, then lane,
+  // read straight from the parameter bank (the same for every CTA and plane).
+  float g4c[7 * 8];
+  float l4c[5 * 8];
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -774,7 +778,8 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 #pragma unroll
             for (int e = 0; e < 7; ++e) {
               const int d = e - 3;
-              const float4 c4 = *reinterpret_cast<const float4*>(g4s + e * N4 + 4 * mm);
+              const float4 c4 = make_float4(a.g4c[e * N4 + 4 * mm], a.g4c[e * N4 + 4 * mm + 1],
+                                            a.g4c[e * N4 + 4 * mm + 2], a.g4c[e * N4 + 4 * mm + 3]);
 #pragma unroll
               for (int hh = 0; hh < 2; ++hh) {
                 const int m = 2 * mm + hh;
@@ -826,7 +831,8 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
               const int d = e - 2;
-              const float4 c4 = *reinterpret_cast<const float4*>(l4s + e * N4 + 4 * mm);
+              const float4 c4 = make_float4(a.l4c[e * N4 + 4 * mm], a.l4c[e * N4 + 4 * mm + 1],
+                                            a.l4c[e * N4 + 4 * mm + 2], a.l4c[e * N4 + 4 * mm + 3]);
 #pragma unroll
               for (int hh = 0; hh < 2; ++hh) {
                 const int m = 2 * mm + hh;
@@ -1157,6 +1163,10 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
   a.red = p->red;
   const int64_t n4 = dims[3];
   if (n4 == 8) {
+    for (int i4 = 0; i4 < 8; ++i4) {
+      for (int e = 0; e < 7; ++e) a.g4c[e * 8 + i4] = p->ws_g4[i4 * 7 + e];
+      for (int e = 0; e < 5; ++e) a.l4c[e * 8 + i4] = p->ws_l4[i4 * 5 + e];
+    }
     return cg_mode ? launch_ws<true>(p, a, s) : launch_ws<false>(p, a, s);
   } else if (n4 == 4) {
     return cg_mode ? launch_fused<4, 16, 32, 4, 256, 3, true>(p, a, s) : launch_fused<4, 16, 32, 4, 256, 3, false>(p, a, s);

@@ -422,6 +422,11 @@ extern "C" tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, con
   if (e == cudaSuccess) e = cudaMemsetAsync(p->red.ticket, 0, 2 * sizeof(unsigned int), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(Scalars), stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  // Mode-4 bands of the warp-specialised sweep travel as kernel parameters.
+  if (e == cudaSuccess && p->fused_ok && order == 4 && p->n[3] == 8) {
+    e = cudaMemcpy(p->ws_g4, p->mode[3].gram.band.w32, sizeof(p->ws_g4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(p->ws_l4, p->mode[3].lap.w32, sizeof(p->ws_l4), cudaMemcpyDeviceToHost);
+  }
   if (e != cudaSuccess) {
     set_cuda_error(e);
     destroy_plan(p);

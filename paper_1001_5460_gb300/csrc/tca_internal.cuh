@@ -113,6 +113,8 @@ struct tca_plan_s {
   bool fused_ok = false;          // fused normal-operator sweep applies to this shape
   int fused_nchunks = 0;          // autotuned chunk count along mode 1 (0: wave model)
   int fused_model_nchunks = 0;    // chunk count the last fused launch used
+  float ws_g4[8 * 7] = {};        // n4 = 8 plans: G_4 and lambda L_4 bands (host copies, [i4][tap])
+  float ws_l4[8 * 5] = {};
 
   int64_t ws_elems = 0;           // capacity of each ping-pong buffer (elements)
   void* ws[2] = {nullptr, nullptr};
