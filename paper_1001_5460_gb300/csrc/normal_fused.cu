@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
 namespace ws {
 
 constexpr int NA = 256, NB = 256, NT = NA + NB;
-constexpr int REG_A = 112, REG_B = 144;  // 256 x 112 + 256 x 144 = 65536 = 512 x 128 at launch
+constexpr int REG_A = 104, REG_B = 152;  // 256 x 112 + 256 x 144 = 65536 = 512 x 128 at launch
 constexpr int BAR_A = 1, BAR_FULL = 2, BAR_EMPTY = 4;
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
@@ -685,6 +685,27 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
       if (jb + s < je) issue(jb + s, s);
       cp_async_commit();
     }
+    static_assert(H2 == 22 && T2 == 16 && C::NBQ == 8 && NA == 256, "stage-A slot map");
+    int slot_ar = -1, slot_bq = 0;
+    if (tid < 128) {
+      slot_ar = 3 + (tid & 15);
+      slot_bq = tid >> 4;
+    } else if (tid < 176) {
+      const int h = tid - 128;  // 0 .. 47
+      const int hr = h % 6;
+      slot_ar = hr < 3 ? hr : hr + T2;
+      slot_bq = h / 6;
+    }
+    // G3 and lambda L3 coefficients of this slot's two columns, the same for every plane.
+    float gc3[T3P][7], lc3[T3P][5];
+#pragma unroll
+    for (int t = 0; t < T3P; ++t) {
+      const int col = (slot_ar >= 0 ? slot_bq * T3P : 0) + t;
+#pragma unroll
+      for (int e = 0; e < 7; ++e) gc3[t][e] = g3s[col * 8 + e];
+#pragma unroll
+      for (int e = 0; e < 5; ++e) lc3[t][e] = l3s[col * 8 + e];
+    }
 #pragma unroll 1
     for (int it = 0; it < nplanes; ++it) {
       const int j = jb + it;
@@ -722,17 +743,6 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
       // per scheduler; the lighter halo-row slots (G3, G4 only) fill warp 4
       // and half of warp 5.  No warp mixes the two kinds, and the fewest
       // warps issue the light work (issue slots, not lanes, are the limit).
-      static_assert(H2 == 22 && T2 == 16 && C::NBQ == 8 && NA == 256, "stage-A slot map");
-      int slot_ar = -1, slot_bq = 0;
-      if (tid < 128) {
-        slot_ar = 3 + (tid & 15);
-        slot_bq = tid >> 4;
-      } else if (tid < 176) {
-        const int h = tid - 128;  // 0 .. 47
-        const int hr = h % 6;
-        slot_ar = hr < 3 ? hr : hr + T2;
-        slot_bq = h / 6;
-      }
       if (slot_ar >= 0) {
         const int ar = slot_ar;
         const int bq = slot_bq;
@@ -750,9 +760,7 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
         float2 u[T3P][NV];
 #pragma unroll
         for (int t = 0; t < T3P; ++t) {
-          const float4 ga = *reinterpret_cast<const float4*>(g3s + (b0 + t) * 8);
-          const float4 gb = *reinterpret_cast<const float4*>(g3s + (b0 + t) * 8 + 4);
-          const float gc[7] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z};
+          const float* gc = gc3[t];
 #pragma unroll
           for (int m = 0; m < NV; ++m) {
             float2 s2 = make_float2(0.f, 0.f);
@@ -808,8 +816,7 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
           float2 lin[T3P][NV];
 #pragma unroll
           for (int t = 0; t < T3P; ++t) {
-            const float4 la = *reinterpret_cast<const float4*>(l3s + (b0 + t) * 8);
-            const float lc[5] = {la.x, la.y, la.z, la.w, l3s[(b0 + t) * 8 + 4]};
+            const float* lc = lc3[t];
 #pragma unroll
             for (int m = 0; m < NV; ++m) {
               float2 s2 = make_float2(0.f, 0.f);
@@ -900,6 +907,11 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 #pragma unroll
     for (int e = 0; e < 5; ++e) l1r[e] = 0.f;
     const int c_off = bcol * N4 + 4 * lq;
+    float2 g2c[7], l2c[5];  // (row a0, row a0 + 1) coefficient pairs, the same for every plane
+#pragma unroll
+    for (int e = 0; e < 7; ++e) g2c[e] = *reinterpret_cast<const float2*>(g2s + e * T2 + a0);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) l2c[e] = *reinterpret_cast<const float2*>(l2s + e * T2 + a0);
 
 #pragma unroll 1
     for (int j = jb; j < c1 + kGramHalf; ++j) {
@@ -928,11 +940,6 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 #pragma unroll
         for (int e = 0; e < 5; ++e) l1r[e] = __ldg(a.l[0] + (int64_t)j * 5 + e);
         const bool own_plane = (j >= c0) && (j < c1);
-        float2 g2c[7], l2c[5];  // (row a0, row a0 + 1) coefficient pairs
-#pragma unroll
-        for (int e = 0; e < 7; ++e) g2c[e] = *reinterpret_cast<const float2*>(g2s + e * T2 + a0);
-#pragma unroll
-        for (int e = 0; e < 5; ++e) l2c[e] = *reinterpret_cast<const float2*>(l2s + e * T2 + a0);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
 #pragma unroll
