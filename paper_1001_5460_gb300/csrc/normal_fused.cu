@@ -28,6 +28,7 @@
 // pairs (fma.rn.f32x2) wherever both operands pair up naturally, and the
 // accumulator ring along mode 1 is indexed by compile-time slots (a switch on
 // j mod 7) so it never moves between registers.
+#include <cuda.h>
 #include <algorithm>
 #include <cstdio>
 #include <type_traits>
@@ -55,6 +56,11 @@ struct FusedArgs {
   // read straight from the parameter bank (the same for every CTA and plane).
   float g4c[7 * 8];
   float l4c[5 * 8];
+  // Warp-specialised sweep with TMA halo loads: 4D maps (n4, n3, n2, n1) of r
+  // and p_old, box (8, 22, 22, 1) = one halo tile; set by the TMA launch only.
+  CUtensorMap tm_r;
+  CUtensorMap tm_p;
+  int* timeout_flag;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -71,6 +77,35 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// mbarrier and TMA (cp.async.bulk.tensor) helpers for the warp-specialised sweep.
+constexpr long long kTmaWaitPolls = 1ll << 24;  // try_wait polls before a wait gives up
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, unsigned parity) {
+  for (long long it = 0; it < kTmaWaitPolls; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // d = a * b + c on a pair of FP32 lanes (one packed FMA instruction).
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -567,7 +602,9 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
 // Warp-specialised variant for n4 = 8 (the 4D workloads): the same sweep with
 // the work of a plane split between two warp groups that run one plane apart.
 //   loader/in-plane warps (A, 8 warps): copy the halo tiles of r and p_old
-//     (cp.async, 3 stages), form p = r + beta p_old, apply G_3, G_4 along the
+//     (one TMA box per tensor and plane into a 3-stage mbarrier ring, or
+//     cp.async when the tile is wider than the tensor or a tensor is not
+//     16-byte aligned), form p = r + beta p_old, apply G_3, G_4 along the
 //     rows of the halo tile (S1) and lambda (L_3 + L_4) on the core rows (SL);
 //   column/ring warps (B, 8 warps): G_2 and lambda L_2 down the columns, the
 //     scatter into the 7-slot register ring along mode 1, the outputs q and
@@ -589,13 +626,16 @@ __device__ __forceinline__ void bar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <bool CG>
-__global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
+template <bool CG, bool TMA>
+__global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int N4 = 8, T2 = 16, T3 = 16, T3P = 2, STAGES = 3;
   using C = Cfg<N4, T2, T3, T3P, NB, STAGES, true>;  // smem layout of the CG configuration (P tiles, ring)
   constexpr int H2 = C::H2, ROW = C::ROW, ROW1 = C::ROW1, P = C::P;
   constexpr int NIN = CG ? 2 : 1;
-  extern __shared__ __align__(16) float sm[];
+  // No static shared memory in this kernel (the reduction's flag lives in the
+  // dynamic block too), so the dynamic block starts at the 128-byte aligned
+  // base that the TMA stages need; checked below.
+  extern __shared__ __align__(128) float sm[];
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
 
@@ -625,6 +665,19 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
   float* g2s = sm + C::OFF_G2;
   float* l2s = sm + C::OFF_L2;
   double* s_red = reinterpret_cast<double*>(sm + C::OFF_RED);
+  // TMA: one mbarrier per stage and a CTA-wide give-up flag after the reduction scratch.
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(sm + C::OFF_RED + 2 * (NT / 32));
+  volatile int* s_abort = reinterpret_cast<volatile int*>(tbar + STAGES);
+  volatile int* s_last = s_abort + 1;
+  if (TMA && tid == 0) {
+    for (int b = 0; b < STAGES; ++b) mbar_init1(&tbar[b]);
+    // A stage off the 128-byte grid would fault the copy: give up instead
+    // (no copies, no waits, error flag set; the sweep's output is invalid).
+    const bool misaligned = (smem_u32(sm) & 127u) != 0;
+    *s_abort = misaligned ? 1 : 0;
+    if (misaligned && a.timeout_flag) atomicExch(a.timeout_flag, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 
   for (int t = tid; t < T3 * 8; t += NT) {
     const int r = t >> 3, e = t & 7, i3 = i3_0 + r;
@@ -650,8 +703,25 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
     // ======================= A: loads, p, stage A =======================
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_A));
     constexpr int ELEMS = H2 * C::H3 * 2;  // 16-byte copies per tensor and plane
-    constexpr int NCP = (ELEMS + NA - 1) / NA;
+    constexpr int NCP = TMA ? 1 : (ELEMS + NA - 1) / NA;
     int cp_dst[NCP], cp_src[NCP];
+    // TMA: one thread of warp 7 (idle in stage A) copies each tensor's 22 x 22
+    // x 8 halo tile as one box into its stage, densely packed (row pitch
+    // H3 * N4); the p pass re-pitches it into the padded P tile.
+    constexpr int TMA_WARP = NA / 32 - 1;
+    constexpr unsigned TMA_BYTES = NIN * H2 * C::H3 * N4 * sizeof(float);
+    static_assert((C::TILE * sizeof(float)) % 128 == 0, "TMA stages must stay 128-byte aligned");
+    int n_issued = 0;  // issuing thread: planes jb .. jb + n_issued - 1 copied (in order)
+    auto issue_tma = [&](int jj, int b) {
+      if ((tid & 31) == 0 && !*s_abort) {
+        n_issued = jj - jb + 1;
+        mbar_expect_tx(&tbar[b], TMA_BYTES);
+#pragma unroll
+        for (int src_i = 0; src_i < NIN; ++src_i)
+          tma_load_4d(s_in + (b * 2 + src_i) * C::TILE, (CG && src_i == 0) ? &a.tm_r : &a.tm_p, 0, i3_0 - 3,
+                      i2_0 - 3, jj, &tbar[b]);
+      }
+    };
 #pragma unroll
     for (int i = 0; i < NCP; ++i) {
       const int t = tid + i * NA;
@@ -682,8 +752,12 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
     };
 #pragma unroll 1
     for (int s = 0; s < STAGES - 1; ++s) {
-      if (jb + s < je) issue(jb + s, s);
-      cp_async_commit();
+      if constexpr (TMA) {
+        if (warp == TMA_WARP && jb + s < je) issue_tma(jb + s, s);
+      } else {
+        if (jb + s < je) issue(jb + s, s);
+        cp_async_commit();
+      }
     }
     static_assert(H2 == 22 && T2 == 16 && C::NBQ == 8 && NA == 256, "stage-A slot map");
     int slot_ar = -1, slot_bq = 0;
@@ -711,9 +785,20 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
       const int j = jb + it;
       const int par = it & 1;
       const int buf = it % STAGES;
-      cp_async_wait<STAGES - 2>();
-      bar_sync(BAR_A, NA);  // plane j landed for every A thread; all are done with plane j - 1's stage
-      {
+      if constexpr (TMA) {
+        // Plane j's rows have landed once its stage barrier completes.  Every
+        // A thread passed the barrier after the p pass of plane j - 1, so its
+        // stage (the one refilled next) is free.  A wait that gives up marks
+        // the CTA and the kernel runs on without waiting (garbage out, flag set).
+        if (!*s_abort && !mbar_wait_parity(&tbar[buf], (unsigned)((it / STAGES) & 1))) {
+          *s_abort = 1;
+          if (a.timeout_flag) atomicExch(a.timeout_flag, 1);
+        }
+        const int jn = j + STAGES - 1;
+        if (warp == TMA_WARP && jn < je) issue_tma(jn, (it + STAGES - 1) % STAGES);
+      } else {
+        cp_async_wait<STAGES - 2>();
+        bar_sync(BAR_A, NA);  // plane j landed for every A thread; all are done with plane j - 1's stage
         const int jn = j + STAGES - 1;
         if (jn < je) issue(jn, (it + STAGES - 1) % STAGES);
         cp_async_commit();
@@ -723,7 +808,21 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
       {
         const float4* pp = reinterpret_cast<const float4*>(s_in + (buf * 2 + (CG ? 1 : 0)) * C::TILE);
         float4* out = reinterpret_cast<float4*>(pdst);
-        if constexpr (CG) {
+        if constexpr (TMA) {
+          // Dense stage rows (H3 * N4 / 4 vectors) into padded P rows (ROW / 4).
+          constexpr int DR = C::H3 * N4 / 4, PR = ROW / 4;
+          const float4* rr = reinterpret_cast<const float4*>(s_in + (buf * 2 + 0) * C::TILE);
+          for (int t = tid; t < H2 * DR; t += NA) {
+            const int o = (t / DR) * PR + t % DR;
+            if constexpr (CG) {
+              const float4 x = rr[t], y = pp[t];
+              out[o] = make_float4(fmaf(beta, y.x, x.x), fmaf(beta, y.y, x.y), fmaf(beta, y.z, x.z),
+                                   fmaf(beta, y.w, x.w));
+            } else {
+              out[o] = pp[t];
+            }
+          }
+        } else if constexpr (CG) {
           const float4* rr = reinterpret_cast<const float4*>(s_in + (buf * 2 + 0) * C::TILE);
           for (int t = tid; t < C::TILE / 4; t += NA) {
             const float4 x = rr[t], y = pp[t];
@@ -868,7 +967,17 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
       __threadfence_block();
       bar_arrive(BAR_FULL + par, NT);  // plane j's P, S1 and SL tiles are ready for B
     }
-    cp_async_wait<0>();
+    if constexpr (TMA) {
+      // After a give-up, wait (bounded) for the last copy into each stage so
+      // that no transfer into shared memory outlives the CTA.
+      if (*s_abort && warp == TMA_WARP && (tid & 31) == 0) {
+        // Plane k went to stage k % STAGES in phase (k / STAGES) & 1.
+        for (int k = max(0, n_issued - STAGES); k < n_issued; ++k)
+          (void)mbar_wait_parity(&tbar[k % STAGES], (unsigned)((k / STAGES) & 1));
+      }
+    } else {
+      cp_async_wait<0>();
+    }
     for (int it = max(0, nplanes - 2); it < nplanes; ++it) bar_sync(BAR_EMPTY + (it & 1), NT);
   } else {
     // ======================= B: columns, ring, outputs =======================
@@ -1031,7 +1140,7 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
   __syncthreads();
   if constexpr (CG) {
     double total;
-    if (dev::grid_sum_last(dot, a.red, &total, s_red)) {
+    if (dev::grid_sum_last_at(dot, a.red, &total, s_red, s_last)) {
       Scalars* sc = a.scal;
       sc->pq = total;
       const double alpha = sc->rho / total;
@@ -1047,7 +1156,9 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(FusedArgs a) {
 
 constexpr size_t ws_bytes() {
   using C = Cfg<8, 16, 16, 2, NB, 3, true>;
-  return sizeof(float) * (size_t)(C::OFF_RED + 2 * (NT / 32));  // reduction scratch for 16 warps
+  // reduction scratch for 16 warps, then 3 stage mbarriers, the give-up flag
+  // and the reduction's last-block flag
+  return sizeof(float) * (size_t)(C::OFF_RED + 2 * (NT / 32)) + 3 * sizeof(uint64_t) + 16;
 }
 
 }  // namespace ws
@@ -1102,10 +1213,12 @@ template <bool CG>
 tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   constexpr size_t bytes = ws::ws_bytes();
   static_assert(bytes <= 227 * 1024, "shared memory budget");
-  auto kfn = ws::fused_ws_kernel<CG>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(ws::fused_ws_kernel<CG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ws::fused_ws_kernel<CG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) {
       set_cuda_error(e);
       return TCA_ERR_CUDA;
@@ -1113,6 +1226,19 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
     attr_done = true;
   }
   FusedArgs a = base;
+  // Halo tiles by TMA when both maps encode (16-byte aligned tensors); else cp.async.
+  bool tma = true;
+  {
+    const uint64_t dims[4] = {8, (uint64_t)a.n3, (uint64_t)a.n2, (uint64_t)a.n1};
+    const uint64_t strides[3] = {8 * sizeof(float), (uint64_t)a.n3 * 8 * sizeof(float),
+                                 (uint64_t)a.n2 * a.n3 * 8 * sizeof(float)};
+    // One box per tensor and plane; boxes wider than the tensor are left to cp.async.
+    const uint32_t box[4] = {8, 22, 22, 1};
+    tma = a.n2 >= 22 && a.n3 >= 22 && encode_tmap_f32(&a.tm_p, a.pold, 4, dims, strides, box);
+    if (tma && CG) tma = encode_tmap_f32(&a.tm_r, a.r, 4, dims, strides, box);
+  }
+  a.timeout_flag = wait_timeout_flag();
+  auto kfn = tma ? ws::fused_ws_kernel<CG, true> : ws::fused_ws_kernel<CG, false>;
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
   const int tiles2 = (n2 + 15) / 16, tiles3 = (n3 + 15) / 16;
   const int tiles = tiles2 * tiles3;

@@ -2,6 +2,7 @@
 // small device helpers shared by the kernels.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -231,6 +232,11 @@ tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, 
 tca_status read_wait_timeout(int* flag, bool reset);
 // Device address of the wait-timeout flag (for kernels in other translation units).
 int* wait_timeout_flag();
+// Tiled FP32 tensor map (no swizzle, zero fill out of bounds): dims innermost
+// first, strides in bytes for dims 1 .. rank-1.  False if the driver rejects it
+// (alignment) or the encoder is unavailable.
+bool encode_tmap_f32(CUtensorMap* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                     const uint32_t* box);
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);
@@ -272,14 +278,16 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // Last-block-finishes grid reduction.  Every block calls it with its partial;
 // the block that arrives last sums all partials in a fixed order and returns
 // true in thread 0 with the total in *total.  Deterministic for a fixed grid.
-__device__ __forceinline__ bool grid_sum_last(double v, Reduce red, double* total, double* sh) {
-  __shared__ bool am_last;
+// am_last: one int of shared memory for the block's verdict.
+__device__ __forceinline__ bool grid_sum_last_at(double v, Reduce red, double* total, double* sh,
+                                                 volatile int* am_last_flag) {
+  volatile int& am_last = *am_last_flag;
   const double bs = block_sum(v, sh);
   if (threadIdx.x == 0) {
     red.partials[blockIdx.x] = bs;
     __threadfence();
     const unsigned int t = atomicAdd(red.ticket, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == gridDim.x - 1) ? 1 : 0;
   }
   __syncthreads();
   if (!am_last) return false;
@@ -292,6 +300,11 @@ __device__ __forceinline__ bool grid_sum_last(double v, Reduce red, double* tota
     *red.ticket = 0u;
   }
   return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ bool grid_sum_last(double v, Reduce red, double* total, double* sh) {
+  __shared__ int am_last;
+  return grid_sum_last_at(v, red, total, sh, &am_last);
 }
 
 template <typename T> __device__ __forceinline__ float to_f(T v);
