@@ -39,7 +39,10 @@
  * Errors.  No call aborts or throws across this boundary: every failure comes
  * back as a tca_status.  A CUDA error is reported as TCA_ERR_CUDA and
  * tca_last_error_string() gives the CUDA message.  Device-side waits are
- * bounded and end in TCA_ERR_TIMEOUT instead of hanging.
+ * bounded: a wait that gives up sets a device flag and its kernel finishes
+ * without waiting further (its output is then invalid); tca_solve,
+ * tca_solve_batched and tca_solve_net report the flag as TCA_ERR_TIMEOUT, and
+ * tca_check_timeout reads it after asynchronous calls.
  */
 #ifndef TCA_H
 #define TCA_H
@@ -250,6 +253,18 @@ TCA_API tca_status tca_rel_residual_noalloc(const double* rhs, const double* kx,
                                             cudaStream_t stream);
 
 /* Free a plan and its device memory (NULL is ignored). */
+/* Synchronise the stream, then report whether any bounded device wait (TMA
+ * and tensor-core pipelines) gave up since the last check: TCA_ERR_TIMEOUT,
+ * clearing the flag, or TCA_OK.  The flag is per process, not per plan. */
+TCA_API tca_status tca_check_timeout(cudaStream_t stream);
+
+/* Diagnostic of the wait machinery: one block waits on an mbarrier that
+ * nothing arrives at, at most `polls` polls (>= 0), then gives up exactly as
+ * a real wait would.  Returns the tca_check_timeout verdict: TCA_ERR_TIMEOUT
+ * for any polls count (the wait cannot succeed), TCA_ERR_INVALID_ARG for
+ * polls < 0.  The context stays usable.  Synchronises the stream. */
+TCA_API tca_status tca_wait_selftest(int64_t polls, cudaStream_t stream);
+
 TCA_API void tca_destroy(tca_plan_t plan);
 
 /* Static text for a status code. */

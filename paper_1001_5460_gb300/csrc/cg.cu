@@ -928,8 +928,10 @@ extern "C" tca_status tca_solve_batched(int count, tca_plan_t* plans, const void
     for (int k = 0; k < i; ++k)
       if (plans[k] == plans[i]) return TCA_ERR_INVALID_ARG;  // each instance needs its own plan
   }
-  return solve_batched_impl(count, plans, reinterpret_cast<const float* const*>(b), reinterpret_cast<float* const*>(x),
-                            opts, info, stream);
+  const tca_status st = solve_batched_impl(count, plans, reinterpret_cast<const float* const*>(b),
+                                           reinterpret_cast<float* const*>(x), opts, info, stream);
+  const tca_status tw = check_wait_timeout(stream);
+  return tw != TCA_OK ? tw : st;
 }
 
 extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
@@ -961,5 +963,7 @@ extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const t
     TCA_CUDA_TRY(cudaMemcpyAsync(x, p->stage_x, es * (size_t)p->N, cudaMemcpyDefault, stream));
     TCA_CUDA_TRY(cudaStreamSynchronize(stream));
   }
-  return st;
+  // A bounded device wait that gave up outranks the solver's own verdict.
+  const tca_status tw = check_wait_timeout(stream);
+  return tw != TCA_OK ? tw : st;
 }

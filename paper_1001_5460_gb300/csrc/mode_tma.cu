@@ -413,6 +413,63 @@ int* wait_timeout_flag() {
   return addr;
 }
 
+// Give-up check of the wait machinery: one block waits on an mbarrier that
+// nothing arrives at, `polls` times at most, then records the give-up like a
+// real wait would.  Bounded by construction; touches no memory but its own.
+__global__ void wait_selftest_kernel(long long polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool done = false;
+  for (long long i = 0; i < polls && !done; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(&bar)), "r"(0u)
+        : "memory");
+    done = ok != 0;
+  }
+  if (!done && threadIdx.x == 0) atomicExch(&g_wait_timeout, 1);
+}
+
+// Pinned word the flag is read into (one per process; calls serialise on it).
+static int* flag_host() {
+  static int* h = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    if (cudaMallocHost((void**)&h, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      h = nullptr;
+    }
+  });
+  return h;
+}
+
+tca_status check_wait_timeout(cudaStream_t s) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int* dflag = wait_timeout_flag();
+  int* h = flag_host();
+  if (!dflag || !h) return TCA_ERR_CUDA;
+  TCA_CUDA_TRY(cudaMemcpyAsync(h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (*h == 0) return TCA_OK;
+  TCA_CUDA_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return TCA_ERR_TIMEOUT;
+}
+
+tca_status wait_selftest(long long polls, cudaStream_t s) {
+  if (polls < 0) return TCA_ERR_INVALID_ARG;
+  wait_selftest_kernel<<<1, 32, 0, s>>>(polls);
+  TCA_LAUNCH_CHECK();
+  return check_wait_timeout(s);
+}
+
 tca_status read_wait_timeout(int* flag, bool reset) {
   TCA_CUDA_TRY(cudaMemcpyFromSymbol(flag, g_wait_timeout, sizeof(int)));
   if (reset && *flag) {
@@ -423,3 +480,9 @@ tca_status read_wait_timeout(int* flag, bool reset) {
 }
 
 }  // namespace tca
+
+extern "C" tca_status tca_check_timeout(cudaStream_t stream) { return tca::check_wait_timeout(stream); }
+
+extern "C" tca_status tca_wait_selftest(int64_t polls, cudaStream_t stream) {
+  return tca::wait_selftest((long long)polls, stream);
+}

@@ -232,6 +232,8 @@ tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, 
 tca_status read_wait_timeout(int* flag, bool reset);
 // Device address of the wait-timeout flag (for kernels in other translation units).
 int* wait_timeout_flag();
+// Synchronise s; TCA_ERR_TIMEOUT (and clear the flag) if a bounded wait gave up.
+tca_status check_wait_timeout(cudaStream_t s);
 // Tiled FP32 tensor map (no swizzle, zero fill out of bounds): dims innermost
 // first, strides in bytes for dims 1 .. rank-1.  False if the driver rejects it
 // (alignment) or the encoder is unavailable.

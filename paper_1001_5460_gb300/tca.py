@@ -118,6 +118,10 @@ _lib.tca_kernel_launches.argtypes = [ctypes.c_int]
 _lib.tca_kernel_launches.restype = ctypes.c_uint64
 _lib.tca_version.argtypes = []
 _lib.tca_version.restype = ctypes.c_int
+_lib.tca_check_timeout.argtypes = [_vp]
+_lib.tca_check_timeout.restype = ctypes.c_int
+_lib.tca_wait_selftest.argtypes = [ctypes.c_int64, _vp]
+_lib.tca_wait_selftest.restype = ctypes.c_int
 
 
 class TcaError(RuntimeError):
@@ -169,6 +173,16 @@ def kernel_launches(reset: bool = False) -> int:
     return int(_lib.tca_kernel_launches(1 if reset else 0))
 
 
+def check_timeout(stream=None) -> int:
+    """Synchronise the stream; ERR_TIMEOUT (flag cleared) if a bounded device wait gave up, else OK."""
+    return int(_lib.tca_check_timeout(_stream(stream)))
+
+
+def wait_selftest(polls: int, stream=None) -> int:
+    """Run a bounded wait that cannot succeed (at most `polls` polls); returns its status (ERR_TIMEOUT)."""
+    return int(_lib.tca_wait_selftest(int(polls), _stream(stream)))
+
+
 def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
     """||rhs - kx|| / ||rhs|| of two FP64 device vectors into out (one FP64 device value).
 
@@ -185,7 +199,8 @@ def exported_symbols() -> list[str]:
             "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
-            "tca_net_use_tensor_cores", "tca_net_destroy", "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
+            "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",
+            "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
 
 
 class Factor:

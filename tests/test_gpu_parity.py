@@ -325,3 +325,23 @@ def test_solve_mixed_precision_refinement(kind, shape, prec):
     assert abs(info["rel_res_true"] - rel) < 1e-7
     ref = O.solve(b.astype(np.float64), mats, inst.lam, rtol=1e-12).x
     assert rel_l2(got, ref) < 1e-4
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """A device wait that cannot succeed gives up after its poll limit, the
+    status reaches the host as ERR_TIMEOUT, the flag clears, and the context
+    keeps working (a solve right after is correct and reports OK)."""
+    tca = lib()
+    assert tca.check_timeout() == tca.OK
+    for polls in (0, 1, 1000):
+        assert tca.wait_selftest(polls) == tca.ERR_TIMEOUT
+        assert tca.check_timeout() == tca.OK  # cleared by the report
+    assert tca.wait_selftest(-1) == tca.ERR_INVALID_ARG
+    inst = synth.instance_bspline((24, 22, 23, 8), seed=670, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-6)
+    assert st == tca.OK
+    assert O.rel_residual(x.cpu().numpy(), b.astype(np.float64), mats, inst.lam) <= 1.5e-6
