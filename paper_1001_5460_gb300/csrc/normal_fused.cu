@@ -618,6 +618,7 @@ namespace ws {
 constexpr int NA = 256, NB = 256, NT = NA + NB;
 constexpr int REG_A = 104, REG_B = 152;  // 256 x 112 + 256 x 144 = 65536 = 512 x 128 at launch
 constexpr int BAR_A = 1, BAR_FULL = 2, BAR_EMPTY = 4;
+constexpr int kMaxPlanes = 256;  // planes a CTA may visit (chunk + 6): size of the G1 / L1 table
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -669,6 +670,10 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
   uint64_t* tbar = reinterpret_cast<uint64_t*>(sm + C::OFF_RED + 2 * (NT / 32));
   volatile int* s_abort = reinterpret_cast<volatile int*>(tbar + STAGES);
   volatile int* s_last = s_abort + 1;
+  // Plain sweep: G1 (7 taps) and lambda L1 (5 taps) of every plane this CTA
+  // visits, one 16-float row per plane (read by B with three broadcast 16-byte
+  // loads).  The CG sweep, short of registers in B, reads them from global.
+  float* s_g1l1 = reinterpret_cast<float*>(tbar + 4);
   if (TMA && tid == 0) {
     for (int b = 0; b < STAGES; ++b) mbar_init1(&tbar[b]);
     // A stage off the 128-byte grid would fault the copy: give up instead
@@ -693,6 +698,10 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
     const int e = t / N4, i4 = t % N4;
     g4s[t] = a.g[3][i4 * 7 + e];
     if (e < 5) l4s[t] = a.l[3][i4 * 5 + e];
+  }
+  for (int t = tid; !CG && t < nplanes * 16; t += NT) {
+    const int pl = t >> 4, e = t & 15, jj = jb + pl;
+    s_g1l1[t] = e < 7 ? a.g[0][(int64_t)jj * 7 + e] : (e < 12 ? a.l[0][(int64_t)jj * 5 + (e - 7)] : 0.f);
   }
   __syncthreads();
 
@@ -1044,10 +1053,18 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
         for (int r = 0; r < 2; ++r) slv[r] = *reinterpret_cast<const float4*>(s_sl + (a0 + r) * ROW1 + c_off);
         __threadfence_block();
         bar_arrive(BAR_EMPTY + par, NT);  // everything B reads of plane j is in registers
+        if constexpr (CG) {
 #pragma unroll
-        for (int e = 0; e < 7; ++e) g1r[e] = __ldg(a.g[0] + (int64_t)j * 7 + e);
+          for (int e = 0; e < 7; ++e) g1r[e] = __ldg(a.g[0] + (int64_t)j * 7 + e);
 #pragma unroll
-        for (int e = 0; e < 5; ++e) l1r[e] = __ldg(a.l[0] + (int64_t)j * 5 + e);
+          for (int e = 0; e < 5; ++e) l1r[e] = __ldg(a.l[0] + (int64_t)j * 5 + e);
+        } else {
+          const float4* cr = reinterpret_cast<const float4*>(s_g1l1 + (j - jb) * 16);
+          const float4 c0v = cr[0], c1v = cr[1], c2v = cr[2];
+          g1r[0] = c0v.x; g1r[1] = c0v.y; g1r[2] = c0v.z; g1r[3] = c0v.w;
+          g1r[4] = c1v.x; g1r[5] = c1v.y; g1r[6] = c1v.z;
+          l1r[0] = c1v.w; l1r[1] = c2v.x; l1r[2] = c2v.y; l1r[3] = c2v.z; l1r[4] = c2v.w;
+        }
         const bool own_plane = (j >= c0) && (j < c1);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -1156,9 +1173,10 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
 
 constexpr size_t ws_bytes() {
   using C = Cfg<8, 16, 16, 2, NB, 3, true>;
-  // reduction scratch for 16 warps, then 3 stage mbarriers, the give-up flag
-  // and the reduction's last-block flag
-  return sizeof(float) * (size_t)(C::OFF_RED + 2 * (NT / 32)) + 3 * sizeof(uint64_t) + 16;
+  // reduction scratch for 16 warps, then 3 stage mbarriers, the give-up flag,
+  // the reduction's last-block flag and the G1 / L1 table (kMaxPlanes rows)
+  return sizeof(float) * (size_t)(C::OFF_RED + 2 * (NT / 32)) + 4 * sizeof(uint64_t) +
+         sizeof(float) * 16 * kMaxPlanes;
 }
 
 }  // namespace ws
@@ -1247,6 +1265,7 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   for (int nc = 1; nc <= n1; ++nc) {
     const int len = (n1 + nc - 1) / nc;
     if ((int64_t)tiles * nc > p->red.max_blocks) break;
+    if (len + 2 * kGramHalf > ws::kMaxPlanes) continue;
     const int64_t waves = ((int64_t)tiles * nc + p->num_sms - 1) / p->num_sms;
     const double cost = (double)waves * (len + 2 * kGramHalf);
     if (cost < best_cost - 1e-9) {
@@ -1254,10 +1273,12 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
       best_nc = nc;
     }
   }
-  if (p->fused_nchunks > 0 && (int64_t)tiles * p->fused_nchunks <= p->red.max_blocks)
+  if (p->fused_nchunks > 0 && (int64_t)tiles * p->fused_nchunks <= p->red.max_blocks &&
+      (n1 + p->fused_nchunks - 1) / p->fused_nchunks + 2 * kGramHalf <= ws::kMaxPlanes)
     best_nc = std::min(p->fused_nchunks, n1);
   p->fused_model_nchunks = best_nc;
   a.chunk = (n1 + best_nc - 1) / best_nc;
+  if (a.chunk + 2 * kGramHalf > ws::kMaxPlanes) return TCA_ERR_UNSUPPORTED;
   a.nchunks = (n1 + a.chunk - 1) / a.chunk;
   a.tiles3 = tiles3;
   const int grid = tiles * a.nchunks;

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(const float2* __restri
 // per tap, and the taps of each element accumulated in the order of
 // residual_ff_kernel (so the two give the same values).
 template <int L>
-__global__ void __launch_bounds__(256) residual_ff_vec_kernel(const float2* __restrict__ rhs,
+__global__ void __launch_bounds__(256, 4) residual_ff_vec_kernel(const float2* __restrict__ rhs,
                                                               const float2* __restrict__ kx,
                                                               const float* __restrict__ x, float* __restrict__ r_out,
                                                               int64_t total, RegFF reg, Scalars* sc, Reduce red,
