@@ -10,6 +10,11 @@ CG iterations and the FP64 true-residual check), with b resident in HBM.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle
 on the machine's host cores instead (bounded sample, extrapolated; see below).
+
+``value`` times plain solves (one graph launch each: the CG passes loop on the
+device).  The roofline's sweep time comes from a profiled solve run right after
+each timed one: the same solve with every CG sweep bracketed by CUDA events on
+the solve's stream (one graph pass per launch, the host reading the events).
 """
 from __future__ import annotations
 
@@ -543,23 +548,30 @@ def run_tca(args, rank, world, local):
     s = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 0)):
+        st, info = plan.solve(b, x, rtol=RTOL)
         st, info = plan.solve(b, x, rtol=RTOL, profile=True)
     barrier(world)
     torch.cuda.synchronize()
     tca.kernel_launches(reset=True)
     times, sweep_ms, sweep_n, infos = [], 0.0, 0, []
+    launches = 0
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            st, info = plan.solve(b, x, rtol=RTOL, profile=True)
+            st, info = plan.solve(b, x, rtol=RTOL)
             e1.record(s)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-            sweep_ms += info["sweep_ms"]
-            sweep_n += info["sweep_launches"]
             infos.append(info)
-        launches = tca.kernel_launches()
+            launches += tca.kernel_launches(reset=True)
+            # The same solve with every CG sweep bracketed by CUDA events on the
+            # solve's stream (one graph pass per launch): the sweep's live
+            # launch time for the roofline, sampled right after each timed solve.
+            st_p, info_p = plan.solve(b, x, rtol=RTOL, profile=True)
+            sweep_ms += info_p["sweep_ms"]
+            sweep_n += info_p["sweep_launches"]
+            tca.kernel_launches(reset=True)
         torch.cuda.synchronize()
     barrier(world)
     ms = max_over_ranks(statistics.mean(times), world)

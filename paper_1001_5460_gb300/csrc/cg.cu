@@ -186,13 +186,23 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(const T* __restri
                                                                int set_bnorm, Reduce red2) {
   __shared__ double sh[kVecThreads / 32];
   double a_rr = 0.0, a_bb = 0.0;
+  T p_rr = T(0), p_bb = T(0);  // short runs in T, FP64 beyond (the FP64 pipe is the slow one)
+  int cnt = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T b = rhs[i];
     const T v = kx ? (T)(b - kx[i]) : b;
     r[i] = v;
-    a_rr += (double)v * (double)v;
-    a_bb += (double)b * (double)b;
+    p_rr += v * v;
+    p_bb += b * b;
+    if (++cnt == 16) {
+      a_rr += (double)p_rr;
+      a_bb += (double)p_bb;
+      p_rr = p_bb = T(0);
+      cnt = 0;
+    }
   }
+  a_rr += (double)p_rr;
+  a_bb += (double)p_bb;
   // Two independent reductions, each with its own scratch and ticket.
   double t_rr, t_bb;
   const bool last1 = dev::grid_sum_last(a_rr, red, &t_rr, sh);
@@ -328,8 +338,65 @@ static tca_status ensure_solver_buffers(tca_plan_s* p) {
   return TCA_OK;
 }
 
+namespace {
+
+// Loop condition: one thread sets the handle from the instance's stop flags.
+__global__ void cond_running_kernel(const Scalars* sc, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, cg_done(sc) ? 0u : 1u);
+}
+
+// Conditional handle owned by the graph that stream s is capturing into.
+tca_status capture_handle(cudaStream_t s, unsigned default_value, bool assign_default, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  TCA_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive || !g) {
+    set_error_message("stream is not capturing");
+    return TCA_ERR_CUDA;
+  }
+  TCA_CUDA_TRY(cudaGraphConditionalHandleCreate(h, g, default_value, assign_default ? cudaGraphCondAssignDefault : 0));
+  return TCA_OK;
+}
+
+// Append a WHILE node on handle h to the capture sequence of s; returns its body graph.
+tca_status capture_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  TCA_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edges, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  TCA_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  TCA_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return TCA_OK;
+}
+
+// Capture `fill(stream)` into the (empty) graph g.
+template <typename F>
+tca_status capture_into(cudaGraph_t g, cudaStream_t cs, F fill) {
+  TCA_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const tca_status st = fill(cs);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (st != TCA_OK) return st;
+  TCA_CUDA_TRY(e);
+  return TCA_OK;
+}
+
+}  // namespace
+
 // Build (or reuse) the graph of `iters` iterations (a multiple of kDirBufs:
-// the direction buffers rotate) for this x buffer.
+// the direction buffers rotate) for this x buffer.  Unprofiled graphs wrap
+// the iterations in a device-side WHILE loop that runs passes until the stop
+// flags are set, so one launch finishes the iteration; profiled graphs run
+// one pass per launch (the host reads each pass's sweep events).
 template <typename T>
 static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaStream_t s) {
   if (p->graph_exec && p->graph_x == x && p->graph_iters == iters && p->graph_profiled == profile) return TCA_OK;
@@ -346,13 +413,36 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   tca_status st = TCA_OK;
+  cudaGraph_t body = nullptr;
+  cudaGraphConditionalHandle h{};
+  uint64_t after_head = before;
   if (e == cudaSuccess) {
-    for (int it = 0; it < iters && st == TCA_OK; ++it) {
-      st = enqueue_iteration<T>(p, x, it, cs, profile ? p->sweep_ev[2 * it] : nullptr,
-                                profile ? p->sweep_ev[2 * it + 1] : nullptr);
+    if (profile) {
+      for (int it = 0; it < iters && st == TCA_OK; ++it) {
+        st = enqueue_iteration<T>(p, x, it, cs, p->sweep_ev[2 * it], p->sweep_ev[2 * it + 1]);
+      }
+    } else {
+      st = capture_handle(cs, 0, false, &h);
+      if (st == TCA_OK) {
+        st = [&]() -> tca_status {
+          cond_running_kernel<<<1, 1, 0, cs>>>(p->scal, h);
+          TCA_LAUNCH_CHECK();
+          return TCA_OK;
+        }();
+      }
+      if (st == TCA_OK) st = capture_while(cs, h, &body);
+      after_head = tca_kernel_launches(0);
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
+  }
+  if (!profile && st == TCA_OK && e == cudaSuccess) {
+    st = capture_into(body, cs, [&](cudaStream_t bs) -> tca_status {
+      for (int it = 0; it < iters; ++it) TCA_TRY(enqueue_iteration<T>(p, x, it, bs, nullptr, nullptr));
+      cond_running_kernel<<<1, 1, 0, bs>>>(p->scal, h);
+      TCA_LAUNCH_CHECK();
+      return TCA_OK;
+    });
   }
   const uint64_t after = tca_kernel_launches(0);
   tca_kernel_launches(1);
@@ -377,7 +467,8 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
   p->graph_x = x;
   p->graph_iters = iters;
   p->graph_profiled = profile;
-  p->graph_launches = after - before;
+  p->graph_head_launches = after_head - before;     // kernels before the loop (unprofiled)
+  p->graph_launches = after - after_head;           // kernels per pass
   return TCA_OK;
 }
 
@@ -413,10 +504,16 @@ static tca_status cg_iterate(tca_plan_s* p, double rtol, int max_iter, int every
   while (!conv && !hs->breakdown && hs->iters < max_iter) {
     const int it_before = hs->iters;
     TCA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, s));
-    note_launches(p->graph_launches);
     TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     TCA_CUDA_TRY(cudaStreamSynchronize(s));
     conv = hs->converged != 0;
+    {
+      // Passes the launch ran: one per `every` iterations started (the last
+      // one partly returning at entry).
+      const int done = hs->iters - it_before;
+      const int passes = profile ? 1 : std::max(1, (done + every - 1) / every);
+      note_launches(p->graph_head_launches + (uint64_t)passes * p->graph_launches);
+    }
     if (profile) {
       // Iterations of this replay that did work; the rest returned at entry.
       const int ran = std::min(every, hs->iters - it_before + (hs->breakdown ? 1 : 0));
@@ -492,7 +589,6 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
     cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, inner, max_iter - total);
     TCA_LAUNCH_CHECK();
     TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(float) * N, s));
-    TCA_CUDA_TRY(cudaMemsetAsync(p->p[1], 0, sizeof(float) * N, s));
     TCA_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(float) * N, s));
     cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, nullptr, (float*)p->r, N, p->scal,
                                                           first_reduce(p), 1, second_reduce(p));
@@ -551,7 +647,6 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, rtol, max_iter);
   TCA_LAUNCH_CHECK();
   TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(T) * N, s));
-  TCA_CUDA_TRY(cudaMemsetAsync(p->p[1], 0, sizeof(T) * N, s));
   const int vgrid = std::min(vector_grid(p, N), second_reduce(p).max_blocks - 1);
   if (x0) {
     if constexpr (sizeof(T) == 4) {
@@ -632,11 +727,6 @@ namespace {
 
 constexpr int kMaxRestarts = 16;
 
-// Loop condition: one thread sets the handle from the instance's stop flags.
-__global__ void cond_running_kernel(const Scalars* sc, cudaGraphConditionalHandle h) {
-  cudaGraphSetConditional(h, cg_done(sc) ? 0u : 1u);
-}
-
 // Start-of-iteration stop test on the device (a zero right-hand side or an
 // exact initial guess), so that such an instance does no iteration at all.
 __global__ void batch_start_test_kernel(Scalars* sc) {
@@ -699,7 +789,6 @@ tca_status enqueue_setup(tca_plan_s* p, const float* b, float* x, double rtol, i
   TCA_LAUNCH_CHECK();
   const int64_t N = p->N;
   TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(float) * N, s));
-  TCA_CUDA_TRY(cudaMemsetAsync(p->p[1], 0, sizeof(float) * N, s));
   const int vgrid = std::min(vector_grid(p, N), second_reduce(p).max_blocks - 1);
   const float* kx = nullptr;
   if (x0) {
@@ -714,51 +803,6 @@ tca_status enqueue_setup(tca_plan_s* p, const float* b, float* x, double rtol, i
   TCA_LAUNCH_CHECK();
   batch_start_test_kernel<<<1, 1, 0, s>>>(p->scal);
   TCA_LAUNCH_CHECK();
-  return TCA_OK;
-}
-
-// Conditional handle owned by the graph that stream s is capturing into.
-tca_status capture_handle(cudaStream_t s, unsigned default_value, bool assign_default, cudaGraphConditionalHandle* h) {
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t g = nullptr;
-  TCA_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, nullptr, nullptr, nullptr));
-  if (cst != cudaStreamCaptureStatusActive || !g) {
-    set_error_message("stream is not capturing");
-    return TCA_ERR_CUDA;
-  }
-  TCA_CUDA_TRY(cudaGraphConditionalHandleCreate(h, g, default_value, assign_default ? cudaGraphCondAssignDefault : 0));
-  return TCA_OK;
-}
-
-// Append a WHILE node on handle h to the capture sequence of s; returns its body graph.
-tca_status capture_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  const cudaGraphEdgeData* edges = nullptr;
-  size_t nd = 0;
-  TCA_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edges, &nd));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t node;
-  TCA_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
-  *body = cp.conditional.phGraph_out[0];
-  TCA_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-  return TCA_OK;
-}
-
-// Capture `fill(stream)` into the (empty) graph g.
-template <typename F>
-tca_status capture_into(cudaGraph_t g, cudaStream_t cs, F fill) {
-  TCA_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  const tca_status st = fill(cs);
-  cudaGraph_t out = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(cs, &out);
-  if (st != TCA_OK) return st;
-  TCA_CUDA_TRY(e);
   return TCA_OK;
 }
 

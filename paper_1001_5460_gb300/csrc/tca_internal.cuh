@@ -142,7 +142,8 @@ struct tca_plan_s {
   const void* graph_x = nullptr;
   int graph_iters = 0;
   bool graph_profiled = false;
-  uint64_t graph_launches = 0;  // kernels per graph replay
+  uint64_t graph_launches = 0;       // kernels per pass of the iteration graph
+  uint64_t graph_head_launches = 0;  // kernels before its loop (unprofiled graphs)
   cudaEvent_t sweep_ev[2 * tca::kMaxProfiledIters] = {};  // start/end per iteration of a profiled graph
 
   int num_sms = 0;
