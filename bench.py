@@ -182,7 +182,7 @@ def run_batched(args, device):
     t0 = time.perf_counter()
     st, infos = tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
     torch.cuda.synchronize()
-    first_s = time.perf_counter() - t0  # graph capture + autotune + solve
+    first_s = time.perf_counter() - t0  # graph capture + solve
     for _ in range(max(args.warmup - 1, 0)):
         tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
     torch.cuda.synchronize()
@@ -217,7 +217,6 @@ def run_batched(args, device):
         "rel_res_true_max": max(i["rel_res_true"] for i in infos),
         "seq_iters_total": int(sum(i["iters"] for i in seq_infos)),
         "gpu_launches_lower_bound": int(launches),
-        "autotuned_chunks": [p.autotune() for p, i in zip(plans, insts) if i.factors[0].kind == "ell4"],
         "slowest_alone": [{"shape": list(insts[k].shape), "kind": insts[k].factors[0].kind,
                            "iters": seq_infos[k]["iters"], "ms": round(1e3 * seq_infos[k]["seconds"], 2)}
                           for k in slowest],

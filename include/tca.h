@@ -200,9 +200,11 @@ TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_
  * host or unaligned buffers give TCA_ERR_UNSUPPORTED.  opts applies to every
  * instance (rtol, max_iter, x0_given, check_every = CG iterations per pass
  * of an instance's inner loop; profile is ignored).
- * The first call for a given set of plans, buffers and options autotunes
- * the banded plans (tca_autotune) and captures one graph in which every
- * instance is an independent branch: set-up (A^T b in double-float, scalars,
+ * The first call for a given set of plans, buffers and options captures one
+ * graph in which every instance is an independent branch, its kernels sized
+ * for a quarter of the GPU's SMs so that several instances run side by side
+ * (fused-sweep chunks from the wave model at that size; tca_autotune's choice
+ * applies to single solves): set-up (A^T b in double-float, scalars,
  * first residual), then a while-conditional loop of restarts whose body runs
  * a nested while-conditional loop of check_every CG iterations until the
  * recursive residual meets rtol, recomputes the true residual in

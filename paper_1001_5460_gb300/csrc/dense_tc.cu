@@ -297,7 +297,7 @@ int tc_sm_count() {
 }  // namespace
 
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
-                           cudaStream_t s) {
+                           cudaStream_t s, int sm_cap) {
   const int n_in = (int)d.n_in, n_out = (int)d.n_out;
   if (!d.a32 || n_in <= 0 || n_out <= 0) return TCA_ERR_UNSUPPORTED;
   if ((uintptr_t)x % 16 != 0) return TCA_ERR_UNSUPPORTED;
@@ -326,7 +326,7 @@ tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, 
   // Persistent: at most one CTA per SM.  When the tile's shared memory leaves
   // room for a second CTA, both TMEM allocations fit (2 x 2 Np <= 512 columns
   // for Np <= 128) or the second waits for the first to free its columns.
-  const int64_t grid = std::min<int64_t>(g.tiles, (int64_t)tc_sm_count());
+  const int64_t grid = std::min<int64_t>(g.tiles, (int64_t)(sm_cap > 0 ? std::min(sm_cap, tc_sm_count()) : tc_sm_count()));
   dense_tc_kernel<<<(unsigned)std::max<int64_t>(grid, 1), kTcThreads, bytes, s>>>(x, y, d.a32, g,
                                                                                   wait_timeout_flag());
   TCA_LAUNCH_CHECK();

@@ -213,10 +213,10 @@ tca_status launch_mode_op(const ModeOp& op, const Tin* x, Tout* y, int64_t O, in
   if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4 && sizeof(Tc) == 4) {
     // FP32 bands: TMA-staged row tiles or register fibres when the shape allows.
     if (!dense) {
-      const tca_status st = launch_band_fast(op.band, (const float*)x, (float*)y, O, I, s);
+      const tca_status st = launch_band_fast(op.band, (const float*)x, (float*)y, O, I, s, op.sm_cap);
       if (st != TCA_ERR_UNSUPPORTED) return st;
     } else if (op.tc_split > 0) {
-      const tca_status st = launch_dense_tc(op.dense, (const float*)x, (float*)y, O, I, op.tc_split, s);
+      const tca_status st = launch_dense_tc(op.dense, (const float*)x, (float*)y, O, I, op.tc_split, s, op.sm_cap);
       if (st != TCA_ERR_UNSUPPORTED) return st;
     }
   }

@@ -300,9 +300,10 @@ bool row_tile_shape(int64_t O, int64_t I, int RB, int* Ti, int* To) {
 }
 
 template <int NIN, int NOUT>
-tca_status launch_fibre(const Band& band, const float* x, float* y, int64_t O, cudaStream_t s) {
+tca_status launch_fibre(const Band& band, const float* x, float* y, int64_t O, cudaStream_t s, int sm_cap) {
   const int64_t want = (O + kThreads - 1) / kThreads;
-  const int64_t grid = std::min<int64_t>(want, (int64_t)sm_count() * 8);
+  const int sms = sm_cap > 0 ? std::min(sm_cap, sm_count()) : sm_count();
+  const int64_t grid = std::min<int64_t>(want, (int64_t)sms * 8);
   band_fibre_kernel<NIN, NOUT><<<(unsigned)grid, kThreads, 0, s>>>(x, y, O, band.start, band.w32, band.W);
   TCA_LAUNCH_CHECK();
   return TCA_OK;
@@ -310,12 +311,13 @@ tca_status launch_fibre(const Band& band, const float* x, float* y, int64_t O, c
 
 }  // namespace
 
-tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t O, int64_t I, cudaStream_t s) {
+tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t O, int64_t I, cudaStream_t s,
+                            int sm_cap) {
   const int n_in = (int)band.n_in, n_out = (int)band.n_out, W = band.W;
   if ((uintptr_t)x % 16 != 0 || (uintptr_t)y % 16 != 0) return TCA_ERR_UNSUPPORTED;
   if (I == 1) {
 #define TCA_FIBRE(a, b) \
-  if (n_in == a && n_out == b) return launch_fibre<a, b>(band, x, y, O, s);
+  if (n_in == a && n_out == b) return launch_fibre<a, b>(band, x, y, O, s, sm_cap);
     TCA_FIBRE(8, 8)
     TCA_FIBRE(8, 12)
     TCA_FIBRE(12, 8)
@@ -361,7 +363,8 @@ tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t 
   g.stages = per_sm > 0
                  ? (int)std::max<size_t>(2, std::min<size_t>(3, (200 * 1024) / (per_sm * stage_bytes)))
                  : 1;
-  const int64_t grid = per_sm > 0 ? std::min<int64_t>(g.tiles, (int64_t)sm_count() * per_sm) : g.tiles;
+  const int sms = sm_cap > 0 ? std::min(sm_cap, sm_count()) : sm_count();
+  const int64_t grid = per_sm > 0 ? std::min<int64_t>(g.tiles, (int64_t)sms * per_sm) : g.tiles;
   if (grid > ((int64_t)1 << 31) - 1) return TCA_ERR_UNSUPPORTED;
   const size_t sm = sizeof(float) * (size_t)g.stages * g.stage_floats + 128 + 8 * g.stages;
   static bool attr = false;

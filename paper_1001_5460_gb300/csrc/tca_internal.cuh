@@ -48,6 +48,7 @@ struct ModeOp {
   Band band;
   Dense dense;
   int tc_split = 0;  // dense FP32 products on tensor cores: 0 off, 1 TF32, 2 3xTF32
+  int sm_cap = 0;    // SMs its persistent kernels may fill (0: the whole GPU; set by batched solves)
   int64_t n_out() const { return kind == OP_BAND ? band.n_out : dense.n_out; }
   int64_t n_in() const { return kind == OP_BAND ? band.n_in : dense.n_in; }
 };
@@ -225,11 +226,12 @@ tca_status residual_ff(tca_plan_s* p, const float* x, const float2* rhs_ff, floa
 
 // TMA-staged / register-fibre banded mode products (mode_tma.cu); UNSUPPORTED
 // when the shape or alignment does not fit, so callers fall back.
-tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t O, int64_t I, cudaStream_t s);
+tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t O, int64_t I, cudaStream_t s,
+                            int sm_cap = 0);
 int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W);
 // Dense mode product on tcgen05 tensor cores (dense_tc.cu); split 1 = TF32, 2 = 3xTF32.
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
-                           cudaStream_t s);
+                           cudaStream_t s, int sm_cap = 0);
 tca_status read_wait_timeout(int* flag, bool reset);
 // Device address of the wait-timeout flag (for kernels in other translation units).
 int* wait_timeout_flag();
