@@ -473,14 +473,6 @@ tca_status wait_selftest(long long polls, cudaStream_t s) {
   return check_wait_timeout(s);
 }
 
-tca_status read_wait_timeout(int* flag, bool reset) {
-  TCA_CUDA_TRY(cudaMemcpyFromSymbol(flag, g_wait_timeout, sizeof(int)));
-  if (reset && *flag) {
-    const int zero = 0;
-    TCA_CUDA_TRY(cudaMemcpyToSymbol(g_wait_timeout, &zero, sizeof(int)));
-  }
-  return TCA_OK;
-}
 
 }  // namespace tca
 

@@ -232,7 +232,6 @@ int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W);
 // Dense mode product on tcgen05 tensor cores (dense_tc.cu); split 1 = TF32, 2 = 3xTF32.
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
                            cudaStream_t s, int sm_cap = 0);
-tca_status read_wait_timeout(int* flag, bool reset);
 // Device address of the wait-timeout flag (for kernels in other translation units).
 int* wait_timeout_flag();
 // Synchronise s; TCA_ERR_TIMEOUT (and clear the flag) if a bounded wait gave up.
