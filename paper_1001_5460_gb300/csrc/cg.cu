@@ -619,7 +619,7 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
 
 template <typename T>
 static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_solve_opts* o, tca_solve_info* info,
-                             cudaStream_t s) {
+                             cudaStream_t s, void* x_host = nullptr) {
   const auto t0 = std::chrono::steady_clock::now();
   TCA_TRY(ensure_solver_buffers<T>(p));
   const int64_t N = p->N;
@@ -671,6 +671,17 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   for (;;) {
     TCA_TRY(cg_iterate(p, rtol, max_iter, every, profile, &sweep_ms, &sweep_n, s));
     TCA_TRY(flush_pending_x<T>(p, x, s));
+    if (x_host) {
+      // x is final for this round: copy it to the host on a side stream while
+      // the true residual is computed (a restart re-copies after its round).
+      if (!p->copy_stream) {
+        TCA_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        TCA_CUDA_TRY(cudaEventCreateWithFlags(&p->copy_ev, cudaEventDisableTiming));
+      }
+      TCA_CUDA_TRY(cudaEventRecord(p->copy_ev, s));
+      TCA_CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->copy_ev, 0));
+      TCA_CUDA_TRY(cudaMemcpyAsync(x_host, x, sizeof(T) * (size_t)p->N, cudaMemcpyDeviceToHost, p->copy_stream));
+    }
     if (hs->breakdown) {
       status = TCA_ERR_BREAKDOWN;
       break;
@@ -694,6 +705,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
                                                       first_reduce(p), 0, second_reduce(p));
     TCA_LAUNCH_CHECK();
   }
+  if (x_host && p->copy_stream) TCA_CUDA_TRY(cudaStreamSynchronize(p->copy_stream));
   if (info) {
     info->iters = hs->iters;
     info->refinements = restarts;
@@ -1026,10 +1038,14 @@ extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const t
     dx = p->stage_x;
   }
   tca_status st;
-  if (p->prec == TCA_F64) st = solve_impl<double>(p, db, (double*)dx, opts, info, stream);
-  else if (p->prec == TCA_F32) st = solve_impl<float>(p, db, (float*)dx, opts, info, stream);
+  // Host x that the device can copy into directly: the solve copies x back
+  // itself, overlapped with its final true-residual check.
+  void* x_back = (!x_dev && !is_device_ptr(x)) ? x : nullptr;
+  if (p->prec == TCA_F64) st = solve_impl<double>(p, db, (double*)dx, opts, info, stream, x_back);
+  else if (p->prec == TCA_F32) st = solve_impl<float>(p, db, (float*)dx, opts, info, stream, x_back);
   else st = solve_ir(p, db, (float*)dx, opts, info, stream);
-  if (!x_dev && (st == TCA_OK || st == TCA_ERR_NOT_CONVERGED || st == TCA_ERR_BREAKDOWN)) {
+  const bool copied = x_back && (p->prec == TCA_F64 || p->prec == TCA_F32);
+  if (!x_dev && !copied && (st == TCA_OK || st == TCA_ERR_NOT_CONVERGED || st == TCA_ERR_BREAKDOWN)) {
     TCA_CUDA_TRY(cudaMemcpyAsync(x, p->stage_x, es * (size_t)p->N, cudaMemcpyDefault, stream));
     TCA_CUDA_TRY(cudaStreamSynchronize(stream));
   }

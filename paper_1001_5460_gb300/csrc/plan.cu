@@ -330,6 +330,8 @@ static void destroy_plan(tca_plan_s* p) {
   cudaFree(p->dbuf);
   cudaFree(p->stage_x);
   cudaFree(p->stage_b);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->copy_ev) cudaEventDestroy(p->copy_ev);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (cudaEvent_t& ev : p->sweep_ev)
     if (ev) cudaEventDestroy(ev);

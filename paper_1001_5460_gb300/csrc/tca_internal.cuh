@@ -133,6 +133,8 @@ struct tca_plan_s {
   float* dbuf = nullptr;    // refinement correction d (mixed-precision plans)
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
+  cudaStream_t copy_stream = nullptr;  // host-pointer solves: x copied back under the true residual
+  cudaEvent_t copy_ev = nullptr;
 
   tca::Scalars* scal = nullptr;  // device
   tca::Scalars* scal_host = nullptr;  // pinned mirror

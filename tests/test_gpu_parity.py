@@ -161,21 +161,26 @@ def test_solve_bspline_fp32(shape):
     assert abs(info["rel_res_true"] - O.rel_residual(got, b.astype(np.float64), mats, inst.lam)) < 1e-7
 
 
-def test_solve_host_buffers_match_device():
+@pytest.mark.parametrize("prec", ["f32", "f64", "tf32_ir"])
+def test_solve_host_buffers_match_device(prec):
+    """Host (pageable and pinned) buffers give the device-buffer result bit for bit; the
+    plain plans copy x back under their final true-residual check, the _IR plan after."""
     tca = lib()
     torch = need_cuda()
+    dt = np.float64 if prec == "f64" else np.float32
+    tdt = torch.float64 if prec == "f64" else torch.float32
     inst = synth.instance_bspline((24, 20, 22, 8), seed=500, dtype=np.float64)
     mats = [f.dense() for f in inst.factors]
-    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
-    plan = tca.plan_from_instance(inst, precision="f32")
-    xd = empty_dev(inst.shape, np.float32)
-    plan.solve(to_dev(b, np.float32), xd, rtol=1e-6)
-    xh = np.zeros(inst.shape, np.float32)
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(dt)
+    plan = tca.plan_from_instance(inst, precision=prec)
+    xd = empty_dev(inst.shape, dt)
+    plan.solve(to_dev(b, dt), xd, rtol=1e-6)
+    xh = np.zeros(inst.shape, dt)
     st, info = plan.solve(np.ascontiguousarray(b), xh, rtol=1e-6)
     assert st == tca.OK
     np.testing.assert_array_equal(xh, xd.cpu().numpy())
     pinned = torch.from_numpy(b).pin_memory()
-    xp = torch.zeros(inst.shape, dtype=torch.float32).pin_memory()
+    xp = torch.zeros(inst.shape, dtype=tdt).pin_memory()
     plan.solve(pinned, xp, rtol=1e-6)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(xp.numpy(), xd.cpu().numpy())
