@@ -36,11 +36,27 @@ struct Acc2 {
     s = t;
     c += err + pe;
   }
+  // += (wh + wl) * x for an FP32 (exact, single-float) x: the same sum without
+  // the product with x's zero low part.
+  __device__ __forceinline__ void add_x(float wh, float wl, float x) {
+    const float ph = wh * x;
+    float pe = fmaf(wh, x, -ph);
+    pe = fmaf(wl, x, pe);
+    const float t = s + ph;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (ph - bb);
+    s = t;
+    c += err + pe;
+  }
   __device__ __forceinline__ float2 result() const {  // FastTwoSum(s, c)
     const float h = s + c;
     return make_float2(h, c - (h - s));
   }
 };
+
+// acc += c * v, v an FP32 value (low part zero) or a double-float pair.
+__device__ __forceinline__ void acc_add(Acc2& acc, float2 c, float v) { acc.add_x(c.x, c.y, v); }
+__device__ __forceinline__ void acc_add(Acc2& acc, float2 c, float2 v) { acc.add(c.x, c.y, v.x, v.y); }
 
 template <typename T> __device__ __forceinline__ float2 as_ff(T v);
 template <> __device__ __forceinline__ float2 as_ff<float>(float v) { return make_float2(v, 0.f); }
@@ -97,11 +113,10 @@ __global__ void __launch_bounds__(256) band_ff_inner_kernel(const Tin* __restric
   }
 }
 
-// Four consecutive elements (16-byte aligned) as double-float pairs.
-__device__ __forceinline__ void load4_ff(const float* p, float2 (&v)[4]) {
+// Four consecutive elements (16-byte aligned): FP32 values or double-float pairs.
+__device__ __forceinline__ void load4_ff(const float* p, float (&v)[4]) {
   const float4 a = *reinterpret_cast<const float4*>(p);
-  v[0] = make_float2(a.x, 0.f); v[1] = make_float2(a.y, 0.f);
-  v[2] = make_float2(a.z, 0.f); v[3] = make_float2(a.w, 0.f);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
 __device__ __forceinline__ void load4_ff(const float2* p, float2 (&v)[4]) {
   const float4 a = reinterpret_cast<const float4*>(p)[0];
@@ -121,20 +136,20 @@ __device__ __forceinline__ void taps4(Acc2 (&acc)[4], const Tin* x0, int64_t pit
 #pragma unroll 2
     for (int e = 0; e < W; ++e) {
       const float2 c = wj[e];
-      float2 v[4];
+      Tin v[4];
       load4_ff(xr + (int64_t)e * pitch, v);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q].add(c.x, c.y, v[q].x, v[q].y);
+      for (int q = 0; q < 4; ++q) acc_add(acc[q], c, v[q]);
     }
   } else {
     for (int e = 0; e < W; ++e) {
       const int l = s0 + e;
       if (l < 0 || l >= n_in) continue;
       const float2 c = wj[e];
-      float2 v[4];
+      Tin v[4];
       load4_ff(x0 + (int64_t)l * pitch, v);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q].add(c.x, c.y, v[q].x, v[q].y);
+      for (int q = 0; q < 4; ++q) acc_add(acc[q], c, v[q]);
     }
   }
 }
@@ -270,8 +285,8 @@ __global__ void __launch_bounds__(256) band_ff_outer_kernel(const Tin* __restric
           const float2 c = wj[e];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 v = q < nq ? as_ff(xf[q * sin + l]) : make_float2(0.f, 0.f);
-            acc[q].add(c.x, c.y, v.x, v.y);
+            const Tin v = q < nq ? xf[q * sin + l] : Tin{};
+            acc_add(acc[q], c, v);
           }
         }
 #pragma unroll
@@ -297,8 +312,8 @@ __global__ void __launch_bounds__(256) band_ff_outer_kernel(const Tin* __restric
           const int l = s0 + e;
           const bool ok = l >= 0 && l < n_in;
           const float2 c = ok ? w[(int64_t)j * W + e] : make_float2(0.f, 0.f);
-          const float2 v = ok ? as_ff(xf[l * I]) : make_float2(0.f, 0.f);
-          acc.add(c.x, c.y, v.x, v.y);
+          const Tin v = ok ? xf[l * I] : Tin{};
+          acc_add(acc, c, v);
         }
         const float2 r = acc.result();
         const int64_t oi = o0 * sout + t;
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(const float2* __restri
         const int64_t c = im - 2 + e;
         if (c >= 0 && c < reg.n[m]) {
           const float2 cf = wm[e];
-          acc.add(-cf.x, -cf.y, __ldg(x + idx + (c - im) * reg.stride[m]), 0.f);
+          acc.add_x(-cf.x, -cf.y, __ldg(x + idx + (c - im) * reg.stride[m]));
         }
       }
     }
@@ -421,7 +436,7 @@ __global__ void __launch_bounds__(256, 4) residual_ff_vec_kernel(const float2* _
             const int c = row - 2 + e;
             if (c >= 0 && c < nL) {
               const float2 cf = wm[e];
-              acc[i].add(-cf.x, -cf.y, win[i + 2 + e], 0.f);
+              acc[i].add_x(-cf.x, -cf.y, win[i + 2 + e]);
             }
           }
         }
@@ -441,7 +456,7 @@ __global__ void __launch_bounds__(256, 4) residual_ff_vec_kernel(const float2* _
               xv[0] = t.x; xv[1] = t.y; xv[2] = t.z; xv[3] = t.w;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i].add(-cf.x, -cf.y, xv[i], 0.f);
+            for (int i = 0; i < 4; ++i) acc[i].add_x(-cf.x, -cf.y, xv[i]);
           }
         }
       }
