@@ -617,9 +617,18 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
   return status;
 }
 
+// Side stream and events for host-buffer solves (created on first use).
+static tca_status ensure_copy_stream(tca_plan_s* p) {
+  if (p->copy_stream) return TCA_OK;
+  TCA_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  TCA_CUDA_TRY(cudaEventCreateWithFlags(&p->copy_ev, cudaEventDisableTiming));
+  for (cudaEvent_t& ev : p->chunk_ev) TCA_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  return TCA_OK;
+}
+
 template <typename T>
 static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_solve_opts* o, tca_solve_info* info,
-                             cudaStream_t s, void* x_host = nullptr) {
+                             cudaStream_t s, void* x_host = nullptr, const void* b_host = nullptr) {
   const auto t0 = std::chrono::steady_clock::now();
   TCA_TRY(ensure_solver_buffers<T>(p));
   const int64_t N = p->N;
@@ -639,7 +648,21 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   // the iteration.  FP64 plans: native FP64.
   if constexpr (sizeof(T) == 4) {
     TCA_TRY(ensure_ws64_public(p));
-    TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
+    tca_status up = TCA_ERR_UNSUPPORTED;
+    if (b_host) {
+      // b from the host: uploaded in row runs under A^T b's first mode product.
+      TCA_TRY(ensure_copy_stream(p));
+      up = chain_ff_rhs_from_host(p, (const float*)b_host, (float*)p->stage_b, reinterpret_cast<float2*>(p->rhs64),
+                                  (float*)p->rhs, reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s,
+                                  p->copy_stream, p->chunk_ev, 8);
+      if (up != TCA_OK && up != TCA_ERR_UNSUPPORTED) return up;
+      if (up == TCA_ERR_UNSUPPORTED) {
+        TCA_CUDA_TRY(cudaMemcpyAsync(p->stage_b, b_host, sizeof(float) * (size_t)p->M, cudaMemcpyHostToDevice, s));
+        b_in = p->stage_b;
+      }
+    }
+    if (up != TCA_OK)
+      TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
                      reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
   } else {
     TCA_TRY((apply_chain<T, T, T>(p, true, (const T*)b_in, (T*)p->rhs, p->ws, p->ws_elems, s)));
@@ -674,10 +697,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
     if (x_host) {
       // x is final for this round: copy it to the host on a side stream while
       // the true residual is computed (a restart re-copies after its round).
-      if (!p->copy_stream) {
-        TCA_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
-        TCA_CUDA_TRY(cudaEventCreateWithFlags(&p->copy_ev, cudaEventDisableTiming));
-      }
+      TCA_TRY(ensure_copy_stream(p));
       TCA_CUDA_TRY(cudaEventRecord(p->copy_ev, s));
       TCA_CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->copy_ev, 0));
       TCA_CUDA_TRY(cudaMemcpyAsync(x_host, x, sizeof(T) * (size_t)p->N, cudaMemcpyDeviceToHost, p->copy_stream));
@@ -1028,7 +1048,9 @@ extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const t
   const void* db = b;
   void* dx = x;
   if (!b_dev || !x_dev) TCA_TRY(ensure_stage(p));
-  if (!b_dev) {
+  // FP32 plans take a host b themselves (uploaded under A^T b).
+  const void* b_up = (!b_dev && p->prec == TCA_F32 && !is_device_ptr(b)) ? b : nullptr;
+  if (!b_dev && !b_up) {
     TCA_CUDA_TRY(cudaMemcpyAsync(p->stage_b, b, es * (size_t)p->M, cudaMemcpyHostToDevice, stream));
     db = p->stage_b;
   }
@@ -1042,7 +1064,7 @@ extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const t
   // itself, overlapped with its final true-residual check.
   void* x_back = (!x_dev && !is_device_ptr(x)) ? x : nullptr;
   if (p->prec == TCA_F64) st = solve_impl<double>(p, db, (double*)dx, opts, info, stream, x_back);
-  else if (p->prec == TCA_F32) st = solve_impl<float>(p, db, (float*)dx, opts, info, stream, x_back);
+  else if (p->prec == TCA_F32) st = solve_impl<float>(p, db, (float*)dx, opts, info, stream, x_back, b_up);
   else st = solve_ir(p, db, (float*)dx, opts, info, stream);
   const bool copied = x_back && (p->prec == TCA_F64 || p->prec == TCA_F32);
   if (!x_dev && !copied && (st == TCA_OK || st == TCA_ERR_NOT_CONVERGED || st == TCA_ERR_BREAKDOWN)) {

@@ -218,6 +218,7 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     TCA_TRY(dmalloc(&bb.w64, n * W));
     TCA_TRY(dmalloc(&bb.w32, n * W));
     TCA_CUDA_TRY(cudaMemcpyAsync(bb.start, ts.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    bb.start_host.assign(ts.begin(), ts.end());
     TCA_CUDA_TRY(cudaMemcpyAsync(bb.w64, wt.data(), sizeof(double) * n * W, cudaMemcpyHostToDevice, s));
     cast_kernel<<<nblk(n * W), 256, 0, s>>>(bb.w64, bb.w32, n * W);
     TCA_LAUNCH_CHECK();
@@ -332,6 +333,8 @@ static void destroy_plan(tca_plan_s* p) {
   cudaFree(p->stage_b);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   if (p->copy_ev) cudaEventDestroy(p->copy_ev);
+  for (cudaEvent_t& ev : p->chunk_ev)
+    if (ev) cudaEventDestroy(ev);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (cudaEvent_t& ev : p->sweep_ev)
     if (ev) cudaEventDestroy(ev);

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) band_ff_inner4_kernel(const Tin* __restri
                                                              float* __restrict__ y32, int n_in, int n_out, int64_t I,
                                                              const int32_t* __restrict__ start,
                                                              const float2* __restrict__ w, int W, int64_t i_chunks,
-                                                             int j_chunks) {
+                                                             int j_chunks, int j_begin, int j_end) {
   constexpr int JT = 4;
   const int64_t b = blockIdx.x;
   const int jc = (int)(b % j_chunks);
@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(256) band_ff_inner4_kernel(const Tin* __restri
   const Tin* xo = x + o * (int64_t)n_in * I + i;
 #pragma unroll 1
   for (int t = 0; t < JT; ++t) {
-    const int j = jc * (4 * JT) + threadIdx.y + 4 * t;
-    if (j >= n_out) break;
+    const int j = j_begin + jc * (4 * JT) + threadIdx.y + 4 * t;
+    if (j >= j_end) break;
     Acc2 acc[4];
     taps4<Tin>(acc, xo, I, start[j], W, n_in, w + (int64_t)j * W);
     store4_ff(y, y32, (o * (int64_t)n_out + j) * I + i, acc);
@@ -512,7 +512,7 @@ static tca_status launch_ff(const int32_t* start, const float2* w, int W, int n_
     const int64_t ich = (I / 4 + 63) / 64;
     const int jch = (n_out + 15) / 16;
     band_ff_inner4_kernel<Tin><<<(unsigned)(O * ich * jch), dim3(64, 4), 0, s>>>(x, y, y32, n_in, n_out, I, start,
-                                                                                 w, W, ich, jch);
+                                                                                 w, W, ich, jch, 0, n_out);
   } else if (I >= 32) {
     const int64_t ich = (I + 63) / 64;
     const int jch = (n_out + 31) / 32;
@@ -590,6 +590,82 @@ tca_status chain_ff(tca_plan_s* p, bool transpose, bool gram, const float* x, fl
       TCA_TRY(launch_ff<float>(start, w, W, n_in, n_out, (const float*)src, dst, last ? y32 : nullptr, O, I, s));
     else
       TCA_TRY(launch_ff<float2>(start, w, W, n_in, n_out, (const float2*)src, dst, last ? y32 : nullptr, O, I, s));
+    src = dst;
+  }
+  return TCA_OK;
+}
+
+// A^T b for a host b (FP32), overlapped with its upload, in the plan's own
+// mode order and arithmetic (bit-identical to chain_ff on a device copy of b).
+// The first product of that order must run on the inner layout with O = 1
+// (its mode is the outermost): b then arrives in `chunks` contiguous runs of
+// that mode's rows (one copy each on cs, each with an event), and after each
+// run the output rows whose band lies entirely in the rows received so far are
+// computed.  The other modes follow as in chain_ff.  TCA_ERR_UNSUPPORTED when
+// the first product is not of that form (the caller uploads b whole).
+tca_status chain_ff_rhs_from_host(tca_plan_s* p, const float* b_host, float* b_stage, float2* y, float* y32,
+                                  float2* const* ws, int64_t ws_elems, cudaStream_t s, cudaStream_t cs,
+                                  cudaEvent_t* ev, int chunks) {
+  const int d = p->d;
+  if (d < 2) return TCA_ERR_UNSUPPORTED;
+  int64_t cur[kMaxModes];
+  for (int k = 0; k < d; ++k) cur[k] = p->m[k];
+  const int k0 = p->order_bwd[0];
+  const ModeOp& op0 = p->mode[k0].bwd;
+  if (op0.kind != OP_BAND || (int64_t)op0.band.start_host.size() != op0.band.n_out) return TCA_ERR_UNSUPPORTED;
+  int64_t O = 1, I = 1;
+  for (int a = 0; a < k0; ++a) O *= cur[a];
+  for (int a = k0 + 1; a < d; ++a) I *= cur[a];
+  const int n_in0 = (int)op0.n_in(), n_out0 = (int)op0.n_out();
+  const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
+  if (O != 1 || I % 4 != 0 || I < 32 || n_in0 < chunks || !al16(b_stage) || !al16(ws[0]) || !al16(b_host) ||
+      I * n_out0 > ws_elems)
+    return TCA_ERR_UNSUPPORTED;
+  const std::vector<int32_t>& st0 = op0.band.start_host;
+  const int W0 = op0.band.W;
+  float2* dst0 = ws[0];
+  const int64_t ich = (I / 4 + 63) / 64;
+  int j_done = 0;
+  for (int c = 0; c < chunks; ++c) {
+    const int64_t r0 = (int64_t)n_in0 * c / chunks, r1 = (int64_t)n_in0 * (c + 1) / chunks;
+    if (r1 <= r0) continue;
+    TCA_CUDA_TRY(cudaMemcpyAsync(b_stage + r0 * I, b_host + r0 * I, sizeof(float) * (size_t)((r1 - r0) * I),
+                                 cudaMemcpyHostToDevice, cs));
+    TCA_CUDA_TRY(cudaEventRecord(ev[c], cs));
+    TCA_CUDA_TRY(cudaStreamWaitEvent(s, ev[c], 0));
+    // Output rows whose taps (clipped to [0, n_in)) lie below row r1.
+    int j_hi = j_done;
+    if (c == chunks - 1) {
+      j_hi = n_out0;
+    } else {
+      while (j_hi < n_out0 && std::min<int64_t>((int64_t)st0[j_hi] + W0, n_in0) <= r1) ++j_hi;
+    }
+    if (j_hi > j_done) {
+      const int jch = (j_hi - j_done + 15) / 16;
+      band_ff_inner4_kernel<float><<<(unsigned)(ich * jch), dim3(64, 4), 0, s>>>(
+          b_stage, dst0, nullptr, n_in0, n_out0, I, op0.band.start, op0.band.wff, W0, ich, jch, j_done, j_hi);
+      TCA_LAUNCH_CHECK();
+      j_done = j_hi;
+    }
+  }
+  cur[k0] = n_out0;
+  const void* src = dst0;
+  const int32_t* start;
+  const float2* w;
+  int W;
+  for (int st = 1; st < d; ++st) {
+    const int k = p->order_bwd[st];
+    const ModeOp& op = p->mode[k].bwd;
+    int64_t Ok = 1, Ik = 1;
+    for (int a = 0; a < k; ++a) Ok *= cur[a];
+    for (int a = k + 1; a < d; ++a) Ik *= cur[a];
+    const int n_in = (int)op.n_in(), n_out = (int)op.n_out();
+    cur[k] = n_out;
+    const bool last = st == d - 1;
+    if (!last && Ok * Ik * n_out > ws_elems) return TCA_ERR_SHAPE;
+    float2* dst = last ? y : ws[st % 2];
+    op_band_ff(op, &start, &w, &W);
+    TCA_TRY(launch_ff<float2>(start, w, W, n_in, n_out, (const float2*)src, dst, last ? y32 : nullptr, Ok, Ik, s));
     src = dst;
   }
   return TCA_OK;

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
+#include <vector>
 
 #include "../../include/tca.h"
 
@@ -30,6 +31,7 @@ struct Band {
   float2* wff = nullptr;     // device, n_out * W: w64 split into (hi, lo) floats
   int rows32 = 0;            // input rows spanned by any 32 consecutive outputs (TMA tile height)
   bool unit = false;         // start[j] = start[0] + j (Gram and regulariser bands)
+  std::vector<int32_t> start_host;  // host copy of start (transposed-factor bands)
 };
 
 // Row-major n_out x n_in matrix.
@@ -133,8 +135,9 @@ struct tca_plan_s {
   float* dbuf = nullptr;    // refinement correction d (mixed-precision plans)
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
-  cudaStream_t copy_stream = nullptr;  // host-pointer solves: x copied back under the true residual
-  cudaEvent_t copy_ev = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host-pointer solves: b uploaded under A^T b, x copied back
+  cudaEvent_t copy_ev = nullptr;       // under the true residual
+  cudaEvent_t chunk_ev[8] = {};
 
   tca::Scalars* scal = nullptr;  // device
   tca::Scalars* scal_host = nullptr;  // pinned mirror
@@ -223,6 +226,9 @@ int vector_grid(const tca_plan_s* p, int64_t n);
 tca_status split_ff(const double* a, float2* b, int64_t n, cudaStream_t s);
 tca_status chain_ff(tca_plan_s* p, bool transpose, bool gram, const float* x, float2* y, float* y32,
                     float2* const* ws, int64_t ws_elems, cudaStream_t s);
+tca_status chain_ff_rhs_from_host(tca_plan_s* p, const float* b_host, float* b_stage, float2* y, float* y32,
+                                  float2* const* ws, int64_t ws_elems, cudaStream_t s, cudaStream_t cs,
+                                  cudaEvent_t* ev, int chunks);
 tca_status residual_ff(tca_plan_s* p, const float* x, const float2* rhs_ff, float2* kx_ff, float* r_out,
                        Reduce red, Reduce red2, cudaStream_t s);
 
