@@ -598,38 +598,53 @@ tca_status chain_ff(tca_plan_s* p, bool transpose, bool gram, const float* x, fl
 // A^T b for a host b (FP32), overlapped with its upload, in the plan's own
 // mode order and arithmetic (bit-identical to chain_ff on a device copy of b).
 // The first product of that order must run on the inner layout with O = 1
-// (its mode is the outermost): b then arrives in `chunks` contiguous runs of
-// that mode's rows (one copy each on cs, each with an event), and after each
-// run the output rows whose band lies entirely in the rows received so far are
-// computed.  The other modes follow as in chain_ff.  TCA_ERR_UNSUPPORTED when
-// the first product is not of that form (the caller uploads b whole).
+// (its mode is the outermost).  b arrives in `chunks` contiguous runs of that
+// mode's rows (one copy each on cs, each with an event); after each run, the
+// output rows of the first product whose band lies entirely in the rows
+// received so far are computed, and so are those rows' slabs of every later
+// product (the other modes act within a slab of the outermost index), so the
+// chain trails the upload by one run.  TCA_ERR_UNSUPPORTED when the first
+// product is not of that form (the caller uploads b whole).
 tca_status chain_ff_rhs_from_host(tca_plan_s* p, const float* b_host, float* b_stage, float2* y, float* y32,
                                   float2* const* ws, int64_t ws_elems, cudaStream_t s, cudaStream_t cs,
                                   cudaEvent_t* ev, int chunks) {
   const int d = p->d;
   if (d < 2) return TCA_ERR_UNSUPPORTED;
-  int64_t cur[kMaxModes];
-  for (int k = 0; k < d; ++k) cur[k] = p->m[k];
   const int k0 = p->order_bwd[0];
   const ModeOp& op0 = p->mode[k0].bwd;
-  if (op0.kind != OP_BAND || (int64_t)op0.band.start_host.size() != op0.band.n_out) return TCA_ERR_UNSUPPORTED;
-  int64_t O = 1, I = 1;
-  for (int a = 0; a < k0; ++a) O *= cur[a];
-  for (int a = k0 + 1; a < d; ++a) I *= cur[a];
-  const int n_in0 = (int)op0.n_in(), n_out0 = (int)op0.n_out();
+  if (k0 != 0 || op0.kind != OP_BAND || (int64_t)op0.band.start_host.size() != op0.band.n_out)
+    return TCA_ERR_UNSUPPORTED;
+  // Extents after each step and the per-step geometry (O and I per unit of the outermost index).
+  int64_t cur[kMaxModes];
+  for (int k = 0; k < d; ++k) cur[k] = p->m[k];
+  int64_t Pk[kMaxModes], Ik[kMaxModes];
+  int nin[kMaxModes], nout[kMaxModes];
+  for (int st = 0; st < d; ++st) {
+    const int k = p->order_bwd[st];
+    const ModeOp& op = p->mode[k].bwd;
+    int64_t P = 1, I = 1;
+    for (int a = 1; a < k; ++a) P *= cur[a];
+    for (int a = k + 1; a < d; ++a) I *= cur[a];
+    Pk[st] = P;
+    Ik[st] = I;
+    nin[st] = (int)op.n_in();
+    nout[st] = (int)op.n_out();
+    cur[k] = nout[st];
+    if (st < d - 1 && (k == 0 ? 1 : cur[0]) * P * I * nout[st] > ws_elems) return TCA_ERR_UNSUPPORTED;
+  }
+  const int64_t I0 = Ik[0];
+  const int n_in0 = nin[0], n_out0 = nout[0];
   const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
-  if (O != 1 || I % 4 != 0 || I < 32 || n_in0 < chunks || !al16(b_stage) || !al16(ws[0]) || !al16(b_host) ||
-      I * n_out0 > ws_elems)
+  if (I0 % 4 != 0 || I0 < 32 || n_in0 < chunks || !al16(b_stage) || !al16(ws[0]) || !al16(b_host))
     return TCA_ERR_UNSUPPORTED;
   const std::vector<int32_t>& st0 = op0.band.start_host;
   const int W0 = op0.band.W;
-  float2* dst0 = ws[0];
-  const int64_t ich = (I / 4 + 63) / 64;
+  const int64_t ich = (I0 / 4 + 63) / 64;
   int j_done = 0;
   for (int c = 0; c < chunks; ++c) {
     const int64_t r0 = (int64_t)n_in0 * c / chunks, r1 = (int64_t)n_in0 * (c + 1) / chunks;
     if (r1 <= r0) continue;
-    TCA_CUDA_TRY(cudaMemcpyAsync(b_stage + r0 * I, b_host + r0 * I, sizeof(float) * (size_t)((r1 - r0) * I),
+    TCA_CUDA_TRY(cudaMemcpyAsync(b_stage + r0 * I0, b_host + r0 * I0, sizeof(float) * (size_t)((r1 - r0) * I0),
                                  cudaMemcpyHostToDevice, cs));
     TCA_CUDA_TRY(cudaEventRecord(ev[c], cs));
     TCA_CUDA_TRY(cudaStreamWaitEvent(s, ev[c], 0));
@@ -640,33 +655,28 @@ tca_status chain_ff_rhs_from_host(tca_plan_s* p, const float* b_host, float* b_s
     } else {
       while (j_hi < n_out0 && std::min<int64_t>((int64_t)st0[j_hi] + W0, n_in0) <= r1) ++j_hi;
     }
-    if (j_hi > j_done) {
-      const int jch = (j_hi - j_done + 15) / 16;
-      band_ff_inner4_kernel<float><<<(unsigned)(ich * jch), dim3(64, 4), 0, s>>>(
-          b_stage, dst0, nullptr, n_in0, n_out0, I, op0.band.start, op0.band.wff, W0, ich, jch, j_done, j_hi);
-      TCA_LAUNCH_CHECK();
-      j_done = j_hi;
+    if (j_hi <= j_done) continue;
+    const int jch = (j_hi - j_done + 15) / 16;
+    band_ff_inner4_kernel<float><<<(unsigned)(ich * jch), dim3(64, 4), 0, s>>>(
+        b_stage, ws[0], nullptr, n_in0, n_out0, I0, op0.band.start, op0.band.wff, W0, ich, jch, j_done, j_hi);
+    TCA_LAUNCH_CHECK();
+    // The slabs j_done .. j_hi - 1 of the outermost index through the other modes.
+    const int64_t nj = j_hi - j_done;
+    const float2* src = ws[0];
+    for (int st = 1; st < d; ++st) {
+      const int k = p->order_bwd[st];
+      const bool last = st == d - 1;
+      float2* dst = last ? y : ws[st % 2];
+      const int64_t in_slab = Pk[st] * nin[st] * Ik[st], out_slab = Pk[st] * nout[st] * Ik[st];
+      const int32_t* start;
+      const float2* w;
+      int W;
+      op_band_ff(p->mode[k].bwd, &start, &w, &W);
+      TCA_TRY(launch_ff<float2>(start, w, W, nin[st], nout[st], src + j_done * in_slab, dst + j_done * out_slab,
+                                last ? y32 + j_done * out_slab : nullptr, nj * Pk[st], Ik[st], s));
+      src = dst;
     }
-  }
-  cur[k0] = n_out0;
-  const void* src = dst0;
-  const int32_t* start;
-  const float2* w;
-  int W;
-  for (int st = 1; st < d; ++st) {
-    const int k = p->order_bwd[st];
-    const ModeOp& op = p->mode[k].bwd;
-    int64_t Ok = 1, Ik = 1;
-    for (int a = 0; a < k; ++a) Ok *= cur[a];
-    for (int a = k + 1; a < d; ++a) Ik *= cur[a];
-    const int n_in = (int)op.n_in(), n_out = (int)op.n_out();
-    cur[k] = n_out;
-    const bool last = st == d - 1;
-    if (!last && Ok * Ik * n_out > ws_elems) return TCA_ERR_SHAPE;
-    float2* dst = last ? y : ws[st % 2];
-    op_band_ff(op, &start, &w, &W);
-    TCA_TRY(launch_ff<float2>(start, w, W, n_in, n_out, (const float2*)src, dst, last ? y32 : nullptr, Ok, Ik, s));
-    src = dst;
+    j_done = j_hi;
   }
   return TCA_OK;
 }
