@@ -82,6 +82,29 @@ def test_normal_operator(kind, shape, prec):
     assert rel_l2(got, ref) < tol
 
 
+@pytest.mark.parametrize("shape", [(1, 30, 25, 8), (7, 22, 22, 8), (300, 22, 23, 8), (9, 21, 40, 8)])
+def test_fused_sweep_edge_shapes(shape):
+    """The warp-specialised sweep at its edges: one plane along mode 1, n2 = n3 = 22 (the
+    smallest extent copied by TMA boxes), a long mode 1 (many chunks), and n2 = 21 (the
+    cp.async halo path); plain operator and, through 5 CG iterations, the CG-mode sweep."""
+    tca = lib()
+    inst = synth.instance_bspline(shape, seed=680, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    plan = tca.plan_from_instance(inst, precision="f32")
+    rng = np.random.default_rng(681)
+    x = rng.standard_normal(inst.shape).astype(np.float32)
+    kx = empty_dev(inst.shape, np.float32)
+    plan.apply_normal(to_dev(x, np.float32), kx)
+    ref = O.normal_apply(x.astype(np.float64), mats, inst.lam)
+    assert rel_l2(kx.cpu().numpy(), ref) < TOL_F32
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    xs = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), xs, rtol=1e-14, max_iter=5, raise_on_error=False)
+    assert info["iters"] == 5
+    ref5 = O.solve(b.astype(np.float64), mats, inst.lam, rtol=0.0, max_iter=5).x
+    assert rel_l2(xs.cpu().numpy(), ref5) < 1e-4
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("op", [0, 1, 2])
 def test_single_mode_products(mode, op):
