@@ -158,7 +158,7 @@ typedef struct {
   int32_t x0_given;     /* 1: x holds the initial guess; 0: start from x = 0 */
   double inner_rtol;    /* _IR plans: relative tolerance of each inner solve (0: default 1e-3) */
   int32_t max_refine;   /* _IR plans: cap on refinement steps (0: default 30) */
-  int32_t check_every;  /* iterations between host convergence reads (0: default 16; rounded up to a multiple of 4) */
+  int32_t check_every;  /* CG iterations per pass of the device loop; the stop flags are tested between passes (0: default 8, 16 for tca_solve_batched; rounded up to a multiple of 4) */
   int32_t profile;      /* 1: time every normal-operator sweep with CUDA events (info->sweep_*) */
 } tca_solve_opts;
 
@@ -180,8 +180,9 @@ typedef struct {
  * residual is then recomputed and, if it is still above rtol, CG restarts
  * from the current x.  b: m-shaped data, x: n-shaped solution (in: initial
  * guess when opts->x0_given).  Scalars alpha, beta and all inner products are
- * kept in FP64 on the device; the host reads the convergence flag every
- * check_every iterations.  The update C += alpha P is applied once per four
+ * kept in FP64 on the device; one graph launch runs passes of check_every
+ * iterations until the device's stop flags are set (no host round trip in
+ * between; iterations of the last pass after the stop return at entry).  The update C += alpha P is applied once per four
  * iterations from the four directions kept meanwhile (the same terms in the
  * same order and rounding as one update per iteration; a group cut short by
  * the stop test is completed before the true residual is formed), so x is

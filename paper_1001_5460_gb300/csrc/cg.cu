@@ -555,7 +555,7 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
   const double inner = (o && o->inner_rtol > 0.0) ? o->inner_rtol : 1e-3;
   const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
   const int max_refine = (o && o->max_refine > 0) ? o->max_refine : 30;
-  int every = (o && o->check_every > 0) ? o->check_every : 16;
+  int every = (o && o->check_every > 0) ? o->check_every : 8;
   every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
   const bool profile = o && o->profile;
   if (profile) every = std::min(every, kMaxProfiledIters);
@@ -635,7 +635,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   const double rtol = o ? o->rtol : 1e-6;
   const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
   const bool x0 = o && o->x0_given;
-  int every = (o && o->check_every > 0) ? o->check_every : 16;
+  int every = (o && o->check_every > 0) ? o->check_every : 8;
   every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
   const bool profile = o && o->profile;
   if (profile) every = std::min(every, kMaxProfiledIters);

@@ -281,7 +281,7 @@ class Plan:
         return y
 
     def solve(self, b, x, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
-              check_every: int = 16, inner_rtol: float = 0.0, max_refine: int = 0, stream=None,
+              check_every: int = 0, inner_rtol: float = 0.0, max_refine: int = 0, stream=None,
               raise_on_error: bool = True, profile: bool = False):
         """Solve (A^T A + lambda R) x = A^T b; returns (status, info dict)."""
         opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, float(inner_rtol),
@@ -399,7 +399,7 @@ class Net:
              stream=None):
         _check(_lib.tca_net_adam(self._h, lr, beta1, beta2, eps, grad_scale, _stream(stream)), "tca_net_adam")
 
-    def solve(self, plan: "Plan", b, x, rtol: float = 1e-6, max_iter: int = 10000, check_every: int = 16,
+    def solve(self, plan: "Plan", b, x, rtol: float = 1e-6, max_iter: int = 10000, check_every: int = 0,
               inner_rtol: float = 0.0, max_refine: int = 0, net_every: int = 0, stream=None,
               raise_on_error: bool = True, profile: bool = False):
         """tca_solve from x0 = s Net(A^T b / s), plus a network step every net_every iterations (0: none)."""
