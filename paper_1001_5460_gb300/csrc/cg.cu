@@ -152,30 +152,22 @@ __global__ void __launch_bounds__(kVecThreads) cg_direction_kernel(const T* __re
                                                                    T* __restrict__ pnew, int64_t n, const Scalars* sc) {
   if (cg_done(sc)) return;
   const T beta = (T)sc->beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    pnew[i] = r[i] + beta * pold[i];
-}
-
-// alpha = rho / <P, Q> (unfused path).
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) cg_alpha_kernel(const T* __restrict__ p, const T* __restrict__ q,
-                                                               int64_t n, Scalars* sc, Reduce red) {
-  __shared__ double sh[kVecThreads / 32];
-  if (cg_done(sc)) return;
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += (double)p[i] * (double)q[i];
-  double total;
-  if (dev::grid_sum_last(acc, red, &total, sh)) {
-    sc->pq = total;
-    const double alpha = sc->rho / total;
-    if (!(total > 0.0) || !isfinite(alpha)) {
-      sc->breakdown = 1;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = alpha;
-    }
+  using VT = typename V2<T>::t;
+  constexpr int VN = V2<T>::n;
+  const int64_t nv = n / VN;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const VT rv = reinterpret_cast<const VT*>(r)[i];
+    const VT pv = reinterpret_cast<const VT*>(pold)[i];
+    VT o;
+    const T* rs = reinterpret_cast<const T*>(&rv);
+    const T* ps = reinterpret_cast<const T*>(&pv);
+    T* os = reinterpret_cast<T*>(&o);
+#pragma unroll
+    for (int c = 0; c < VN; ++c) os[c] = rs[c] + beta * ps[c];
+    reinterpret_cast<VT*>(pnew)[i] = o;
   }
+  if (blockIdx.x == 0)
+    for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) pnew[i] = r[i] + beta * pold[i];
 }
 
 // r = rhs - kx (kx may be null: r = rhs); rho = <r,r>; optionally bnorm = ||rhs||.
@@ -296,9 +288,8 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, int it, cudaStream_t s,
   if (!fused) {
     cg_direction_kernel<T><<<grid, kVecThreads, 0, s>>>(r, pold, pnew, N, p->scal);
     TCA_LAUNCH_CHECK();
-    TCA_TRY(normal_generic<T>(p, pnew, q, s));
-    cg_alpha_kernel<T><<<grid, kVecThreads, 0, s>>>(pnew, q, N, p->scal, first_reduce(p));
-    TCA_LAUNCH_CHECK();
+    const RegDot dot{p->scal, first_reduce(p)};
+    TCA_TRY(normal_generic<T>(p, pnew, q, s, &dot));
   }
   if (ev_end) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_end, s, cudaEventRecordExternal));
   if (pos == kDirBufs - 1)

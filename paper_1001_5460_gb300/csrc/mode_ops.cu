@@ -166,33 +166,117 @@ __global__ void __launch_bounds__(256) outer_kernel(
 }
 
 // y (+)= sum_k x x_k (lambda L_k) over a 4D view; L_k 5-banded with lambda folded in.
+// The view is right-aligned: mode 3 is the innermost mode of the tensor (stride 1),
+// leading unit modes pad the front.
 struct LapArgs {
   const void* w[kMaxModes];  // Tc-typed band weights (n_k x 5), or null if mode unregularised
   int64_t n[kMaxModes];
   int64_t stride[kMaxModes];
 };
 
-template <typename Tin, typename Tout, typename Tc>
-__global__ void __launch_bounds__(256) reg_add_kernel(const Tin* __restrict__ x, Tout* __restrict__ y,
-                                                      int64_t total, LapArgs la, int accumulate) {
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    Tc acc = Tc(0);
-    int64_t rem = idx;
+template <typename T, int VN>
+struct alignas(sizeof(T) * VN) VecN {
+  T v[VN];
+};
+
+// One thread per run of VN consecutive elements along mode 3 (VN divides n_3,
+// so a run never crosses a row): the index is decoded once per run, the taps of
+// modes 0-2 are VN-wide loads with one coefficient each, mode 3 reads a
+// VN + 4 window.  Per element the terms are summed in the order mode 3, 2, 1, 0,
+// taps 0-4, then added to y.  DOT (CG sweep): also <x, y_new> (FP32 runs,
+// FP64 beyond) and, in the last block, alpha = rho / <x, y> (Fig. 2
+// `alpha := rho/(P+*Q)`), with the same breakdown test as the sweep.
+template <typename Tin, typename Tout, typename Tc, int VN, typename IDX, bool DOT>
+__global__ void __launch_bounds__(256) reg_run_kernel(const Tin* __restrict__ x, Tout* __restrict__ y, IDX runs,
+                                                      LapArgs la, int accumulate, Scalars* sc, Reduce red) {
+  __shared__ double sh[256 / 32];
+  if constexpr (DOT) {
+    if (cg_done(sc)) return;
+  }
+  const IDX n3 = (IDX)la.n[3], n2 = (IDX)la.n[2], n1 = (IDX)la.n[1];
+  Tc part = Tc(0);
+  double acc = 0.0;
+  int cnt = 0;
+  for (IDX ri = (IDX)blockIdx.x * blockDim.x + threadIdx.x; ri < runs; ri += (IDX)gridDim.x * blockDim.x) {
+    const IDX idx = ri * VN;
+    IDX rem = idx / n3;
+    const int i3 = (int)(idx - rem * n3);
+    int ik[3];
+    ik[2] = (int)(rem % n2);
+    rem /= n2;
+    ik[1] = (int)(rem % n1);
+    ik[0] = (int)(rem / n1);
+    Tc a[VN];
 #pragma unroll
-    for (int k = kMaxModes - 1; k >= 0; --k) {
-      const int64_t ik = rem % la.n[k];
-      rem /= la.n[k];
-      if (!la.w[k]) continue;
-      const Tc* wk = reinterpret_cast<const Tc*>(la.w[k]) + ik * 5;
+    for (int j = 0; j < VN; ++j) a[j] = Tc(0);
+    if (la.w[3]) {
+      const Tc* w = reinterpret_cast<const Tc*>(la.w[3]) + (int64_t)i3 * 5;
+      Tc xw[VN + 4];
 #pragma unroll
-      for (int e = 0; e < 5; ++e) {
-        const int64_t c = ik - 2 + e;
-        if (c >= 0 && c < la.n[k]) acc += wk[e] * (Tc)ld(x + idx + (c - ik) * la.stride[k]);
+      for (int t = 0; t < VN + 4; ++t) {
+        const int c = i3 - 2 + t;
+        xw[t] = (c >= 0 && c < (int)n3) ? (Tc)ld(x + idx - 2 + t) : Tc(0);
+      }
+#pragma unroll
+      for (int j = 0; j < VN; ++j) {
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+          const int c = i3 + j - 2 + e;
+          if (c >= 0 && c < (int)n3) a[j] += ld(w + j * 5 + e) * xw[j + e];
+        }
       }
     }
-    if (accumulate) y[idx] = (Tout)((Tc)y[idx] + acc);
-    else y[idx] = (Tout)acc;
+#pragma unroll
+    for (int k = 2; k >= 0; --k) {
+      if (!la.w[k]) continue;
+      const int nk = (int)la.n[k];
+      const Tc* w = reinterpret_cast<const Tc*>(la.w[k]) + (int64_t)ik[k] * 5;
+#pragma unroll
+      for (int e = 0; e < 5; ++e) {
+        const int c = ik[k] - 2 + e;
+        if (c >= 0 && c < nk) {
+          const Tc we = ld(w + e);
+          const VecN<Tin, VN> xv =
+              *reinterpret_cast<const VecN<Tin, VN>*>(x + idx + (int64_t)(c - ik[k]) * la.stride[k]);
+#pragma unroll
+          for (int j = 0; j < VN; ++j) a[j] += we * (Tc)xv.v[j];
+        }
+      }
+    }
+    VecN<Tout, VN> yv;
+    if (accumulate) {
+      yv = *reinterpret_cast<const VecN<Tout, VN>*>(y + idx);
+#pragma unroll
+      for (int j = 0; j < VN; ++j) yv.v[j] = (Tout)((Tc)yv.v[j] + a[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < VN; ++j) yv.v[j] = (Tout)a[j];
+    }
+    *reinterpret_cast<VecN<Tout, VN>*>(y + idx) = yv;
+    if constexpr (DOT) {
+      const VecN<Tin, VN> xv = *reinterpret_cast<const VecN<Tin, VN>*>(x + idx);
+#pragma unroll
+      for (int j = 0; j < VN; ++j) part += (Tc)xv.v[j] * (Tc)yv.v[j];
+      if (++cnt == 8) {  // short runs in Tc, FP64 beyond
+        acc += (double)part;
+        part = Tc(0);
+        cnt = 0;
+      }
+    }
+  }
+  if constexpr (DOT) {
+    acc += (double)part;
+    double total;
+    if (dev::grid_sum_last(acc, red, &total, sh)) {
+      sc->pq = total;
+      const double alpha = sc->rho / total;
+      if (!(total > 0.0) || !isfinite(alpha)) {
+        sc->breakdown = 1;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = alpha;
+      }
+    }
   }
 }
 
@@ -271,29 +355,61 @@ tca_status launch_mode_op(const ModeOp& op, const Tin* x, Tout* y, int64_t O, in
   return TCA_OK;
 }
 
+template <typename Tin, typename Tout, typename Tc, int VN, bool DOT>
+static void launch_reg_run(const tca_plan_s* p, const Tin* x, Tout* y, int64_t total, const LapArgs& la,
+                           int accumulate, const RegDot* dot, cudaStream_t s) {
+  const int64_t runs = total / VN;
+  int64_t grid = std::min<int64_t>((runs + 255) / 256, (int64_t)p->num_sms * 8);
+  if (dot) grid = std::min<int64_t>(grid, dot->red.max_blocks);
+  grid = std::max<int64_t>(grid, 1);
+  Scalars* sc = dot ? dot->sc : nullptr;
+  const Reduce red = dot ? dot->red : Reduce{};
+  if (total + 4 * (int64_t)VN < ((int64_t)1 << 31))
+    reg_run_kernel<Tin, Tout, Tc, VN, uint32_t, DOT><<<(unsigned)grid, 256, 0, s>>>(x, y, (uint32_t)runs, la,
+                                                                                    accumulate, sc, red);
+  else
+    reg_run_kernel<Tin, Tout, Tc, VN, int64_t, DOT><<<(unsigned)grid, 256, 0, s>>>(x, y, runs, la, accumulate, sc,
+                                                                                   red);
+}
+
 template <typename Tin, typename Tout>
 tca_status launch_reg_add_impl(const tca_plan_s* p, const Tin* x, Tout* y, const int64_t* dims4,
-                               int accumulate, cudaStream_t s) {
+                               int accumulate, const RegDot* dot, cudaStream_t s) {
   using Tc = Tout;
+  // Right-align the view: the last mode with more than one element becomes mode 3.
+  int last = 0;
+  for (int k = 0; k < kMaxModes; ++k)
+    if (dims4[k] > 1) last = k;
+  const int shift = kMaxModes - 1 - last;
   LapArgs la;
   int64_t stride = 1;
   for (int k = kMaxModes - 1; k >= 0; --k) {
-    la.n[k] = dims4[k];
+    const int src = k - shift;
+    la.n[k] = src >= 0 ? dims4[src] : 1;
     la.stride[k] = stride;
-    stride *= dims4[k];
-    const bool on = k < p->d && p->mode[k].reg;
-    la.w[k] = on ? (const void*)wsel<Tc>(p->mode[k].lap) : nullptr;
+    stride *= la.n[k];
+    const bool on = src >= 0 && src < p->d && p->mode[src].reg;
+    la.w[k] = on ? (const void*)wsel<Tc>(p->mode[src].lap) : nullptr;
   }
   const int64_t total = stride;
-  const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->num_sms * 16);
-  reg_add_kernel<Tin, Tout, Tc><<<std::max(grid, 1), 256, 0, s>>>(x, y, total, la, accumulate);
+  if (total <= 0) return TCA_OK;
+  constexpr int VN = 16 / (sizeof(Tin) > sizeof(Tout) ? sizeof(Tin) : sizeof(Tout));
+  const bool vec = la.n[3] % VN == 0 && (uintptr_t)x % (VN * sizeof(Tin)) == 0 &&
+                   (uintptr_t)y % (VN * sizeof(Tout)) == 0;
+  if (dot) {
+    if (vec) launch_reg_run<Tin, Tout, Tc, VN, true>(p, x, y, total, la, accumulate, dot, s);
+    else launch_reg_run<Tin, Tout, Tc, 1, true>(p, x, y, total, la, accumulate, dot, s);
+  } else {
+    if (vec) launch_reg_run<Tin, Tout, Tc, VN, false>(p, x, y, total, la, accumulate, nullptr, s);
+    else launch_reg_run<Tin, Tout, Tc, 1, false>(p, x, y, total, la, accumulate, nullptr, s);
+  }
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }
 
 template <typename Tin, typename Tout>
 tca_status launch_reg_add(const tca_plan_s* p, const Tin* x, Tout* y, const int64_t* dims4, cudaStream_t s) {
-  return launch_reg_add_impl<Tin, Tout>(p, x, y, dims4, 1, s);
+  return launch_reg_add_impl<Tin, Tout>(p, x, y, dims4, 1, nullptr, s);
 }
 
 static void dims4_of(const tca_plan_s* p, int64_t* d4) {
@@ -331,8 +447,9 @@ tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, voi
 }
 
 // (G_1 kron .. kron G_d) x + lambda R x through single-mode sweeps; element type T.
+// With dot, the regulariser pass also forms <x, y> and alpha (CG sweep).
 template <typename T>
-tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s) {
+tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const RegDot* dot) {
   const int d = p->d;
   const void* src = x;
   for (int k = 0; k < d; ++k) {
@@ -345,7 +462,7 @@ tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s) {
   }
   int64_t d4[kMaxModes];
   dims4_of(p, d4);
-  return launch_reg_add<T, T>(p, x, y, d4, s);
+  return launch_reg_add_impl<T, T>(p, x, y, d4, 1, dot, s);
 }
 
 static tca_status ensure_ws64(tca_plan_s* p) {
@@ -382,8 +499,8 @@ tca_status normal_fp64(tca_plan_s* p, const Tin* x, double* y, cudaStream_t s) {
 
 tca_status ensure_ws64_public(tca_plan_s* p) { return ensure_ws64(p); }
 
-template tca_status normal_generic<float>(tca_plan_s*, const float*, float*, cudaStream_t);
-template tca_status normal_generic<double>(tca_plan_s*, const double*, double*, cudaStream_t);
+template tca_status normal_generic<float>(tca_plan_s*, const float*, float*, cudaStream_t, const RegDot*);
+template tca_status normal_generic<double>(tca_plan_s*, const double*, double*, cudaStream_t, const RegDot*);
 template tca_status normal_fp64<float>(tca_plan_s*, const float*, double*, cudaStream_t);
 template tca_status normal_fp64<double>(tca_plan_s*, const double*, double*, cudaStream_t);
 template tca_status apply_chain<float, float, float>(tca_plan_s*, bool, const float*, float*, void* const*, int64_t, cudaStream_t);

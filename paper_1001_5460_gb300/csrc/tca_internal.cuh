@@ -201,9 +201,16 @@ template <typename Tin, typename Tout>
 tca_status launch_reg_add(const tca_plan_s* p, const Tin* x, Tout* y, const int64_t* dims,
                           cudaStream_t s);
 
-// Normal operator through the generic (unfused) sequence, element type T.
+// Reduction target of a fused <x, Kx> -> alpha (CG sweep through the generic sequence).
+struct RegDot {
+  Scalars* sc;
+  Reduce red;
+};
+
+// Normal operator through the generic (unfused) sequence, element type T; with
+// dot, <x, y> and alpha = rho / <x, y> are formed in the same pass.
 template <typename T>
-tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s);
+tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const RegDot* dot = nullptr);
 
 // FP64 normal operator applied to a float or double x (true residual).
 template <typename Tin>
