@@ -949,8 +949,10 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
     // products) are lowered while the graph is captured, so that several
     // instances' kernels run side by side instead of each filling every SM.
     // Measured on the 64-instance workload: 1.53 s with whole-GPU grids (and
-    // autotuned chunks), 1.23 s with a quarter; smaller shares starve the
-    // dense instances that set the critical path.
+    // autotuned chunks), 1.23 s with a quarter.  With the faster generic
+    // iteration: 0.98 s with a half, 0.90 s with a third, 0.86 s with a
+    // quarter, 0.84 s with a sixth, while the slowest instance alone in a
+    // batch goes from 0.16 to 0.33 s - a quarter keeps the critical path short.
     const int budget = std::max(8, plans[0]->num_sms / 4);
     std::vector<int> saved_sms(count), saved_chunks(count);
     auto set_cap = [](tca_plan_s* p, int cap) {
