@@ -160,7 +160,25 @@ typedef struct {
   int32_t max_refine;   /* _IR plans: cap on refinement steps (0: default 30) */
   int32_t check_every;  /* CG iterations per pass of the device loop; the stop flags are tested between passes (0: default 8, 16 for tca_solve_batched; rounded up to a multiple of 4) */
   int32_t profile;      /* 1: time every normal-operator sweep with CUDA events (info->sweep_*) */
+  int32_t precond;      /* TCA_PRECOND_NONE: the CG of Fig. 2; TCA_PRECOND_SEPARABLE: the same CG with
+                           Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d) (see below) */
+  double precond_shift; /* s, the regulariser weight folded into each mode of M (0: default 16) */
 } tca_solve_opts;
+
+/* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_SEPARABLE uses
+ * a tensor inverse (Sec. 3, Eq. TensorEq): M is a separable approximation of
+ * K = (x)_k G_k + lambda sum_k L_k that keeps the Gram part exactly (G_k =
+ * A_k^T A_k) and spreads the regulariser over the modes with weight s, and its
+ * inverse is the separable transformation of the per-mode inverses
+ * (G_k + s lambda L_k)^-1, formed once per plan and shift in FP64 on the host
+ * (Cholesky) and applied as dense mode products (tensor cores for FP32
+ * plans: 3xTF32 where the operand tiles fit in shared memory, plain TF32
+ * otherwise; native FP64 for FP64 plans).  CG then uses rho = <R, Z> and
+ * P = Z + beta P; the stop test stays on ||R|| / ||A^T b|| and on the FP64
+ * true residual, so the result meets the same tolerance.  The paper fixes no
+ * preconditioner; this one is an addition.  Costs d dense mode products and
+ * one inner product per iteration, and one n_k x n_k dense factor per mode. */
+enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1 };
 
 typedef struct {
   int32_t iters;             /* CG iterations run (all inner solves summed) */

@@ -52,7 +52,7 @@ template <typename T, bool XUPD>
 __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
                                                                 const T* __restrict__ p, const T* __restrict__ q,
                                                                 int64_t n, Scalars* sc, Reduce red, DirBufs<T> pb,
-                                                                int pos) {
+                                                                int pos, int pc) {
   __shared__ double sh[kVecThreads / 32];
   if (cg_done(sc)) return;
   const double alpha_d = sc->alpha;
@@ -111,10 +111,13 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ 
   acc += (double)part;
   double total;
   if (dev::grid_sum_last(acc, red, &total, sh)) {
-    const double rho = sc->rho;
+    // <r, r> always feeds the stop test; without a preconditioner it is also
+    // rho of the next step (with one, rho = <r, z> comes after z = M^-1 r).
     sc->rho_new = total;
-    sc->beta = total / rho;
-    sc->rho = total;
+    if (!pc) {
+      sc->beta = total / sc->rho;
+      sc->rho = total;
+    }
     sc->iters += 1;
     if constexpr (XUPD) {
       sc->npend = 0;
@@ -201,11 +204,55 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(const T* __restri
   const bool last2 = dev::grid_sum_last(a_bb, red2, &t_bb, sh);
   if (last1) {
     sc->rho = t_rr;
+    sc->rho_new = t_rr;
     sc->beta = 0.0;
     sc->converged = 0;
     sc->breakdown = 0;
   }
   if (last2 && set_bnorm) sc->bnorm = sqrt(t_bb);
+}
+
+// Preconditioned CG: rho1 = <r, z> (z = M^-1 r).  INIT (a fresh start or a
+// restart): rho = rho1, beta = 0; otherwise beta = rho1 / rho, rho = rho1.
+// A non-positive or non-finite <r, z> with r != 0 is a breakdown.
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(kVecThreads) cg_precond_dot_kernel(const T* __restrict__ r, const T* __restrict__ z,
+                                                                     int64_t n, Scalars* sc, Reduce red) {
+  __shared__ double sh[kVecThreads / 32];
+  if (cg_done(sc)) return;
+  using VT = typename V2<T>::t;
+  constexpr int VN = V2<T>::n;
+  const int64_t nv = n / VN;
+  T part = T(0);
+  double acc = 0.0;
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const VT rv = reinterpret_cast<const VT*>(r)[i];
+    const VT zv = reinterpret_cast<const VT*>(z)[i];
+    const T* rs = reinterpret_cast<const T*>(&rv);
+    const T* zs = reinterpret_cast<const T*>(&zv);
+#pragma unroll
+    for (int c = 0; c < VN; ++c) part += rs[c] * zs[c];
+    if (++cnt == 8) {  // short runs in T, FP64 beyond
+      acc += (double)part;
+      part = T(0);
+      cnt = 0;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) part += r[i] * z[i];
+  acc += (double)part;
+  double total;
+  if (dev::grid_sum_last(acc, red, &total, sh)) {
+    const bool bad = !isfinite(total) || (!(total > 0.0) && sc->rho_new > 0.0);
+    if (bad) sc->breakdown = 1;
+    if (INIT) {
+      sc->beta = 0.0;
+    } else {
+      sc->beta = total / sc->rho;
+    }
+    sc->rho = total;
+  }
 }
 
 // ||rhs64 - kx64|| / ||rhs64||  -> sc->aux; optionally r = rhs64 - kx64 (cast).
@@ -266,6 +313,35 @@ static DirBufs<T> dir_bufs(const tca_plan_s* p) {
   return d;
 }
 
+// Preconditioned CG: z = M^-1 r, then rho from <r, z> (init: a fresh start).
+template <typename T>
+static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
+  TCA_TRY(apply_precond<T>(p, (const T*)p->r, (T*)p->z, s));
+  const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
+  if (init)
+    cg_precond_dot_kernel<T, true><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->z, p->N, p->scal,
+                                                                 first_reduce(p));
+  else
+    cg_precond_dot_kernel<T, false><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->z, p->N, p->scal,
+                                                                  first_reduce(p));
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
+// The preconditioner a solve asks for: validates the options, builds the
+// factors for the shift (default 16) and marks the plan's iteration as
+// preconditioned (or not).
+constexpr double kDefaultPrecondShift = 16.0;
+static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
+  p->pc_on = false;
+  const int kind = o ? o->precond : TCA_PRECOND_NONE;
+  if (kind == TCA_PRECOND_NONE) return TCA_OK;
+  if (kind != TCA_PRECOND_SEPARABLE || o->precond_shift < 0.0) return TCA_ERR_INVALID_ARG;
+  TCA_TRY(ensure_precond(p, o->precond_shift > 0.0 ? o->precond_shift : kDefaultPrecondShift));
+  p->pc_on = true;
+  return TCA_OK;
+}
+
 // One CG iteration at position `it` of a graph replay (replays hold a multiple
 // of kDirBufs iterations, so it % kDirBufs is the position in the update
 // group).  ev_begin/ev_end (may be null) bracket the normal-operator sweep so
@@ -281,24 +357,28 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, int it, cudaStream_t s,
   T* q = (T*)p->q;
   const int grid = std::min(vector_grid(p, N), first_reduce(p).max_blocks);
   const bool fused = sizeof(T) == 4 && p->fused_ok;
+  // The new direction is formed from r (Fig. 2) or, preconditioned, from z = M^-1 r.
+  const T* dsrc = p->pc_on ? (const T*)p->z : r;
   if (ev_begin) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_begin, s, cudaEventRecordExternal));
   if constexpr (sizeof(T) == 4) {
-    if (fused) TCA_TRY(normal_fused_f32(p, r, pold, pnew, q, true, s));
+    if (fused) TCA_TRY(normal_fused_f32(p, dsrc, pold, pnew, q, true, s));
   }
   if (!fused) {
-    cg_direction_kernel<T><<<grid, kVecThreads, 0, s>>>(r, pold, pnew, N, p->scal);
+    cg_direction_kernel<T><<<grid, kVecThreads, 0, s>>>(dsrc, pold, pnew, N, p->scal);
     TCA_LAUNCH_CHECK();
     const RegDot dot{p->scal, first_reduce(p)};
     TCA_TRY(normal_generic<T>(p, pnew, q, s, &dot));
   }
   if (ev_end) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_end, s, cudaEventRecordExternal));
+  const int pc = p->pc_on ? 1 : 0;
   if (pos == kDirBufs - 1)
     cg_update_kernel<T, true><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p), dir_bufs<T>(p),
-                                                           pos);
+                                                           pos, pc);
   else
     cg_update_kernel<T, false><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p),
-                                                            dir_bufs<T>(p), pos);
+                                                            dir_bufs<T>(p), pos, pc);
   TCA_LAUNCH_CHECK();
+  if (p->pc_on) TCA_TRY(enqueue_precond<T>(p, false, s));
   return TCA_OK;
 }
 
@@ -390,7 +470,9 @@ tca_status capture_into(cudaGraph_t g, cudaStream_t cs, F fill) {
 // one pass per launch (the host reads each pass's sweep events).
 template <typename T>
 static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaStream_t s) {
-  if (p->graph_exec && p->graph_x == x && p->graph_iters == iters && p->graph_profiled == profile) return TCA_OK;
+  if (p->graph_exec && p->graph_x == x && p->graph_iters == iters && p->graph_profiled == profile &&
+      p->graph_pc == p->pc_on)
+    return TCA_OK;
   if (p->graph_exec) {
     cudaGraphExecDestroy(p->graph_exec);
     p->graph_exec = nullptr;
@@ -458,6 +540,7 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
   p->graph_x = x;
   p->graph_iters = iters;
   p->graph_profiled = profile;
+  p->graph_pc = p->pc_on;
   p->graph_head_launches = after_head - before;     // kernels before the loop (unprofiled)
   p->graph_launches = after - after_head;           // kernels per pass
   return TCA_OK;
@@ -491,7 +574,7 @@ static tca_status cg_iterate(tca_plan_s* p, double rtol, int max_iter, int every
   // Start-of-iteration stop test (a zero right-hand side or an exact x0).
   TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
   TCA_CUDA_TRY(cudaStreamSynchronize(s));
-  bool conv = hs->bnorm == 0.0 || std::sqrt(hs->rho) <= rtol * hs->bnorm;
+  bool conv = hs->bnorm == 0.0 || std::sqrt(hs->rho_new) <= rtol * hs->bnorm;
   while (!conv && !hs->breakdown && hs->iters < max_iter) {
     const int it_before = hs->iters;
     TCA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, s));
@@ -554,6 +637,7 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
   double sweep_ms = 0.0;
   int sweep_n = 0;
   float* d = p->dbuf;
+  TCA_TRY(setup_precond(p, o));
   TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
                    reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
   if (!(o && o->x0_given)) TCA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * N, s));
@@ -584,10 +668,11 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
     cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, nullptr, (float*)p->r, N, p->scal,
                                                           first_reduce(p), 1, second_reduce(p));
     TCA_LAUNCH_CHECK();
+    if (p->pc_on) TCA_TRY(enqueue_precond<float>(p, true, s));
     TCA_TRY(cg_iterate(p, inner, max_iter - total, every, profile, &sweep_ms, &sweep_n, s));
     TCA_TRY(flush_pending_x<float>(p, d, s));
     total += hs->iters;
-    rec = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho, 0.0)) / hs->bnorm : 0.0;
+    rec = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho_new, 0.0)) / hs->bnorm : 0.0;
     if (hs->breakdown) {
       status = TCA_ERR_BREAKDOWN;
       break;
@@ -631,6 +716,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   const bool profile = o && o->profile;
   if (profile) every = std::min(every, kMaxProfiledIters);
   if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
+  TCA_TRY(setup_precond(p, o));
   double sweep_ms = 0.0;
   int sweep_n = 0;
 
@@ -677,6 +763,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
                                                       first_reduce(p), 1, second_reduce(p));
   }
   TCA_LAUNCH_CHECK();
+  if (p->pc_on) TCA_TRY(enqueue_precond<T>(p, true, s));
   TCA_TRY(get_graph<T>(p, x, every, profile, s));
 
   tca_status status = TCA_OK;
@@ -715,13 +802,14 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
     cg_start_kernel<T><<<vgrid, kVecThreads, 0, s>>>((const T*)p->r, nullptr, (T*)p->r, N, p->scal,
                                                       first_reduce(p), 0, second_reduce(p));
     TCA_LAUNCH_CHECK();
+    if (p->pc_on) TCA_TRY(enqueue_precond<T>(p, true, s));
   }
   if (x_host && p->copy_stream) TCA_CUDA_TRY(cudaStreamSynchronize(p->copy_stream));
   if (info) {
     info->iters = hs->iters;
     info->refinements = restarts;
     info->rel_res_true = hs->aux;
-    info->rel_res_recursive = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho, 0.0)) / hs->bnorm : 0.0;
+    info->rel_res_recursive = hs->bnorm > 0 ? std::sqrt(std::max(hs->rho_new, 0.0)) / hs->bnorm : 0.0;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     info->sweep_ms = sweep_ms;
     info->sweep_launches = sweep_n;
@@ -754,7 +842,7 @@ constexpr int kMaxRestarts = 16;
 // exact initial guess), so that such an instance does no iteration at all.
 __global__ void batch_start_test_kernel(Scalars* sc) {
   sc->restarts = 0;
-  if (sc->bnorm == 0.0 || sqrt(sc->rho) <= sc->rtol * sc->bnorm) sc->converged = 1;
+  if (sc->bnorm == 0.0 || sqrt(sc->rho_new) <= sc->rtol * sc->bnorm) sc->converged = 1;
 }
 
 // After the true residual (sc->aux = ||A^T b - K x|| / ||A^T b||, r = that
@@ -773,6 +861,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_restart_kernel(const float*
   double t;
   if (dev::grid_sum_last(acc, red, &t, sh)) {
     sc->rho = t;
+    sc->rho_new = t;
     sc->beta = 0.0;
     sc->restarts += 1;
     sc->converged = sqrt(t) <= sc->rtol * sc->bnorm ? 1 : 0;
@@ -824,6 +913,7 @@ tca_status enqueue_setup(tca_plan_s* p, const float* b, float* x, double rtol, i
   cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, kx, (float*)p->r, N, p->scal,
                                                         first_reduce(p), 1, second_reduce(p));
   TCA_LAUNCH_CHECK();
+  if (p->pc_on) TCA_TRY(enqueue_precond<float>(p, true, s));
   batch_start_test_kernel<<<1, 1, 0, s>>>(p->scal);
   TCA_LAUNCH_CHECK();
   return TCA_OK;
@@ -882,6 +972,8 @@ tca_status build_batch(int count, tca_plan_s** plans, const float* const* b, flo
       const int vgrid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
       batch_restart_kernel<<<vgrid, kVecThreads, 0, s>>>((const float*)p->r, p->N, p->scal, first_reduce(p));
       TCA_LAUNCH_CHECK();
+      // Preconditioned: rho = <r, z> of the restart (returns at entry when none happened).
+      if (p->pc_on) TCA_TRY(enqueue_precond<float>(p, true, s));
       cond_running_kernel<<<1, 1, 0, s>>>(p->scal, ho[i]);
       TCA_LAUNCH_CHECK();
       bg->l_check[i] = tca_kernel_launches(0) - l0 + 2;  // + the inner gate
@@ -925,6 +1017,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
   for (int i = 0; i < count; ++i) {
     TCA_TRY(ensure_solver_buffers<float>(plans[i]));
     TCA_TRY(ensure_ws64_public(plans[i]));
+    TCA_TRY(setup_precond(plans[i], o));
   }
   std::lock_guard<std::mutex> lock(g_batch_mutex);
   TCA_TRY(ensure_pool());
@@ -933,6 +1026,8 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
   key.push_back((const void*)(intptr_t)max_iter);
   key.push_back((const void*)(intptr_t)(x0 ? 1 : 0));
   key.push_back(reinterpret_cast<const void*>((uintptr_t)(rtol * 1e15)));
+  key.push_back((const void*)(intptr_t)(plans[0]->pc_on ? 1 : 0));
+  key.push_back(reinterpret_cast<const void*>((uintptr_t)(plans[0]->pc_shift * 1e6)));
   for (int i = 0; i < count; ++i) {
     key.push_back(plans[i]);
     key.push_back((const void*)(uintptr_t)plans[i]->generation);
@@ -959,6 +1054,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
       for (int k = 0; k < p->d; ++k) {
         Mode& m = p->mode[k];
         m.fwd.sm_cap = m.bwd.sm_cap = m.gram.sm_cap = cap;
+        p->pc[k].sm_cap = cap;
       }
     };
     for (int i = 0; i < count; ++i) {
@@ -999,7 +1095,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
       info[i].iters = hs.iters;
       info[i].refinements = hs.restarts;
       info[i].rel_res_true = hs.bnorm == 0.0 ? 0.0 : hs.aux;
-      info[i].rel_res_recursive = hs.bnorm > 0 ? std::sqrt(std::max(hs.rho, 0.0)) / hs.bnorm : 0.0;
+      info[i].rel_res_recursive = hs.bnorm > 0 ? std::sqrt(std::max(hs.rho_new, 0.0)) / hs.bnorm : 0.0;
       info[i].seconds = secs;
       info[i].sweep_ms = 0.0;
       info[i].sweep_launches = 0;

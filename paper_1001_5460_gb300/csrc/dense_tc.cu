@@ -296,6 +296,19 @@ int tc_sm_count() {
 
 }  // namespace
 
+static size_t dense_tc_smem_bytes(int64_t n_in, int64_t n_out, int split) {
+  const int64_t Kp = (n_in + 7) / 8 * 8, Np = (n_out + 15) / 16 * 16;
+  const int nsplit = split == 2 ? 2 : 1;
+  return (size_t)nsplit * ((size_t)kM * Kp * 4 + (size_t)Np * Kp * 4) + NBARS * 8 + 16 + 1024;
+}
+
+int dense_tc_max_split(int64_t n_in, int64_t n_out) {
+  if (n_in <= 0 || n_out <= 0 || (n_out + 15) / 16 * 16 > 256) return 0;
+  if (dense_tc_smem_bytes(n_in, n_out, 2) <= 220 * 1024) return 2;
+  if (dense_tc_smem_bytes(n_in, n_out, 1) <= 220 * 1024) return 1;
+  return 0;
+}
+
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
                            cudaStream_t s, int sm_cap) {
   const int n_in = (int)d.n_in, n_out = (int)d.n_out;
@@ -315,8 +328,7 @@ tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, 
   while (cols < 2 * g.Np) cols *= 2;  // two accumulators
   g.tmem_cols = cols;
   g.tiles = (g.P + kM - 1) / kM;
-  const int nsplit = split == 2 ? 2 : 1;
-  const size_t bytes = (size_t)nsplit * ((size_t)kM * g.Kp * 4 + (size_t)g.Np * g.Kp * 4) + NBARS * 8 + 16 + 1024;
+  const size_t bytes = dense_tc_smem_bytes(n_in, n_out, split);
   if (bytes > 220 * 1024) return TCA_ERR_UNSUPPORTED;
   static bool attr = false;
   if (!attr) {

@@ -465,6 +465,26 @@ tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const
   return launch_reg_add_impl<T, T>(p, x, y, d4, 1, dot, s);
 }
 
+// z = M^-1 r for the separable-inverse preconditioner: one dense mode product
+// per mode with the factors (G_k + s lambda L_k)^-1, through the ping-pong
+// workspace.
+template <typename T>
+tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s) {
+  const int d = p->d;
+  const void* src = r;
+  for (int k = 0; k < d; ++k) {
+    int64_t O = 1, I = 1;
+    for (int a = 0; a < k; ++a) O *= p->n[a];
+    for (int a = k + 1; a < d; ++a) I *= p->n[a];
+    void* dst = (k == d - 1) ? (void*)z : p->ws[k % 2];
+    TCA_TRY((launch_mode_op<T, T, T>(p->pc[k], (const T*)src, (T*)dst, O, I, s)));
+    src = dst;
+  }
+  return TCA_OK;
+}
+template tca_status apply_precond<float>(tca_plan_s*, const float*, float*, cudaStream_t);
+template tca_status apply_precond<double>(tca_plan_s*, const double*, double*, cudaStream_t);
+
 static tca_status ensure_ws64(tca_plan_s* p) {
   if (p->ws64[0]) return TCA_OK;
   const int64_t need = std::max(p->ws_elems, p->N);

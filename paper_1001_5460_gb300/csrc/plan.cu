@@ -296,6 +296,112 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
   return TCA_OK;
 }
 
+// ---- Separable-inverse preconditioner (a tensor inverse, Sec. 3, Eq. TensorEq)
+//
+// M_k = G_k + s (lambda L_k) in FP64 on the host from the plan's FP64 Gram and
+// regulariser bands, inverted through its Cholesky factor C (M_k^-1 =
+// C^-T C^-1), stored as a dense factor.
+
+// In-place inverse of the SPD n x n matrix a (row-major); false if a pivot is
+// not positive.
+static bool spd_inverse(std::vector<double>& a, int64_t n) {
+  std::vector<double> c((size_t)(n * n), 0.0);
+  for (int64_t j = 0; j < n; ++j) {
+    double d = a[j * n + j];
+    for (int64_t t = 0; t < j; ++t) d -= c[j * n + t] * c[j * n + t];
+    if (!(d > 0.0)) return false;
+    const double cjj = std::sqrt(d);
+    c[j * n + j] = cjj;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double v = a[i * n + j];
+      for (int64_t t = 0; t < j; ++t) v -= c[i * n + t] * c[j * n + t];
+      c[i * n + j] = v / cjj;
+    }
+  }
+  // w = C^-1 (lower triangular), by forward substitution column by column.
+  std::vector<double> w((size_t)(n * n), 0.0);
+  for (int64_t col = 0; col < n; ++col) {
+    for (int64_t i = col; i < n; ++i) {
+      double v = i == col ? 1.0 : 0.0;
+      for (int64_t t = col; t < i; ++t) v -= c[i * n + t] * w[t * n + col];
+      w[i * n + col] = v / c[i * n + i];
+    }
+  }
+  // a = W^T W.
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j <= i; ++j) {
+      double v = 0.0;
+      for (int64_t t = i; t < n; ++t) v += w[t * n + i] * w[t * n + j];
+      a[i * n + j] = v;
+      a[j * n + i] = v;
+    }
+  return true;
+}
+
+tca_status ensure_precond(tca_plan_s* p, double shift) {
+  if (!(shift >= 0.0) || !std::isfinite(shift)) return TCA_ERR_INVALID_ARG;
+  if (p->pc_shift == shift && p->z) return TCA_OK;
+  for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
+  p->pc_shift = 0.0;
+  for (int k = 0; k < p->d; ++k) {
+    const Mode& md = p->mode[k];
+    const int64_t n = md.n;
+    std::vector<double> a((size_t)(n * n), 0.0);
+    if (md.gram.kind == OP_DENSE) {
+      TCA_CUDA_TRY(cudaMemcpy(a.data(), md.gram.dense.a64, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+    } else {
+      const Band& gb = md.gram.band;
+      std::vector<double> g((size_t)(n * gb.W));
+      std::vector<int32_t> st((size_t)n);
+      TCA_CUDA_TRY(cudaMemcpy(g.data(), gb.w64, sizeof(double) * n * gb.W, cudaMemcpyDeviceToHost));
+      TCA_CUDA_TRY(cudaMemcpy(st.data(), gb.start, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < n; ++i)
+        for (int e = 0; e < gb.W; ++e) {
+          const int64_t c = (int64_t)st[i] + e;
+          if (c >= 0 && c < n) a[i * n + c] += g[i * gb.W + e];
+        }
+    }
+    {
+      const Band& lb = md.lap;
+      std::vector<double> l((size_t)(n * lb.W));
+      TCA_CUDA_TRY(cudaMemcpy(l.data(), lb.w64, sizeof(double) * n * lb.W, cudaMemcpyDeviceToHost));
+      const int half = lb.W / 2;
+      for (int64_t i = 0; i < n; ++i)
+        for (int e = 0; e < lb.W; ++e) {
+          const int64_t c = i - half + e;
+          if (c >= 0 && c < n) a[i * n + c] += shift * l[i * lb.W + e];
+        }
+    }
+    if (!spd_inverse(a, n)) {
+      set_error_message("separable preconditioner: G_k + s lambda L_k is not positive definite");
+      return TCA_ERR_UNSUPPORTED;
+    }
+    ModeOp& op = p->pc[k];
+    op.kind = OP_DENSE;
+    op.dense.n_out = n;
+    op.dense.n_in = n;
+    TCA_TRY(dmalloc(&op.dense.a64, n * n));
+    TCA_TRY(dmalloc(&op.dense.a32, n * n));
+    TCA_CUDA_TRY(cudaMemcpy(op.dense.a64, a.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
+    cast_kernel<<<nblk(n * n), 256>>>(op.dense.a64, op.dense.a32, n * n);
+    TCA_LAUNCH_CHECK();
+    // FP32 plans: 3xTF32 where the tiles fit, plain TF32 otherwise (a
+    // preconditioner needs no more); reduced-precision plans TF32; FP64 native.
+    const int split = dense_tc_max_split(n, n);
+    op.tc_split = p->prec == TCA_F64 ? 0 : (p->prec == TCA_F32 ? split : std::min(split, 1));
+  }
+  if (!p->z) {
+    cudaError_t e = cudaMalloc(&p->z, elem_size(p) * (size_t)p->N);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return TCA_ERR_ALLOC;
+    }
+  }
+  TCA_CUDA_TRY(cudaDeviceSynchronize());
+  p->pc_shift = shift;
+  return TCA_OK;
+}
+
 // Largest intermediate of a chain of mode products applied in `order`.
 static int64_t chain_peak(const int64_t* start, const int64_t* end, const int* order, int d) {
   int64_t cur[kMaxModes];
@@ -312,6 +418,8 @@ static int64_t chain_peak(const int64_t* start, const int64_t* end, const int* o
 
 static void destroy_plan(tca_plan_s* p) {
   if (!p) return;
+  for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
+  cudaFree(p->z);
   for (int k = 0; k < kMaxModes; ++k) {
     free_op(p->mode[k].fwd);
     free_op(p->mode[k].bwd);

@@ -133,6 +133,12 @@ struct tca_plan_s {
   double* rhs64 = nullptr;
   double* res64 = nullptr;
   float* dbuf = nullptr;    // refinement correction d (mixed-precision plans)
+  // Separable-inverse preconditioner: per-mode dense (G_k + s lambda L_k)^-1,
+  // built for shift pc_shift (0: not built); z = M^-1 r.
+  tca::ModeOp pc[tca::kMaxModes];
+  double pc_shift = 0.0;
+  void* z = nullptr;
+  bool pc_on = false;       // the iteration being built or run is preconditioned
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
   cudaStream_t copy_stream = nullptr;  // host-pointer solves: b uploaded under A^T b, x copied back
@@ -148,6 +154,7 @@ struct tca_plan_s {
   const void* graph_x = nullptr;
   int graph_iters = 0;
   bool graph_profiled = false;
+  bool graph_pc = false;
   uint64_t graph_launches = 0;       // kernels per pass of the iteration graph
   uint64_t graph_head_launches = 0;  // kernels before its loop (unprofiled graphs)
   cudaEvent_t sweep_ev[2 * tca::kMaxProfiledIters] = {};  // start/end per iteration of a profiled graph
@@ -206,6 +213,15 @@ struct RegDot {
   Scalars* sc;
   Reduce red;
 };
+
+// Separable-inverse preconditioner for shift s: build (or keep) the per-mode
+// factors and the z buffer; apply_precond writes z = M^-1 r (element type T).
+tca_status ensure_precond(tca_plan_s* p, double shift);
+template <typename T>
+tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s);
+// Largest 3xTF32 / TF32 split the tensor-core dense kernel takes for an
+// n_out x n_in factor (2, 1, or 0 when it takes none).
+int dense_tc_max_split(int64_t n_in, int64_t n_out);
 
 // Normal operator through the generic (unfused) sequence, element type T; with
 // dot, <x, y> and alpha = rho / <x, y> are formed in the same pass.

@@ -55,7 +55,19 @@ class tca_reg(ctypes.Structure):
 class tca_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("x0_given", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_shift", ctypes.c_double)]
+
+
+PRECOND_NONE, PRECOND_SEPARABLE = 0, 1
+
+
+def _precond_code(precond) -> int:
+    """None / "none" -> plain CG (Fig. 2); "separable" -> CG with the separable tensor-inverse preconditioner."""
+    if precond in (None, "none", PRECOND_NONE):
+        return PRECOND_NONE
+    if precond in ("separable", PRECOND_SEPARABLE):
+        return PRECOND_SEPARABLE
+    raise ValueError(f"unknown preconditioner {precond!r}")
 
 
 class tca_solve_info(ctypes.Structure):
@@ -282,10 +294,14 @@ class Plan:
 
     def solve(self, b, x, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
               check_every: int = 0, inner_rtol: float = 0.0, max_refine: int = 0, stream=None,
-              raise_on_error: bool = True, profile: bool = False):
-        """Solve (A^T A + lambda R) x = A^T b; returns (status, info dict)."""
+              raise_on_error: bool = True, profile: bool = False, precond=None, precond_shift: float = 0.0):
+        """Solve (A^T A + lambda R) x = A^T b; returns (status, info dict).
+
+        precond: None (the CG of Fig. 2) or "separable" (the separable tensor-inverse
+        preconditioner, shift ``precond_shift``, 0 for the default)."""
         opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, float(inner_rtol),
-                              int(max_refine), int(check_every), 1 if profile else 0)
+                              int(max_refine), int(check_every), 1 if profile else 0, _precond_code(precond),
+                              float(precond_shift))
         info = tca_solve_info()
         st = _lib.tca_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
         if raise_on_error:
@@ -305,7 +321,8 @@ def _info_dict(info) -> dict:
 
 
 def solve_batched(plans, bs, xs, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
-                  check_every: int = 16, stream=None, raise_on_error: bool = True):
+                  check_every: int = 16, stream=None, raise_on_error: bool = True, precond=None,
+                  precond_shift: float = 0.0):
     """Solve every plans[i] system for bs[i] into xs[i] in one graph launch; returns (status, [info dicts])."""
     count = len(plans)
     if not (len(bs) == count == len(xs)) or count == 0:
@@ -313,7 +330,8 @@ def solve_batched(plans, bs, xs, rtol: float = 1e-6, max_iter: int = 10000, x0_g
     hp = (_vp * count)(*[p.handle for p in plans])
     bp = (_vp * count)(*[_ptr(b) for b in bs])
     xp = (_vp * count)(*[_ptr(x) for x in xs])
-    opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, 0.0, 0, int(check_every), 0)
+    opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, 0.0, 0, int(check_every), 0,
+                          _precond_code(precond), float(precond_shift))
     infos = (tca_solve_info * count)()
     st = _lib.tca_solve_batched(count, hp, bp, xp, ctypes.byref(opts), infos, _stream(stream))
     if raise_on_error:
@@ -401,10 +419,10 @@ class Net:
 
     def solve(self, plan: "Plan", b, x, rtol: float = 1e-6, max_iter: int = 10000, check_every: int = 0,
               inner_rtol: float = 0.0, max_refine: int = 0, net_every: int = 0, stream=None,
-              raise_on_error: bool = True, profile: bool = False):
+              raise_on_error: bool = True, profile: bool = False, precond=None, precond_shift: float = 0.0):
         """tca_solve from x0 = s Net(A^T b / s), plus a network step every net_every iterations (0: none)."""
         opts = tca_solve_opts(float(rtol), int(max_iter), 1, float(inner_rtol), int(max_refine), int(check_every),
-                              1 if profile else 0)
+                              1 if profile else 0, _precond_code(precond), float(precond_shift))
         info = tca_solve_info()
         st = _lib.tca_solve_net(plan.handle, self._h, _ptr(b), _ptr(x), ctypes.byref(opts), int(net_every),
                                 ctypes.byref(info), _stream(stream))
