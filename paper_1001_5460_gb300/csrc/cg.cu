@@ -1031,6 +1031,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
   for (int i = 0; i < count; ++i) {
     key.push_back(plans[i]);
     key.push_back((const void*)(uintptr_t)plans[i]->generation);
+    key.push_back((const void*)(uintptr_t)plans[i]->pc_generation);
     key.push_back(b[i]);
     key.push_back(x[i]);
   }

@@ -341,6 +341,13 @@ static bool spd_inverse(std::vector<double>& a, int64_t n) {
 tca_status ensure_precond(tca_plan_s* p, double shift) {
   if (!(shift >= 0.0) || !std::isfinite(shift)) return TCA_ERR_INVALID_ARG;
   if (p->pc_shift == shift && p->z) return TCA_OK;
+  // A cached iteration graph holds the old factors' addresses: drop it.
+  TCA_CUDA_TRY(cudaDeviceSynchronize());
+  if (p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  ++p->pc_generation;
   for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
   p->pc_shift = 0.0;
   for (int k = 0; k < p->d; ++k) {

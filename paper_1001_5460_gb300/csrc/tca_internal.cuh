@@ -137,6 +137,7 @@ struct tca_plan_s {
   // built for shift pc_shift (0: not built); z = M^-1 r.
   tca::ModeOp pc[tca::kMaxModes];
   double pc_shift = 0.0;
+  uint64_t pc_generation = 0;  // bumped whenever the factors are rebuilt (graph cache keys)
   void* z = nullptr;
   bool pc_on = false;       // the iteration being built or run is preconditioned
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)

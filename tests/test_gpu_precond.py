@@ -127,6 +127,41 @@ def test_pcg_batched_matches_single_solves():
         assert abs(infos[i]["iters"] - info1["iters"]) <= 3, (i, infos[i]["iters"], info1["iters"])
 
 
+def test_pcg_host_buffers_match_device():
+    """A preconditioned solve from host buffers (b uploaded under A^T b) gives the device-buffer
+    result bit for bit."""
+    tca = lib()
+    inst = synth.instance_bspline((24, 20, 22, 8), seed=730, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    xd = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), xd, rtol=1e-6, precond="separable")
+    assert st == tca.OK
+    xh = np.zeros(inst.shape, np.float32)
+    st, info_h = plan.solve(np.ascontiguousarray(b), xh, rtol=1e-6, precond="separable")
+    assert st == tca.OK and info_h["iters"] == info["iters"]
+    np.testing.assert_array_equal(xh, xd.cpu().numpy())
+
+
+def test_pcg_shift_change_rebuilds_factors_and_graph():
+    """Switching the shift rebuilds the factors (and drops the cached iteration graph that held
+    the old ones): shift 16, then 32, then 16 again gives the first result bit for bit."""
+    tca = lib()
+    inst = synth.instance_bspline((20, 18, 16, 8), seed=740, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = to_dev((O.apply(inst.x_true, mats) + inst.noise).astype(np.float32), np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    xs = [empty_dev(inst.shape, np.float32) for _ in range(3)]
+    its = []
+    for x, shift in zip(xs, (16.0, 32.0, 16.0)):
+        st, info = plan.solve(b, x, rtol=1e-6, precond="separable", precond_shift=shift)
+        assert st == tca.OK and info["rel_res_true"] <= 1e-6
+        its.append(info["iters"])
+    assert its[0] == its[2]
+    np.testing.assert_array_equal(xs[0].cpu().numpy(), xs[2].cpu().numpy())
+
+
 def test_pcg_argument_checks():
     tca = lib()
     inst = synth.instance_bspline((12, 10, 9, 4), seed=720, dtype=np.float64)
