@@ -48,11 +48,11 @@ __device__ __forceinline__ T group_x_update(T x, const T* __restrict__ const* pb
   return fma(alpha, pnew, x);
 }
 
-template <typename T, bool XUPD>
+template <typename T, bool XUPD, bool PC>
 __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
                                                                 const T* __restrict__ p, const T* __restrict__ q,
                                                                 int64_t n, Scalars* sc, Reduce red, DirBufs<T> pb,
-                                                                int pos, int pc) {
+                                                                int pos) {
   __shared__ double sh[kVecThreads / 32];
   if (cg_done(sc)) return;
   const double alpha_d = sc->alpha;
@@ -113,9 +113,10 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(T* __restrict__ 
   if (dev::grid_sum_last(acc, red, &total, sh)) {
     // <r, r> always feeds the stop test; without a preconditioner it is also
     // rho of the next step (with one, rho = <r, z> comes after z = M^-1 r).
+    const double rho = sc->rho;
     sc->rho_new = total;
-    if (!pc) {
-      sc->beta = total / sc->rho;
+    if constexpr (!PC) {
+      sc->beta = total / rho;
       sc->rho = total;
     }
     sc->iters += 1;
@@ -370,13 +371,15 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, int it, cudaStream_t s,
     TCA_TRY(normal_generic<T>(p, pnew, q, s, &dot));
   }
   if (ev_end) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_end, s, cudaEventRecordExternal));
-  const int pc = p->pc_on ? 1 : 0;
-  if (pos == kDirBufs - 1)
-    cg_update_kernel<T, true><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p), dir_bufs<T>(p),
-                                                           pos, pc);
-  else
-    cg_update_kernel<T, false><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, first_reduce(p),
-                                                            dir_bufs<T>(p), pos, pc);
+  const DirBufs<T> db = dir_bufs<T>(p);
+  const Reduce red = first_reduce(p);
+  if (pos == kDirBufs - 1) {
+    if (p->pc_on) cg_update_kernel<T, true, true><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, red, db, pos);
+    else cg_update_kernel<T, true, false><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, red, db, pos);
+  } else {
+    if (p->pc_on) cg_update_kernel<T, false, true><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, red, db, pos);
+    else cg_update_kernel<T, false, false><<<grid, kVecThreads, 0, s>>>(x, r, pnew, q, N, p->scal, red, db, pos);
+  }
   TCA_LAUNCH_CHECK();
   if (p->pc_on) TCA_TRY(enqueue_precond<T>(p, false, s));
   return TCA_OK;
