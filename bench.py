@@ -15,6 +15,8 @@ on the machine's host cores instead (bounded sample, extrapolated; see below).
 device).  The roofline's sweep time comes from a profiled solve run right after
 each timed one: the same solve with every CG sweep bracketed by CUDA events on
 the solve's stream (one graph pass per launch, the host reading the events).
+``variants`` times the same solve with the separable tensor-inverse
+preconditioner at shifts 16 (the default) and 32, after the plain timing.
 """
 from __future__ import annotations
 

@@ -43,6 +43,31 @@ def test_library_exports_every_declared_symbol(tca):
     assert not missing, missing
 
 
+def _header_struct_fields(name):
+    text = open(os.path.join(ROOT, "include", "tca.h")).read()
+    head = re.split(r"\}\s*" + name + ";", text)[0]
+    body = head.rsplit("typedef struct {", 1)[1]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"^\s*(double|int32_t|int64_t|float)\s+(\w+);", body, flags=re.M)
+
+
+def test_binding_structs_match_the_header(tca):
+    """The ctypes mirrors of tca_solve_opts / tca_solve_info list the header's fields in order,
+    with the same C types (a mismatch would shift every later field across the ABI)."""
+    ctype = {"double": ctypes.c_double, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+             "float": ctypes.c_float}
+    for name, cls in (("tca_solve_opts", tca.tca_solve_opts), ("tca_solve_info", tca.tca_solve_info)):
+        fields = _header_struct_fields(name)
+        assert [(f, ctype[t]) for t, f in fields] == list(cls._fields_), name
+
+
+def test_precond_names(tca):
+    assert tca._precond_code(None) == tca.PRECOND_NONE
+    assert tca._precond_code("separable") == tca.PRECOND_SEPARABLE
+    with pytest.raises(ValueError):
+        tca._precond_code("jacobi")
+
+
 def test_status_strings_and_version(tca):
     assert tca._lib.tca_status_string(0) == b"ok"
     assert tca._lib.tca_status_string(tca.ERR_SHAPE) == b"shape mismatch"
