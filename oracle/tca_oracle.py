@@ -194,12 +194,15 @@ def cg(kop, rhs: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-10,
     return CGResult(c, it, history, history[-1] <= rtol)
 
 
-def separable_inverse_factors(mats, lam: float, shift: float) -> list:
+def separable_inverse_factors(mats, lam: float, shift: float, half_band: int | None = None) -> list:
     """Per-mode factors (A_k^T A_k + shift * lam * D2_k^T D2_k)^-1 of the preconditioner.
 
     The tensor inverse of a separable transformation (Sec. 3, Eq. TensorEq with
     A = A_1 x ... x A_d) is the separable transformation of the per-mode
     inverses; modes with n_k < 3 carry no regulariser, as in ``regulariser``.
+    With ``half_band`` h, each inverse keeps only its entries with |i - j| <= h
+    (a symmetric band; for banded factors the inverses decay away from the
+    diagonal, so a band as wide as the Gram band keeps most of the effect).
     """
     out = []
     for a in mats:
@@ -209,7 +212,12 @@ def separable_inverse_factors(mats, lam: float, shift: float) -> list:
         if n >= 3:
             d2 = second_difference(n)
             m = m + (shift * lam) * (d2.T @ d2)
-        out.append(np.linalg.inv(m))
+        inv = np.linalg.inv(m)
+        inv = 0.5 * (inv + inv.T)  # the inverse of the SPD M_k is symmetric; drop rounding asymmetry
+        if half_band is not None:
+            idx = np.arange(n)
+            inv = np.where(np.abs(idx[:, None] - idx[None, :]) <= half_band, inv, 0.0)
+        out.append(inv)
     return out
 
 
