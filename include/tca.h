@@ -205,8 +205,9 @@ typedef struct {
  * same order and rounding as one update per iteration; a group cut short by
  * the stop test is completed before the true residual is formed), so x is
  * read and written a quarter as often.  Returns TCA_ERR_NOT_CONVERGED (x and info still
- * filled) when max_iter is reached, TCA_ERR_BREAKDOWN when <P, Q> <= 0 or a
- * scalar is not finite.  info may be NULL.  Synchronises the stream. */
+ * filled) when max_iter is reached, TCA_ERR_BREAKDOWN when <P, Q> <= 0 (or,
+ * preconditioned, <R, Z> <= 0) or a scalar is not finite.  opts->precond
+ * selects the optional preconditioner (TCA_PRECOND_* above).  info may be NULL.  Synchronises the stream. */
 TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
                      tca_solve_info* info, cudaStream_t stream);
 
