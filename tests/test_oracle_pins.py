@@ -291,6 +291,29 @@ def test_pcg_with_exact_inverse_takes_one_step():
     np.testing.assert_allclose(res.x, ref, rtol=1e-9, atol=1e-11)
 
 
+def test_pcg_iterates_are_cg_on_the_split_system():
+    """With M = C C^T, preconditioned CG is plain CG on C^-1 K C^-T y = C^-1 rhs: its k-th iterate
+    is C^-T y_k (textbook identity), checked iterate by iterate with explicit matrices."""
+    rng = np.random.default_rng(28)
+    shape, sshape = (4, 3, 5), (6, 5, 7)
+    mats = _rand_mats(rng, shape, sshape)
+    lam = 0.02
+    kmat = O.dense_normal_matrix(mats, lam, shape)
+    inv = O.separable_inverse_factors(mats, lam, 16.0)
+    m_inv = functools.reduce(np.kron, inv)           # M^-1 as a matrix
+    c = np.linalg.cholesky(np.linalg.inv(m_inv))     # M = C C^T
+    c_inv = np.linalg.inv(c)
+    kt = c_inv @ kmat @ c_inv.T
+    b = rng.standard_normal(sshape)
+    rhs = O.apply_T(b, mats)
+    kop = lambda v: O.normal_apply(v, mats, lam)
+    for k in (1, 2, 4, 6):
+        x = O.pcg(kop, lambda r: O.apply_separable(r, inv), rhs, rtol=0.0, max_iter=k).x
+        y = O.cg(lambda v: (kt @ v.ravel()).reshape(v.shape), (c_inv @ rhs.ravel()).reshape(shape),
+                 rtol=0.0, max_iter=k).x
+        np.testing.assert_allclose(x.ravel(), c_inv.T @ y.ravel(), rtol=1e-8, atol=1e-10)
+
+
 def test_pcg_separable_matches_cholesky_and_needs_fewer_iterations():
     """Dense Gaussian factors, small lambda: the separable-inverse PCG reaches the Cholesky solution
     in far fewer iterations than plain CG (the Gram part, whose condition number is the product of
