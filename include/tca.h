@@ -266,7 +266,8 @@ TCA_API int tca_autotuned_chunks(tca_plan_t plan);
  * nothing: its reduction scratch is a fixed 256 KiB device array inside the
  * library, which every GPU that loads the library keeps until the process
  * exits.  The first call on a device looks up that array's address (set-up),
- * so make that first call before any stream capture.  n may not exceed
+ * so make that first call before any stream capture; after a cudaDeviceReset
+ * the next call on that device repeats the set-up.  n may not exceed
  * 134,217,728 (TCA_ERR_UNSUPPORTED, message in tca_last_error_string()).
  * Every call shares the scratch, which keeps the last call's contents; calls
  * that overlap on the GPU (unordered streams) race and give undefined
@@ -274,7 +275,6 @@ TCA_API int tca_autotuned_chunks(tca_plan_t plan);
 TCA_API tca_status tca_rel_residual_noalloc(const double* rhs, const double* kx, int64_t n, double* out,
                                             cudaStream_t stream);
 
-/* Free a plan and its device memory (NULL is ignored). */
 /* Synchronise the stream, then report whether any bounded device wait (TMA
  * and tensor-core pipelines) gave up since the last check: TCA_ERR_TIMEOUT,
  * clearing the flag, or TCA_OK.  The flag is per process, not per plan. */
@@ -287,6 +287,9 @@ TCA_API tca_status tca_check_timeout(cudaStream_t stream);
  * polls < 0.  The context stays usable.  Synchronises the stream. */
 TCA_API tca_status tca_wait_selftest(int64_t polls, cudaStream_t stream);
 
+/* Free a plan and its device memory (NULL is ignored).  Synchronises the
+ * device first, so no work of the plan may still be queued on another stream
+ * that the caller keeps using. */
 TCA_API void tca_destroy(tca_plan_t plan);
 
 /* Static text for a status code. */

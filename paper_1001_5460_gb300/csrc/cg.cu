@@ -657,6 +657,10 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
     TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     TCA_CUDA_TRY(cudaStreamSynchronize(s));
     const double rel = hs->aux;
+    if (std::isnan(rel)) {  // a non-finite b or x0: nothing to refine
+      status = TCA_ERR_BREAKDOWN;
+      break;
+    }
     if (!(rel > rtol)) break;  // converged (or a zero right-hand side)
     if (total >= max_iter || outer >= max_refine) {
       status = TCA_ERR_NOT_CONVERGED;
@@ -796,6 +800,10 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
     TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     TCA_CUDA_TRY(cudaStreamSynchronize(s));
     if (hs->aux <= rtol) break;
+    if (std::isnan(hs->aux)) {  // a non-finite x: restarting cannot recover
+      status = TCA_ERR_BREAKDOWN;
+      break;
+    }
     if (hs->iters >= max_iter) {
       status = TCA_ERR_NOT_CONVERGED;
       break;

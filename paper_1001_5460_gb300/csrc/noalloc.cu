@@ -11,8 +11,10 @@
 //
 // The array below is a static device variable: every GPU that loads this
 // library holds it (256 KiB) until the process exits.  Host code may not use
-// its name as an address; the device address is looked up once per device
-// with cudaGetSymbolAddress during the first call on that device.  Every call
+// its name as an address; the device address is looked up with
+// cudaGetSymbolAddress during the first call on a device (set-up), and again
+// on the first call after that device's context changed (a cudaDeviceReset
+// unloads the module, so an address cached from before would be stale).  Every call
 // shares the array and it keeps the last call's contents, so the call clears
 // the counter it needs at zero before launching, and calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
@@ -38,6 +40,24 @@ static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};  // context the cached address belongs to
+
+// Current driver context (the runtime's primary context of the current
+// device), through the runtime's driver entry point; null if unavailable.
+void* current_context() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  static GetCurrent fn = []() -> GetCurrent {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<GetCurrent>(f);
+    return nullptr;
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 __device__ __forceinline__ double na_block_sum(double v, double* sh) {
   v = tca::dev::warp_sum(v);
@@ -92,7 +112,9 @@ __global__ void __launch_bounds__(kNaThreads) rel_residual_noalloc_kernel(const 
   }
 }
 
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array on the current device: looked up on
+// the first call on that device and again whenever the device's context is
+// not the one the cached address was taken in.
 tca_status scratch_for_current_device(double** addr) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -102,7 +124,8 @@ tca_status scratch_for_current_device(double** addr) {
   }
   if (dev < 0 || dev >= kMaxDevices) return TCA_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  void* ctx = current_context();
+  if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -110,6 +133,8 @@ tca_status scratch_for_current_device(double** addr) {
       return TCA_ERR_CUDA;
     }
     g_scratch_addr[dev] = static_cast<double*>(p);
+    // cudaGetSymbolAddress made the primary context current if it was not yet.
+    g_scratch_ctx[dev] = ctx ? ctx : current_context();
   }
   *addr = g_scratch_addr[dev];
   return TCA_OK;

@@ -195,13 +195,39 @@ def wait_selftest(polls: int, stream=None) -> int:
     return int(_lib.tca_wait_selftest(int(polls), _stream(stream)))
 
 
+def _check_noalloc_args(rhs, kx, out) -> int:
+    """Length n of the no-alloc residual's operands; ValueError unless rhs, kx and out
+    are contiguous float64 CUDA tensors on one device with kx.numel() == n and out
+    holding at least one value (the kernel reads n doubles of each and writes one)."""
+    bufs = {"rhs": rhs, "kx": kx, "out": out}
+    for name, t in bufs.items():
+        if not (hasattr(t, "is_cuda") and hasattr(t, "dtype") and hasattr(t, "numel")):
+            raise ValueError(f"{name} must be a torch CUDA tensor, got {type(t).__name__}")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must live in device memory (got a host tensor)")
+        if str(t.dtype) != "torch.float64":
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if len({t.device for t in bufs.values()}) != 1:
+        raise ValueError("rhs, kx and out must be on the same device")
+    n = int(rhs.numel())
+    if int(kx.numel()) != n:
+        raise ValueError(f"kx holds {kx.numel()} values, rhs {n}")
+    if int(out.numel()) < 1:
+        raise ValueError("out must hold at least one value")
+    return n
+
+
 def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
     """||rhs - kx|| / ||rhs|| of two FP64 device vectors into out (one FP64 device value).
 
     For callers that must not allocate device memory at this point: the library
-    keeps the reduction scratch in a fixed device array of its own.
+    keeps the reduction scratch in a fixed device array of its own.  rhs, kx and
+    out must be contiguous float64 torch CUDA tensors on one device (ValueError
+    otherwise, before anything reaches the library).
     """
-    n = int(rhs.numel() if hasattr(rhs, "numel") else np.asarray(rhs).size)
+    n = _check_noalloc_args(rhs, kx, out)
     return _check(_lib.tca_rel_residual_noalloc(_ptr(rhs), _ptr(kx), n, _ptr(out), _stream(stream)),
                   "tca_rel_residual_noalloc")
 

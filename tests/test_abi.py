@@ -138,3 +138,42 @@ def test_net_init_params_layout():
         assert w.shape == (co, ci, 3, 3, 3) and not b.any()
         std = np.sqrt(2.0 / (27 * ci)) * (0.1 if li == 3 else 1.0)
         assert abs(w.std() / std - 1.0) < 0.25
+
+
+def test_noalloc_binding_rejects_bad_buffers_before_the_call(tca):
+    """rel_residual_noalloc hands raw pointers to a kernel that reads n doubles of rhs and kx
+    and writes one to out: host arrays, host tensors, other dtypes, a shorter kx or an empty
+    out are refused in Python, before anything reaches the library."""
+    import torch
+
+    class FakeDev:
+        """Stands in for a CUDA tensor (none exists on this machine); never reaches the library."""
+
+        def __init__(self, n, dtype=torch.float64, device="cuda:0", contiguous=True):
+            self.is_cuda, self.dtype, self.device, self._n, self._c = True, dtype, device, n, contiguous
+
+        def numel(self):
+            return self._n
+
+        def is_contiguous(self):
+            return self._c
+
+        def data_ptr(self):  # pragma: no cover - a call getting here is the failure
+            raise AssertionError("validation let a bad buffer through")
+
+    good = FakeDev(8)
+    h = np.zeros(8)
+    with pytest.raises(ValueError, match="torch CUDA tensor"):
+        tca.rel_residual_noalloc(h, good, FakeDev(1))
+    with pytest.raises(ValueError, match="device memory"):
+        tca.rel_residual_noalloc(torch.zeros(8, dtype=torch.float64), good, FakeDev(1))
+    with pytest.raises(ValueError, match="float64"):
+        tca.rel_residual_noalloc(FakeDev(8, dtype=torch.float32), good, FakeDev(1))
+    with pytest.raises(ValueError, match="kx holds"):
+        tca.rel_residual_noalloc(good, FakeDev(7), FakeDev(1))
+    with pytest.raises(ValueError, match="at least one"):
+        tca.rel_residual_noalloc(good, FakeDev(8), FakeDev(0))
+    with pytest.raises(ValueError, match="same device"):
+        tca.rel_residual_noalloc(good, FakeDev(8, device="cuda:1"), FakeDev(1))
+    with pytest.raises(ValueError, match="contiguous"):
+        tca.rel_residual_noalloc(good, FakeDev(8, contiguous=False), FakeDev(1))

@@ -66,3 +66,46 @@ def test_noalloc_rejects_oversized_and_bad_arguments():
     assert f(a.data_ptr(), a.data_ptr(), 0, out.data_ptr(), None) == tca.OK
     torch.cuda.synchronize()
     assert out.item() == 0.0
+
+
+@pytest.mark.parametrize("n", [3 * 8192 + 17, 160 * 160 * 160 * 8])
+def test_noalloc_residual_across_many_blocks_twice(n):
+    """Lengths that span many reduction blocks and end in a ragged block: the per-block
+    partials in the library's fixed array, the last-block reduction and the counter reset
+    all run.  Each length is checked on two calls in a row with different data, then
+    once more after a shorter call has left other partials behind, against NumPy's FP64
+    norms of the same vectors."""
+    tca = lib()
+    torch = need_cuda()
+    rng = np.random.default_rng(n)
+    rhs = rng.standard_normal(n)
+    kx1 = rhs + 1e-3 * rng.standard_normal(n)
+    kx2 = rhs * (1.0 + 1e-2 * rng.standard_normal(n))
+    want = [np.linalg.norm(rhs - k) / np.linalg.norm(rhs) for k in (kx1, kx2)]
+    rd = to_dev(rhs, np.float64)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    for k, w in zip((kx1, kx2), want):
+        tca.rel_residual_noalloc(rd, to_dev(k, np.float64), out)
+        torch.cuda.synchronize()
+        assert abs(out.item() - w) <= 1e-12 * w, (n, out.item(), w)
+    # A short call (one block) in between leaves stale partials in the array.
+    short = to_dev(np.ones(100), np.float64)
+    tca.rel_residual_noalloc(short, short, out)
+    torch.cuda.synchronize()
+    assert out.item() == 0.0
+    tca.rel_residual_noalloc(rd, to_dev(kx1, np.float64), out)
+    torch.cuda.synchronize()
+    assert abs(out.item() - want[0]) <= 1e-12 * want[0]
+
+
+def test_noalloc_binding_rejects_device_buffers_of_the_wrong_kind():
+    tca = lib()
+    torch = need_cuda()
+    a = torch.zeros(64, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError, match="float64"):
+        tca.rel_residual_noalloc(a.float(), a, out)
+    with pytest.raises(ValueError, match="kx holds"):
+        tca.rel_residual_noalloc(a, a[:32], out)
+    with pytest.raises(ValueError, match="device memory"):
+        tca.rel_residual_noalloc(a, a, out.cpu())
