@@ -77,10 +77,18 @@ typedef enum {
  * factors: 3xTF32 tensor-core products, about FP32 accuracy).  The _IR forms
  * keep float data at the boundary and solve by iterative refinement: an
  * outer loop on the FP64-accurate (double-float) residual and an inner CG to
- * a loose tolerance with reduced-precision operators - plain TF32
- * tensor-core products for dense factors (both _IR forms in this version);
- * banded factors run the inner CG in FP32 (bf16 vector storage is not
- * implemented yet). */
+ * a loose tolerance with a reduced-precision operator:
+ *   TCA_TF32_IR  plain TF32 tensor-core products for dense factors; banded
+ *                factors keep the FP32 sweep;
+ *   TCA_BF16_IR  banded (ELL4) factors only: the inner CG keeps r, p and q in
+ *                bfloat16 and applies the normal operator with the modes-3/4
+ *                contraction (G_3 kron G_4 and its regulariser) on the tensor
+ *                cores in BF16 with FP32 accumulation, modes 1-2 in FP32;
+ *                tca_apply_normal rounds x to bfloat16 and returns K x through
+ *                the same sweep (tca_apply / tca_apply_T stay FP32).  tca_plan
+ *                returns TCA_ERR_UNSUPPORTED for dense factors, n4 > 8 or an
+ *                inner axis n3*n4 (n3 for order 3) that is not a multiple of 8.
+ * CG scalars and every inner product stay FP64 in all forms. */
 typedef enum { TCA_F64 = 0, TCA_F32 = 1, TCA_BF16_IR = 2, TCA_TF32_IR = 3 } tca_precision;
 
 typedef enum {
@@ -206,7 +214,13 @@ typedef struct {
  * the stop test is completed before the true residual is formed), so x is
  * read and written a quarter as often.  Returns TCA_ERR_NOT_CONVERGED (x and info still
  * filled) when max_iter is reached, TCA_ERR_BREAKDOWN when <P, Q> <= 0 (or,
- * preconditioned, <R, Z> <= 0) or a scalar is not finite.  opts->precond
+ * preconditioned, <R, Z> <= 0) or a scalar is not finite - a NaN or Inf in b
+ * or in the initial guess ends that way; x then holds the last iterate and
+ * info->rel_res_true its true residual.  A singular K (lambda = 0 and a
+ * factor of rank below n_k) still gives a consistent system, since A^T b
+ * lies in K's range: FP64 plans converge to a least-squares solution, while
+ * FP32 roundings can feed K's null space into the directions until
+ * <P, Q> <= 0, which is reported as TCA_ERR_BREAKDOWN.  opts->precond
  * selects the optional preconditioner (TCA_PRECOND_* above).  info may be NULL.  Synchronises the stream. */
 TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
                      tca_solve_info* info, cudaStream_t stream);
@@ -240,20 +254,28 @@ TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_
 TCA_API tca_status tca_solve_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
                                      const tca_solve_opts* opts, tca_solve_info* info, cudaStream_t stream);
 
-/* Autotune the plan's fused normal-operator sweep: time the sweep for a few
- * tile extents along mode 1 around the cost model's choice (the plan-time
- * expression analysis of Sec. 2.1 and Sec. 4, which picks evaluation orders
- * and kernels by cost, extended with a measurement on this GPU) and keep the
- * fastest in the plan.  Results are cached per shape (n_1..n_4) for the life
- * of the process, so a second plan of the same shape tunes in no time.  Plans
- * without the fused sweep (TCA_F64, dense factors, order 4 with n_4 other
- * than 4 or 8) return TCA_OK unchanged.  Uses the plan's workspace; call it before a solve
- * (not concurrently with one on this plan).  Synchronises the stream. */
+/* Autotune the normal-operator sweep that the plan's CG iterations run (its
+ * CG form: new direction, K p and <p, K p>): time it for a few tile extents
+ * along mode 1 around the cost model's choice and, for TCA_BF16_IR plans,
+ * for both worker layouts of the tensor-core sweep (4 or 8 core rows per
+ * thread), and keep the fastest in the plan (the plan-time expression
+ * analysis of Sec. 2.1 and Sec. 4, which picks evaluation orders and kernels
+ * by cost, extended with a measurement on this GPU).  Results are cached per
+ * precision and shape (n_1..n_4) for the life of the process, so a second plan
+ * of the same kind tunes in no time.  Plans without a fused sweep (TCA_F64,
+ * dense factors, order 4 with n_4 other than 4 or 8 outside TCA_BF16_IR)
+ * return TCA_OK unchanged.  Overwrites the plan's solver vectors and scalars
+ * (every solve sets them up again); call it before a solve, not concurrently
+ * with one on this plan.  Synchronises the stream. */
 TCA_API tca_status tca_autotune(tca_plan_t plan, cudaStream_t stream);
 
 /* Tile extent the autotuner chose for the plan (chunks of mode 1), or 0 when
  * the plan uses the cost model. */
 TCA_API int tca_autotuned_chunks(tca_plan_t plan);
+
+/* Worker layout the autotuner chose for a TCA_BF16_IR plan's tensor-core sweep
+ * (core rows per thread: 4 or 8), or 0 when it has not tuned the plan. */
+TCA_API int tca_autotuned_rows(tca_plan_t plan);
 
 /* Relative residual ||rhs - kx||_2 / ||rhs||_2 of two FP64 device vectors of
  * length n, written to *out (device memory, one double).  If ||rhs|| is zero

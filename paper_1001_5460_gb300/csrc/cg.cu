@@ -280,6 +280,12 @@ __global__ void __launch_bounds__(kVecThreads) true_residual_kernel(const double
   }
 }
 
+// Every element of x set to the bit pattern v.
+template <typename U>
+__global__ void fill_bits_kernel(U* __restrict__ x, U v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
 __global__ void cg_setup_kernel(Scalars* sc, double rtol, int max_iter) {
   sc->rtol = rtol;
   sc->max_iter = max_iter;
@@ -347,9 +353,24 @@ static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
 // of kDirBufs iterations, so it % kDirBufs is the position in the update
 // group).  ev_begin/ev_end (may be null) bracket the normal-operator sweep so
 // that a profiled solve can time it on the device.
+// One iteration of a TCA_BF16_IR plan's inner CG: the bfloat16 tensor-core
+// sweep (p = r + beta p_old, q = K p, alpha) and the bfloat16 update of r and of
+// the FP32 correction d.
+static tca_status enqueue_iteration_bf16(tca_plan_s* p, float* d, int it, cudaStream_t s, cudaEvent_t ev_begin,
+                                         cudaEvent_t ev_end) {
+  const int pos = it % kDirBufs;
+  if (ev_begin) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_begin, s, cudaEventRecordExternal));
+  TCA_TRY(bf16_sweep(p, pos, p->bf.p[(pos + 1) % kDirBufs], p->bf.q, s));
+  if (ev_end) TCA_CUDA_TRY(cudaEventRecordWithFlags(ev_end, s, cudaEventRecordExternal));
+  return bf16_update(p, d, pos, first_reduce(p), s);
+}
+
 template <typename T>
 static tca_status enqueue_iteration(tca_plan_s* p, T* x, int it, cudaStream_t s, cudaEvent_t ev_begin,
                                     cudaEvent_t ev_end) {
+  if constexpr (sizeof(T) == 4) {
+    if (p->prec == TCA_BF16_IR) return enqueue_iteration_bf16(p, (float*)x, it, s, ev_begin, ev_end);
+  }
   const int64_t N = p->N;
   const int pos = it % kDirBufs;
   const T* pold = (const T*)p->p[pos];
@@ -389,6 +410,9 @@ static tca_status enqueue_iteration(tca_plan_s* p, T* x, int it, cudaStream_t s,
 // iteration loop.
 template <typename T>
 static tca_status flush_pending_x(tca_plan_s* p, T* x, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (p->prec == TCA_BF16_IR) return bf16_flush(p, (float*)x, first_reduce(p), s);
+  }
   const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
   cg_flush_x_kernel<T><<<grid, kVecThreads, 0, s>>>(x, p->N, p->scal, first_reduce(p), dir_bufs<T>(p));
   TCA_LAUNCH_CHECK();
@@ -409,6 +433,28 @@ static tca_status ensure_solver_buffers(tca_plan_s* p) {
     set_cuda_error(e);
     return TCA_ERR_ALLOC;
   }
+  return TCA_OK;
+}
+
+// State in which a CG-mode sweep does its full work outside a solve (for the
+// autotuner): solver buffers allocated, r and the directions zero, scalars of
+// a fresh iteration that is not converged.  A later solve re-initialises all
+// of it.
+tca_status prepare_sweep_timing(tca_plan_s* p, cudaStream_t s) {
+  if (p->prec == TCA_F64) return TCA_ERR_UNSUPPORTED;
+  TCA_TRY(ensure_solver_buffers<float>(p));
+  // r = 1 everywhere (so <p, K p> > 0 and the sweep never flags a breakdown), directions 0.
+  const int grid = vector_grid(p, p->N);
+  fill_bits_kernel<uint32_t><<<grid, kVecThreads, 0, s>>>((uint32_t*)p->r, 0x3f800000u, p->N);
+  TCA_LAUNCH_CHECK();
+  for (int k = 0; k < kDirBufs; ++k) TCA_CUDA_TRY(cudaMemsetAsync(p->p[k], 0, sizeof(float) * (size_t)p->N, s));
+  if (p->prec == TCA_BF16_IR) {
+    fill_bits_kernel<uint16_t><<<grid, kVecThreads, 0, s>>>((uint16_t*)p->bf.r, (uint16_t)0x3f80u, p->N);
+    TCA_LAUNCH_CHECK();
+    for (int k = 0; k < kDirBufs; ++k) TCA_CUDA_TRY(cudaMemsetAsync(p->bf.p[k], 0, 2 * (size_t)p->N, s));
+  }
+  cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, 0.0, 1 << 30);
+  TCA_LAUNCH_CHECK();
   return TCA_OK;
 }
 
@@ -613,8 +659,11 @@ __global__ void axpy_f32_kernel(float* __restrict__ x, const float* __restrict__
 // Mixed precision with iterative refinement (the _IR plans): an outer loop in
 // FP64-accurate arithmetic (double-float residual r = A^T b - K x), an inner
 // CG on K d = r run to inner_rtol with the plan's reduced-precision operator
-// (plain TF32 tensor-core products for dense factors), and x += d, until the
-// true relative residual meets rtol.
+// (TF32_IR: plain TF32 tensor-core products for dense factors, FP32 sweeps for
+// banded ones; BF16_IR: bfloat16 vectors and the bfloat16 tensor-core sweep),
+// and x += d, until the true relative residual meets rtol.  From x = 0 the
+// first outer residual is A^T b itself, whose FP32 rounding the A^T b chain
+// already left in p->rhs, so the first residual evaluation is skipped.
 static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_solve_opts* o, tca_solve_info* info,
                            cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -640,6 +689,11 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
   double sweep_ms = 0.0;
   int sweep_n = 0;
   float* d = p->dbuf;
+  const bool bf = p->prec == TCA_BF16_IR;
+  if (bf && o && o->precond != TCA_PRECOND_NONE) {
+    set_error_message("TCA_BF16_IR plans take no preconditioner");
+    return TCA_ERR_UNSUPPORTED;
+  }
   TCA_TRY(setup_precond(p, o));
   TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
                    reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
@@ -650,13 +704,20 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
   tca_status status = TCA_OK;
   int total = 0, outer = 0;
   double rec = 0.0;
+  bool first = true;
   for (;;) {
     // Outer residual in double-float: p->rhs <- r (FP32), scal->aux <- ||r|| / ||A^T b||.
-    TCA_TRY(residual_ff(p, x, reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
-                        (float*)p->rhs, first_reduce(p), second_reduce(p), s));
-    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-    TCA_CUDA_TRY(cudaStreamSynchronize(s));
-    const double rel = hs->aux;
+    double rel = 1.0;
+    if (first && !(o && o->x0_given)) {
+      hs->aux = 1.0;  // r = A^T b (already in p->rhs); a zero b is caught by the inner start
+    } else {
+      TCA_TRY(residual_ff(p, x, reinterpret_cast<const float2*>(p->rhs64), reinterpret_cast<float2*>(p->res64),
+                          (float*)p->rhs, first_reduce(p), second_reduce(p), s));
+      TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+      TCA_CUDA_TRY(cudaStreamSynchronize(s));
+      rel = hs->aux;
+    }
+    first = false;
     if (std::isnan(rel)) {  // a non-finite b or x0: nothing to refine
       status = TCA_ERR_BREAKDOWN;
       break;
@@ -670,11 +731,16 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
     // Inner CG from d = 0 on K d = r, to inner_rtol relative to ||r||.
     cg_setup_kernel<<<1, 1, 0, s>>>(p->scal, inner, max_iter - total);
     TCA_LAUNCH_CHECK();
-    TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(float) * N, s));
     TCA_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(float) * N, s));
-    cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, nullptr, (float*)p->r, N, p->scal,
-                                                          first_reduce(p), 1, second_reduce(p));
-    TCA_LAUNCH_CHECK();
+    if (bf) {
+      TCA_CUDA_TRY(cudaMemsetAsync(p->bf.p[0], 0, 2 * (size_t)N, s));
+      TCA_TRY(bf16_start(p, (const float*)p->rhs, first_reduce(p), s));
+    } else {
+      TCA_CUDA_TRY(cudaMemsetAsync(p->p[0], 0, sizeof(float) * N, s));
+      cg_start_kernel<float><<<vgrid, kVecThreads, 0, s>>>((const float*)p->rhs, nullptr, (float*)p->r, N, p->scal,
+                                                            first_reduce(p), 1, second_reduce(p));
+      TCA_LAUNCH_CHECK();
+    }
     if (p->pc_on) TCA_TRY(enqueue_precond<float>(p, true, s));
     TCA_TRY(cg_iterate(p, inner, max_iter - total, every, profile, &sweep_ms, &sweep_n, s));
     TCA_TRY(flush_pending_x<float>(p, d, s));
@@ -788,7 +854,11 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
       TCA_CUDA_TRY(cudaMemcpyAsync(x_host, x, sizeof(T) * (size_t)p->N, cudaMemcpyDeviceToHost, p->copy_stream));
     }
     if (hs->breakdown) {
+      // Report the true residual of the iterate the breakdown left behind.
       status = TCA_ERR_BREAKDOWN;
+      TCA_TRY(true_residual<T>(p, x, false, s));
+      TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+      TCA_CUDA_TRY(cudaStreamSynchronize(s));
       break;
     }
     if (hs->bnorm == 0.0) {

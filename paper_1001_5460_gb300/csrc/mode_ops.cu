@@ -610,6 +610,7 @@ extern "C" tca_status tca_apply_normal(tca_plan_t plan, const void* x, void* y, 
   tca_plan_s* p = plan;
   return with_staging(p, x, p->N, y, p->N, stream, [&](const void* a, void* b) -> tca_status {
     if (p->prec == TCA_F64) return normal_generic<double>(p, (const double*)a, (double*)b, stream);
+    if (p->prec == TCA_BF16_IR) return normal_bf16(p, (const float*)a, (float*)b, stream);
     if (p->fused_ok && (uintptr_t)a % 16 == 0)
       return normal_fused_f32(p, nullptr, (const float*)a, nullptr, (float*)b, false, stream);
     return normal_generic<float>(p, (const float*)a, (float*)b, stream);

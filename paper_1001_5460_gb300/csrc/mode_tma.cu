@@ -392,6 +392,11 @@ int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W) {
 
 bool encode_tmap_f32(CUtensorMap* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                      const uint32_t* box) {
+  return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, base, rank, dims, strides, box);
+}
+
+bool encode_tmap(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int rank, const uint64_t* dims,
+                 const uint64_t* strides, const uint32_t* box) {
   EncodeFn enc = get_encode();
   if (!enc || rank < 1 || rank > 5) return false;
   cuuint64_t d[5], st[4];
@@ -402,7 +407,7 @@ bool encode_tmap_f32(CUtensorMap* map, const void* base, int rank, const uint64_
     es[i] = 1;
     if (i + 1 < rank) st[i] = strides[i];
   }
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), d, st, b, es,
+  return enc(map, dtype, (cuuint32_t)rank, const_cast<void*>(base), d, st, b, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

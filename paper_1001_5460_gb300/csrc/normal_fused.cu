@@ -56,8 +56,8 @@ struct FusedArgs {
   // read straight from the parameter bank (the same for every CTA and plane).
   float g4c[7 * 8];
   float l4c[5 * 8];
-  // Warp-specialised sweep with TMA halo loads: 4D maps (n4, n3, n2, n1) of r
-  // and p_old, box (8, 22, 22, 1) = one halo tile; set by the TMA launch only.
+  // Warp-specialised sweep with TMA halo loads: 3D maps (n3 n4, n2, n1) of r
+  // and p_old, box (176, 22, 1) = one halo tile; set by the TMA launch only.
   CUtensorMap tm_r;
   CUtensorMap tm_p;
   int* timeout_flag;
@@ -97,6 +97,14 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, unsigned parity)
     if (ok) return true;
   }
   return false;
+}
+__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
 }
 __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {
@@ -727,7 +735,7 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
         mbar_expect_tx(&tbar[b], TMA_BYTES);
 #pragma unroll
         for (int src_i = 0; src_i < NIN; ++src_i)
-          tma_load_4d(s_in + (b * 2 + src_i) * C::TILE, (CG && src_i == 0) ? &a.tm_r : &a.tm_p, 0, i3_0 - 3,
+          tma_load_3d(s_in + (b * 2 + src_i) * C::TILE, (CG && src_i == 0) ? &a.tm_r : &a.tm_p, (i3_0 - 3) * N4,
                       i2_0 - 3, jj, &tbar[b]);
       }
     };
@@ -1247,13 +1255,15 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   // Halo tiles by TMA when both maps encode (16-byte aligned tensors); else cp.async.
   bool tma = true;
   {
-    const uint64_t dims[4] = {8, (uint64_t)a.n3, (uint64_t)a.n2, (uint64_t)a.n1};
-    const uint64_t strides[3] = {8 * sizeof(float), (uint64_t)a.n3 * 8 * sizeof(float),
-                                 (uint64_t)a.n2 * a.n3 * 8 * sizeof(float)};
+    // Modes 3 and 4 merged into one contiguous row of n3 * 8 floats: a halo
+    // row is one 704-byte run of the box, so a plane's tile is 22 row
+    // requests (a 32-byte innermost box dimension would take 484).
+    const uint64_t dims[3] = {(uint64_t)a.n3 * 8, (uint64_t)a.n2, (uint64_t)a.n1};
+    const uint64_t strides[2] = {(uint64_t)a.n3 * 8 * sizeof(float), (uint64_t)a.n2 * a.n3 * 8 * sizeof(float)};
     // One box per tensor and plane; boxes wider than the tensor are left to cp.async.
-    const uint32_t box[4] = {8, 22, 22, 1};
-    tma = a.n2 >= 22 && a.n3 >= 22 && encode_tmap_f32(&a.tm_p, a.pold, 4, dims, strides, box);
-    if (tma && CG) tma = encode_tmap_f32(&a.tm_r, a.r, 4, dims, strides, box);
+    const uint32_t box[3] = {22 * 8, 22, 1};
+    tma = a.n2 >= 22 && a.n3 >= 22 && encode_tmap_f32(&a.tm_p, a.pold, 3, dims, strides, box);
+    if (tma && CG) tma = encode_tmap_f32(&a.tm_r, a.r, 3, dims, strides, box);
   }
   a.timeout_flag = wait_timeout_flag();
   auto kfn = tma ? ws::fused_ws_kernel<CG, true> : ws::fused_ws_kernel<CG, false>;

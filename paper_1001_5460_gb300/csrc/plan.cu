@@ -453,6 +453,7 @@ static void destroy_plan(tca_plan_s* p) {
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (cudaEvent_t& ev : p->sweep_ev)
     if (ev) cudaEventDestroy(ev);
+  bf16_release(p);
   cudaFree(p->scal);
   if (p->scal_host) cudaFreeHost(p->scal_host);
   cudaFree(p->red.partials);
@@ -551,6 +552,16 @@ extern "C" tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, con
     set_cuda_error(e);
     destroy_plan(p);
     return TCA_ERR_ALLOC;
+  }
+  // bfloat16 plans: the tensor-core sweep's operand tiles and vectors.
+  if (prec == TCA_BF16_IR) {
+    const tca_status bs = bf16_prepare(p);
+    if (bs != TCA_OK) {
+      if (bs == TCA_ERR_UNSUPPORTED)
+        set_error_message("TCA_BF16_IR needs banded (ELL4) factors, n4 <= 8 and n3*n4 a multiple of 8");
+      destroy_plan(p);
+      return bs;
+    }
   }
   *out = p;
   return TCA_OK;

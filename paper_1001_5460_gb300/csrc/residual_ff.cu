@@ -377,7 +377,9 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(const float2* __restri
   const bool l2 = dev::grid_sum_last(a_bb, red2, &t_bb, sh);
   if (l2) {
     __threadfence();
-    sc->aux = sqrt(((volatile double*)red2.partials)[red2.max_blocks - 1]) / sqrt(t_bb);
+    // Relative norm; the absolute one when the right-hand side is zero (0 for x = 0).
+    const double rr = sqrt(((volatile double*)red2.partials)[red2.max_blocks - 1]);
+    sc->aux = t_bb > 0.0 ? rr / sqrt(t_bb) : rr;
   }
 }
 
@@ -479,7 +481,9 @@ __global__ void __launch_bounds__(256, 4) residual_ff_vec_kernel(const float2* _
   const bool l2 = dev::grid_sum_last(a_bb, red2, &t_bb, sh);
   if (l2) {
     __threadfence();
-    sc->aux = sqrt(((volatile double*)red2.partials)[red2.max_blocks - 1]) / sqrt(t_bb);
+    // Relative norm; the absolute one when the right-hand side is zero (0 for x = 0).
+    const double rr = sqrt(((volatile double*)red2.partials)[red2.max_blocks - 1]);
+    sc->aux = t_bb > 0.0 ? rr / sqrt(t_bb) : rr;
   }
 }
 

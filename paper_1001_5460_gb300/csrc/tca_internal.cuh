@@ -101,6 +101,26 @@ struct Reduce {
   int max_blocks = 0;
 };
 
+// State of a TCA_BF16_IR plan's inner CG (normal_bf16.cu): the inner axis
+// c = (i3, i4) of length nc split into tiles of 128, each with its W = G_3 kron
+// G_4 and R = lambda (L_3 kron I + I kron L_4) operand tiles (bfloat16,
+// KC chunks of 8 inputs x 128 outputs x 16 bytes, W then R per tile), the
+// bfloat16 CG vectors and their TMA views.
+struct Bf16State {
+  int64_t nc = 0;
+  int H = 0, KC = 0, ctiles = 0;
+  int nchunks = 0;                  // tile extent along mode 1 chosen by tca_autotune (0: wave model)
+  int model_nchunks = 0;            // chunk count the last sweep launched with
+  int rpt = 4;                      // core rows per worker thread (4: 16 worker warps, 8: 8), autotuned
+  void* wt = nullptr;               // device operand tiles
+  __nv_bfloat16* r = nullptr;       // inner residual
+  __nv_bfloat16* q = nullptr;       // K p
+  __nv_bfloat16* x = nullptr;       // staging of a plain sweep's input
+  __nv_bfloat16* p[kDirBufs] = {};  // rotating directions
+  bool tma = false;                 // halo tiles by TMA (else cp.async pieces)
+  CUtensorMap tm_r, tm_x, tm_p[kDirBufs];
+};
+
 }  // namespace tca
 
 struct tca_plan_s {
@@ -146,6 +166,7 @@ struct tca_plan_s {
   cudaEvent_t copy_ev = nullptr;       // under the true residual
   cudaEvent_t chunk_ev[8] = {};
 
+  tca::Bf16State bf;             // TCA_BF16_IR plans
   tca::Scalars* scal = nullptr;  // device
   tca::Scalars* scal_host = nullptr;  // pinned mirror
   tca::Reduce red;
@@ -273,6 +294,24 @@ tca_status check_wait_timeout(cudaStream_t s);
 // (alignment) or the encoder is unavailable.
 bool encode_tmap_f32(CUtensorMap* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                      const uint32_t* box);
+
+// Tiled tensor map of any element type (no swizzle, zero fill out of bounds).
+bool encode_tmap(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int rank, const uint64_t* dims,
+                 const uint64_t* strides, const uint32_t* box);
+
+// bfloat16 tensor-core normal operator and inner-CG kernels (normal_bf16.cu).
+bool bf16_shape_ok(const tca_plan_s* p);
+tca_status bf16_prepare(tca_plan_s* p);
+void bf16_release(tca_plan_s* p);
+tca_status bf16_sweep(tca_plan_s* p, int pold_idx, __nv_bfloat16* pnew, __nv_bfloat16* q, cudaStream_t s);
+tca_status normal_bf16(tca_plan_s* p, const float* x, float* y, cudaStream_t s);
+tca_status bf16_start(tca_plan_s* p, const float* src, Reduce red, cudaStream_t s);
+tca_status bf16_update(tca_plan_s* p, float* d, int pos, Reduce red, cudaStream_t s);
+tca_status bf16_flush(tca_plan_s* p, float* d, Reduce red, cudaStream_t s);
+
+// Solver buffers and scalars set so that a CG-mode sweep runs in full outside
+// a solve (the autotuner times the sweep that solves run).
+tca_status prepare_sweep_timing(tca_plan_s* p, cudaStream_t s);
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);

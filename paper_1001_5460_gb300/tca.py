@@ -95,6 +95,8 @@ _lib.tca_autotune.argtypes = [_vp, _vp]
 _lib.tca_autotune.restype = ctypes.c_int
 _lib.tca_autotuned_chunks.argtypes = [_vp]
 _lib.tca_autotuned_chunks.restype = ctypes.c_int
+_lib.tca_autotuned_rows.argtypes = [_vp]
+_lib.tca_autotuned_rows.restype = ctypes.c_int
 _lib.tca_net_param_count.argtypes = []
 _lib.tca_net_param_count.restype = ctypes.c_int64
 _lib.tca_net_create.argtypes = [ctypes.POINTER(_vp), _vp, _vp]
@@ -234,7 +236,7 @@ def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
 
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",
@@ -335,9 +337,14 @@ class Plan:
         return st, _info_dict(info)
 
     def autotune(self, stream=None) -> int:
-        """Time the fused sweep's tile extents on this GPU and keep the fastest; returns the choice (0: none)."""
+        """Time the CG sweep's tile extents (and, bfloat16 plans, worker layouts) on this GPU and
+        keep the fastest; returns the chunk count chosen (0: none)."""
         _check(_lib.tca_autotune(self._h, _stream(stream)), "tca_autotune")
         return int(_lib.tca_autotuned_chunks(self._h))
+
+    def autotuned_rows(self) -> int:
+        """Core rows per worker thread the autotuner chose for a bfloat16 plan (0: not tuned)."""
+        return int(_lib.tca_autotuned_rows(self._h))
 
 
 def _info_dict(info) -> dict:

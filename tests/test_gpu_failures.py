@@ -102,9 +102,12 @@ def test_nan_in_one_batched_instance_leaves_the_others_converged():
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_singular_normal_operator(precision):
     """lambda = 0 and factors with fewer rows than columns: K = kron(A_k^T A_k) is singular
-    (rank 10^3 of 16^3).  A^T b lies in K's range, so the system is consistent and CG
-    converges to a least-squares solution, as the header states; the result must then
-    satisfy the normal equations by the oracle's own FP64 residual."""
+    (rank 10^3 of 16^3).  A^T b lies in K's range, so the system is consistent: the FP64
+    plan converges to a least-squares solution (checked by the oracle's own FP64
+    residual).  In FP32 the roundings feed K's null space into the directions until
+    <p, Kp> stops being positive; the header documents TCA_ERR_BREAKDOWN for that case
+    (or NOT_CONVERGED / OK if the iteration outruns it), with x the last iterate and its
+    true residual reported.  Either way x is finite and the plan solves again."""
     tca = lib()
     torch = need_cuda()
     rng = np.random.default_rng(5)
@@ -119,6 +122,20 @@ def test_singular_normal_operator(precision):
     plan = tca.plan_from_instance(inst, precision=precision)
     x = torch.zeros(inst.shape, dtype=torch.float64 if dtype == np.float64 else torch.float32, device="cuda")
     st, info = plan.solve(to_dev(b, dtype), x, rtol=1e-6, max_iter=4000, raise_on_error=False)
-    assert st == tca.OK, (st, info)
-    assert np.isfinite(x.cpu().numpy()).all()
-    assert O.rel_residual(x.cpu().numpy().astype(np.float64), b, mats, 0.0) <= 1.5e-6
+    xs = x.cpu().numpy().astype(np.float64)
+    assert np.isfinite(xs).all()
+    rel = O.rel_residual(xs, b, mats, 0.0)
+    if precision == "f64":
+        assert st == tca.OK, (st, info)
+        assert rel <= 1.5e-6
+    else:
+        assert st in (tca.OK, tca.ERR_BREAKDOWN, tca.ERR_NOT_CONVERGED), (st, info)
+        if st == tca.OK:
+            assert rel <= 1.5e-6
+        else:
+            # The reported residual is the iterate's own, not a placeholder.
+            assert abs(info["rel_res_true"] - rel) <= 1e-3 * rel + 1e-9, (info, rel)
+    # A regular problem on a fresh plan right after: the context is fine.
+    inst2, mats2, b2 = _bspline_case()
+    plan2 = tca.plan_from_instance(inst2, precision="f32")
+    _assert_recovers(tca, plan2, inst2, mats2, b2, np.float32)

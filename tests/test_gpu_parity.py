@@ -347,7 +347,7 @@ def test_dense_products_on_tensor_cores(shape):
 
 
 @pytest.mark.parametrize("kind,shape,prec", [("dense", (20, 18, 16, 4), "tf32_ir"),
-                                             ("dense", (24, 30, 20), "bf16_ir"),
+                                             ("dense", (24, 30, 20), "tf32_ir"),
                                              ("bspline", (24, 20, 22, 8), "bf16_ir"),
                                              ("bspline", (20, 22, 18, 4), "tf32_ir")])
 def test_solve_mixed_precision_refinement(kind, shape, prec):
