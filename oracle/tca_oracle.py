@@ -221,6 +221,36 @@ def separable_inverse_factors(mats, lam: float, shift: float, half_band: int | N
     return out
 
 
+def jacobi_diagonal(mats, lam: float, shape) -> np.ndarray:
+    """diag(K) of K = A^T A + lam R as an n-shaped tensor: the point-Jacobi
+    preconditioner of the Fig. 1 solver family.
+
+    Written from the definitions: the diagonal entry of the Kronecker product
+    A_1^T A_1 x ... x A_d^T A_d at (i_1, ..., i_d) is the product of the
+    per-mode diagonal entries, and the regulariser sum_k I x .. x D2_k^T D2_k x
+    .. x I adds the k-th mode's diagonal entry of D2_k^T D2_k (modes with
+    n_k < 3 carry none, as in ``regulariser``).
+    """
+    d = len(shape)
+    diag = np.ones(tuple(shape), dtype=np.float64)
+    for k, a in enumerate(mats):
+        a = np.asarray(a, dtype=np.float64)
+        g = np.sum(a * a, axis=0)  # (A^T A)[i, i] = sum over rows of A[:, i]^2
+        view = [1] * d
+        view[k] = shape[k]
+        diag = diag * g.reshape(view)
+    for k in range(d):
+        n = shape[k]
+        if n < 3:
+            continue
+        d2 = second_difference(n)
+        l = np.sum(d2 * d2, axis=0)
+        view = [1] * d
+        view[k] = n
+        diag = diag + lam * l.reshape(view)
+    return diag
+
+
 def apply_separable(x: np.ndarray, factors) -> np.ndarray:
     """X x_1 F_1 ... x_d F_d for square per-mode factors (Sec. 2.1, Eq. separable_transf)."""
     x = np.asarray(x, dtype=np.float64)

@@ -336,6 +336,43 @@ def test_pcg_separable_matches_cholesky_and_needs_fewer_iterations():
     assert pc.iters * 3 < plain.iters, (pc.iters, plain.iters)
 
 
+@pytest.mark.parametrize("shape,lam", [((6, 5, 7, 4), 0.3), ((5, 2, 6), 0.7), ((7, 6, 5, 1), 1e-3)])
+def test_jacobi_diagonal_is_the_diagonal_of_the_explicit_normal_matrix(shape, lam):
+    """diag(K) from the per-mode definition equals the diagonal of the explicit reshaped normal
+    matrix (Sec. 3 matrix form), regulariser included; a mode with n < 3 carries no regulariser."""
+    inst = synth.instance_bspline(shape, seed=31, lam=lam, with_truth=False)
+    mats = [f.dense() for f in inst.factors]
+    k = O.dense_normal_matrix(mats, lam, shape)
+    np.testing.assert_allclose(O.jacobi_diagonal(mats, lam, shape).ravel(), np.diag(k), rtol=1e-13, atol=1e-14)
+    rng = np.random.default_rng(3)
+    dense = [rng.standard_normal((n + 3, n)) for n in shape]
+    kd = O.dense_normal_matrix(dense, lam, shape)
+    np.testing.assert_allclose(O.jacobi_diagonal(dense, lam, shape).ravel(), np.diag(kd), rtol=1e-13)
+
+
+def test_jacobi_pcg_matches_cholesky_and_fixes_a_bad_scaling():
+    """Factors whose columns differ in scale by 10^4: K is badly scaled, point Jacobi removes the
+    scaling, and the Jacobi-preconditioned CG of Fig. 2 reaches the Cholesky solution in a fraction
+    of plain CG's iterations."""
+    rng = np.random.default_rng(27)
+    shape = (9, 8, 7)
+    sshape = tuple(int(math.ceil(1.5 * n)) for n in shape)
+    mats = [(rng.standard_normal((m, n)) / math.sqrt(m)) * 10.0 ** rng.uniform(-1, 1, n)
+            for m, n in zip(sshape, shape)]
+    lam = 1e-4
+    b = rng.standard_normal(sshape)
+    kop = lambda v: O.normal_apply(v, mats, lam)
+    rhs = O.apply_T(b, mats)
+    dia = O.jacobi_diagonal(mats, lam, shape)
+    pc = O.pcg(kop, lambda r: r / dia, rhs, rtol=1e-10)
+    plain = O.cg(kop, rhs, rtol=1e-10, max_iter=20000)
+    ref = O.direct_solve(b, mats, lam, shape)
+    assert pc.converged
+    err = np.linalg.norm(pc.x - ref) / np.linalg.norm(ref)
+    assert err < 1e-7, err
+    assert pc.iters * 2 < plain.iters, (pc.iters, plain.iters)
+
+
 def test_banded_separable_inverse_is_symmetric_positive_and_still_preconditions():
     """The 7-band truncation of each per-mode inverse (B-spline factors) is symmetric and positive
     definite (eigh), equals the full inverse inside the band, and still cuts the CG count."""
