@@ -169,11 +169,17 @@ typedef struct {
   int32_t check_every;  /* CG iterations per pass of the device loop; the stop flags are tested between passes (0: default 8, 16 for tca_solve_batched; rounded up to a multiple of 4) */
   int32_t profile;      /* 1: time every normal-operator sweep with CUDA events (info->sweep_*) */
   int32_t precond;      /* TCA_PRECOND_NONE: the CG of Fig. 2; TCA_PRECOND_SEPARABLE: the same CG with
-                           Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d) (see below) */
+                           Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d);
+                           TCA_PRECOND_JACOBI: M = diag(K) (see below) */
   double precond_shift; /* s, the regulariser weight folded into each mode of M (0: default 16) */
 } tca_solve_opts;
 
-/* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_SEPARABLE uses
+/* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_JACOBI is point
+ * Jacobi, M = diag(K), the diagonally scaled CG of the paper's Fig. 1 solver
+ * family: diag(K) = prod_k diag(G_k) + lambda sum_k diag(L_k) is formed once
+ * per plan from the per-mode diagonals (FP64, stored as 1 / diag(K) in the
+ * plan's element type, one n-shaped vector) and applied with <R, Z> in one
+ * pass per iteration.  TCA_PRECOND_SEPARABLE uses
  * a tensor inverse (Sec. 3, Eq. TensorEq): M is a separable approximation of
  * K = (x)_k G_k + lambda sum_k L_k that keeps the Gram part exactly (G_k =
  * A_k^T A_k) and spreads the regulariser over the modes with weight s, and its
@@ -186,7 +192,7 @@ typedef struct {
  * true residual, so the result meets the same tolerance.  The paper fixes no
  * preconditioner; this one is an addition.  Costs d dense mode products and
  * one inner product per iteration, and one n_k x n_k dense factor per mode. */
-enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1 };
+enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1, TCA_PRECOND_JACOBI = 2 };
 
 typedef struct {
   int32_t iters;             /* CG iterations run (all inner solves summed) */

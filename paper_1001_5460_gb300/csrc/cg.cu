@@ -256,6 +256,53 @@ __global__ void __launch_bounds__(kVecThreads) cg_precond_dot_kernel(const T* __
   }
 }
 
+// Point-Jacobi preconditioner in one pass: z = r / diag(K) (from the stored
+// reciprocal), rho1 = <r, z>; the same scalar logic as cg_precond_dot_kernel.
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(kVecThreads) cg_jacobi_kernel(const T* __restrict__ r, const T* __restrict__ dinv,
+                                                                T* __restrict__ z, int64_t n, Scalars* sc, Reduce red) {
+  __shared__ double sh[kVecThreads / 32];
+  if (cg_done(sc)) return;
+  using VT = typename V2<T>::t;
+  constexpr int VN = V2<T>::n;
+  const int64_t nv = n / VN;
+  T part = T(0);
+  double acc = 0.0;
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const VT rv = reinterpret_cast<const VT*>(r)[i];
+    const VT dv = reinterpret_cast<const VT*>(dinv)[i];
+    VT zv;
+    const T* rs = reinterpret_cast<const T*>(&rv);
+    const T* ds = reinterpret_cast<const T*>(&dv);
+    T* zs = reinterpret_cast<T*>(&zv);
+#pragma unroll
+    for (int c = 0; c < VN; ++c) {
+      zs[c] = rs[c] * ds[c];
+      part += rs[c] * zs[c];
+    }
+    reinterpret_cast<VT*>(z)[i] = zv;
+    if (++cnt == 8) {  // short runs in T, FP64 beyond
+      acc += (double)part;
+      part = T(0);
+      cnt = 0;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) {
+      z[i] = r[i] * dinv[i];
+      part += r[i] * z[i];
+    }
+  acc += (double)part;
+  double total;
+  if (dev::grid_sum_last(acc, red, &total, sh)) {
+    const bool bad = !isfinite(total) || (!(total > 0.0) && sc->rho_new > 0.0);
+    if (bad) sc->breakdown = 1;
+    sc->beta = INIT ? 0.0 : total / sc->rho;
+    sc->rho = total;
+  }
+}
+
 // ||rhs64 - kx64|| / ||rhs64||  -> sc->aux; optionally r = rhs64 - kx64 (cast).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) true_residual_kernel(const double* __restrict__ rhs,
@@ -321,10 +368,21 @@ static DirBufs<T> dir_bufs(const tca_plan_s* p) {
 }
 
 // Preconditioned CG: z = M^-1 r, then rho from <r, z> (init: a fresh start).
+// Point Jacobi does both in one pass.
 template <typename T>
 static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
-  TCA_TRY(apply_precond<T>(p, (const T*)p->r, (T*)p->z, s));
   const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks);
+  if (p->pc_kind == TCA_PRECOND_JACOBI) {
+    if (init)
+      cg_jacobi_kernel<T, true><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->pc_dinv, (T*)p->z, p->N,
+                                                             p->scal, first_reduce(p));
+    else
+      cg_jacobi_kernel<T, false><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->pc_dinv, (T*)p->z, p->N,
+                                                              p->scal, first_reduce(p));
+    TCA_LAUNCH_CHECK();
+    return TCA_OK;
+  }
+  TCA_TRY(apply_precond<T>(p, (const T*)p->r, (T*)p->z, s));
   if (init)
     cg_precond_dot_kernel<T, true><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->z, p->N, p->scal,
                                                                  first_reduce(p));
@@ -341,11 +399,17 @@ static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
 constexpr double kDefaultPrecondShift = 16.0;
 static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
   p->pc_on = false;
+  p->pc_kind = TCA_PRECOND_NONE;
   const int kind = o ? o->precond : TCA_PRECOND_NONE;
   if (kind == TCA_PRECOND_NONE) return TCA_OK;
-  if (kind != TCA_PRECOND_SEPARABLE || o->precond_shift < 0.0) return TCA_ERR_INVALID_ARG;
-  TCA_TRY(ensure_precond(p, o->precond_shift > 0.0 ? o->precond_shift : kDefaultPrecondShift));
+  if (kind == TCA_PRECOND_JACOBI) {
+    TCA_TRY(ensure_jacobi(p));
+  } else {
+    if (kind != TCA_PRECOND_SEPARABLE || o->precond_shift < 0.0) return TCA_ERR_INVALID_ARG;
+    TCA_TRY(ensure_precond(p, o->precond_shift > 0.0 ? o->precond_shift : kDefaultPrecondShift));
+  }
   p->pc_on = true;
+  p->pc_kind = kind;
   return TCA_OK;
 }
 
@@ -520,7 +584,7 @@ tca_status capture_into(cudaGraph_t g, cudaStream_t cs, F fill) {
 template <typename T>
 static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaStream_t s) {
   if (p->graph_exec && p->graph_x == x && p->graph_iters == iters && p->graph_profiled == profile &&
-      p->graph_pc == p->pc_on)
+      p->graph_pc == (p->pc_on ? p->pc_kind : 0))
     return TCA_OK;
   if (p->graph_exec) {
     cudaGraphExecDestroy(p->graph_exec);
@@ -589,7 +653,7 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
   p->graph_x = x;
   p->graph_iters = iters;
   p->graph_profiled = profile;
-  p->graph_pc = p->pc_on;
+  p->graph_pc = p->pc_on ? p->pc_kind : 0;
   p->graph_head_launches = after_head - before;     // kernels before the loop (unprofiled)
   p->graph_launches = after - after_head;           // kernels per pass
   return TCA_OK;
@@ -1107,7 +1171,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
   key.push_back((const void*)(intptr_t)max_iter);
   key.push_back((const void*)(intptr_t)(x0 ? 1 : 0));
   key.push_back(reinterpret_cast<const void*>((uintptr_t)(rtol * 1e15)));
-  key.push_back((const void*)(intptr_t)(plans[0]->pc_on ? 1 : 0));
+  key.push_back((const void*)(intptr_t)(plans[0]->pc_on ? plans[0]->pc_kind : 0));
   key.push_back(reinterpret_cast<const void*>((uintptr_t)(plans[0]->pc_shift * 1e6)));
   for (int i = 0; i < count; ++i) {
     key.push_back(plans[i]);

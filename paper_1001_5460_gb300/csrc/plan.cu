@@ -409,6 +409,101 @@ tca_status ensure_precond(tca_plan_s* p, double shift) {
   return TCA_OK;
 }
 
+// ---- Point-Jacobi preconditioner (Fig. 1 solver family): M = diag(K) ----
+//
+// diag(K)[i_1..i_d] = prod_k G_k[i_k][i_k] + sum_k lambda L_k[i_k][i_k]: the
+// diagonal of a Kronecker product is the product of the factors' diagonals,
+// and each regulariser term adds its own mode's diagonal.  The per-mode
+// diagonals come from the plan's FP64 bands; one kernel writes 1 / diag(K).
+
+__global__ void jacobi_dinv_kernel(const double* __restrict__ gd, const double* __restrict__ ld, int d, int64_t n0,
+                                   int64_t n1, int64_t n2, int64_t n3, float* __restrict__ out32,
+                                   double* __restrict__ out64, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n[4] = {n0, n1, n2, n3};
+    int64_t idx[4] = {0, 0, 0, 0};
+    int64_t rem = i;
+    for (int k = d - 1; k >= 0; --k) {
+      idx[k] = rem % n[k];
+      rem /= n[k];
+    }
+    double g = 1.0, l = 0.0;
+    int64_t off = 0;
+    for (int k = 0; k < d; ++k) {
+      g *= gd[off + idx[k]];
+      l += ld[off + idx[k]];
+      off += n[k];
+    }
+    const double v = 1.0 / (g + l);
+    if (out32) out32[i] = (float)v;
+    if (out64) out64[i] = v;
+  }
+}
+
+tca_status ensure_jacobi(tca_plan_s* p) {
+  if (p->pc_dinv && p->z) return TCA_OK;
+  int64_t tot = 0;
+  for (int k = 0; k < p->d; ++k) tot += p->n[k];
+  std::vector<double> gd((size_t)tot), ld((size_t)tot);
+  int64_t off = 0;
+  for (int k = 0; k < p->d; ++k) {
+    const Mode& md = p->mode[k];
+    const int64_t n = md.n;
+    if (md.gram.kind == OP_DENSE) {
+      std::vector<double> a((size_t)(n * n));
+      TCA_CUDA_TRY(cudaMemcpy(a.data(), md.gram.dense.a64, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < n; ++i) gd[off + i] = a[i * n + i];
+    } else {
+      const Band& gb = md.gram.band;
+      std::vector<double> g((size_t)(n * gb.W));
+      std::vector<int32_t> st((size_t)n);
+      TCA_CUDA_TRY(cudaMemcpy(g.data(), gb.w64, sizeof(double) * n * gb.W, cudaMemcpyDeviceToHost));
+      TCA_CUDA_TRY(cudaMemcpy(st.data(), gb.start, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < n; ++i) {
+        const int64_t e = i - st[i];  // tap that couples i with itself
+        gd[off + i] = (e >= 0 && e < gb.W) ? g[i * gb.W + e] : 0.0;
+      }
+    }
+    const Band& lb = md.lap;
+    std::vector<double> l((size_t)(n * lb.W));
+    TCA_CUDA_TRY(cudaMemcpy(l.data(), lb.w64, sizeof(double) * n * lb.W, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) ld[off + i] = l[i * lb.W + lb.W / 2];
+    off += n;
+  }
+  for (int64_t i = 0; i < tot; ++i) {
+    if (!(gd[i] >= 0.0)) {
+      set_error_message("Jacobi preconditioner: a Gram diagonal entry is negative or not finite");
+      return TCA_ERR_UNSUPPORTED;
+    }
+  }
+  double *dg = nullptr, *dl = nullptr;
+  tca_status st = dmalloc(&dg, tot);
+  if (st == TCA_OK) st = dmalloc(&dl, tot);
+  if (st != TCA_OK) {
+    cudaFree(dg);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(dg, gd.data(), sizeof(double) * tot, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dl, ld.data(), sizeof(double) * tot, cudaMemcpyHostToDevice);
+  const size_t es = elem_size(p);
+  if (e == cudaSuccess && !p->pc_dinv) e = cudaMalloc(&p->pc_dinv, es * (size_t)p->N);
+  if (e == cudaSuccess && !p->z) e = cudaMalloc(&p->z, es * (size_t)p->N);
+  if (e == cudaSuccess) {
+    jacobi_dinv_kernel<<<std::min(nblk(p->N), 4096), 256>>>(dg, dl, p->d, p->n[0], p->n[1], p->n[2], p->n[3],
+                                            es == 4 ? (float*)p->pc_dinv : nullptr,
+                                            es == 8 ? (double*)p->pc_dinv : nullptr, p->N);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    st = TCA_ERR_CUDA;
+  }
+  cudaFree(dg);
+  cudaFree(dl);
+  return st;
+}
+
 // Largest intermediate of a chain of mode products applied in `order`.
 static int64_t chain_peak(const int64_t* start, const int64_t* end, const int* order, int d) {
   int64_t cur[kMaxModes];
@@ -427,6 +522,7 @@ static void destroy_plan(tca_plan_s* p) {
   if (!p) return;
   for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
   cudaFree(p->z);
+  cudaFree(p->pc_dinv);
   for (int k = 0; k < kMaxModes; ++k) {
     free_op(p->mode[k].fwd);
     free_op(p->mode[k].bwd);

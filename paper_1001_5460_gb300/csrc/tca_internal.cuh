@@ -160,6 +160,8 @@ struct tca_plan_s {
   uint64_t pc_generation = 0;  // bumped whenever the factors are rebuilt (graph cache keys)
   void* z = nullptr;
   bool pc_on = false;       // the iteration being built or run is preconditioned
+  int pc_kind = 0;          // TCA_PRECOND_SEPARABLE or TCA_PRECOND_JACOBI while pc_on
+  void* pc_dinv = nullptr;  // Jacobi: 1 / diag(K), n-shaped, element type of the plan (built on first use)
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
   cudaStream_t copy_stream = nullptr;  // host-pointer solves: b uploaded under A^T b, x copied back
@@ -176,7 +178,7 @@ struct tca_plan_s {
   const void* graph_x = nullptr;
   int graph_iters = 0;
   bool graph_profiled = false;
-  bool graph_pc = false;
+  int graph_pc = 0;  // preconditioner kind the cached graph was built with (0: none)
   uint64_t graph_launches = 0;       // kernels per pass of the iteration graph
   uint64_t graph_head_launches = 0;  // kernels before its loop (unprofiled graphs)
   cudaEvent_t sweep_ev[2 * tca::kMaxProfiledIters] = {};  // start/end per iteration of a profiled graph
@@ -239,6 +241,8 @@ struct RegDot {
 // Separable-inverse preconditioner for shift s: build (or keep) the per-mode
 // factors and the z buffer; apply_precond writes z = M^-1 r (element type T).
 tca_status ensure_precond(tca_plan_s* p, double shift);
+// Point-Jacobi preconditioner: build (once) 1 / diag(K) and the z buffer.
+tca_status ensure_jacobi(tca_plan_s* p);
 template <typename T>
 tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s);
 // Largest 3xTF32 / TF32 split the tensor-core dense kernel takes for an

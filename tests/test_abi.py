@@ -64,8 +64,9 @@ def test_binding_structs_match_the_header(tca):
 def test_precond_names(tca):
     assert tca._precond_code(None) == tca.PRECOND_NONE
     assert tca._precond_code("separable") == tca.PRECOND_SEPARABLE
+    assert tca._precond_code("jacobi") == tca.PRECOND_JACOBI
     with pytest.raises(ValueError):
-        tca._precond_code("jacobi")
+        tca._precond_code("multigrid-typo")
 
 
 def test_status_strings_and_version(tca):
