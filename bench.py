@@ -15,8 +15,17 @@ on the machine's host cores instead (bounded sample, extrapolated; see below).
 device).  The roofline's sweep time comes from a profiled solve run right after
 each timed one: the same solve with every CG sweep bracketed by CUDA events on
 the solve's stream (one graph pass per launch, the host reading the events).
-``variants`` times the same solve with the separable tensor-inverse
-preconditioner at shifts 16 (the default) and 32, after the plain timing.
+``variants`` (after the plain timing, same workload unless stated):
+  separable_pcg_s16 / _s32  the separable tensor-inverse preconditioner;
+  jacobi_pcg                point Jacobi, M = diag(K);
+  bf16_ir                   the bfloat16 mixed-precision form (tensor-core sweep,
+                            double-float refinement), autotuned, with its sweep's
+                            roofline and, in the oracle leg, its error against the
+                            FP64 oracle on the 40x40x40x8 instance of the generator;
+  batched                   64 uneven instances in one graph launch (plain,
+                            separable and Jacobi), against one solve after another;
+  learned                   the network initial guess trained on solver pairs,
+                            evaluated on held-out 160x160x160x8 instances.
 """
 from __future__ import annotations
 
@@ -43,6 +52,7 @@ RTOL = 1e-6
 # to be re-measured (or set to None) whenever that kernel changes.
 K2_TRAFFIC_BYTES = 511_530_000
 SUBVOL = (40, 40, 40, 8)  # iteration-count probe for the oracle arm (same generator)
+BF16_INNER = 3e-2  # inner relative tolerance of the bfloat16 refinement variant
 WORKLOAD = ("bspline4d: unknowns 160x160x160x8 (32.8M) FP32, cubic B-spline factors on 240x240x240x12 "
             "jittered samples, lambda 1e-3, noise 0.01, CG to true rel. residual 1e-6")
 
@@ -54,6 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess variant (training)")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
     ap.add_argument("--shape", default=None, help="sweep cases: tensor shape n1,n2,n3,n4 (profiling runs)")
     ap.add_argument("--train-instances", type=int, default=100, help="learned case: training instances (64^3 x 4)")
@@ -161,7 +172,7 @@ def run_case(args, local):
 BATCH = 64
 
 
-def run_batched(args, device):
+def run_batched(args, device, emit=True):
     """64 uneven instances (3D/4D, n_k ~ U[24,96], n_4 in {1,4,8}, half dense, half B-spline,
     lambda log-uniform in [1e-4,1e-2]) solved to 1e-6 in one graph launch, against the same
     instances solved one after another with tca_solve."""
@@ -225,7 +236,17 @@ def run_batched(args, device):
     # x += alpha p: x, p in, x out), 40 B per unknown, times its iterations.
     inst_gbs = sorted(40.0 * float(np.prod(insts[k].shape)) * seq_infos[k]["iters"] / seq_infos[k]["seconds"] / 1e9
                       for k in range(BATCH))
-    print(json.dumps({
+    # The same batch with the point-Jacobi preconditioner.
+    tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000, precond="jacobi")
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        st_j, j_infos = tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000, precond="jacobi")
+    e1.record()
+    torch.cuda.synchronize()
+    j_batched_ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    j_iters = [i["iters"] for i in j_infos]
+    out = {
         "case": "batched", "instances": BATCH, "unknowns": unknowns, "status": int(st),
         "batched_ms": round(batched_ms, 3), "sequential_ms": round(seq_ms, 3),
         "speedup": round(seq_ms / batched_ms, 3), "first_call_s": round(first_s, 3),
@@ -238,18 +259,30 @@ def run_batched(args, device):
                           "iters_median": int(statistics.median(pc_iters)), "iters_max": max(pc_iters),
                           "iters_total": int(sum(pc_iters)),
                           "rel_res_true_max": max(i["rel_res_true"] for i in pc_infos)},
+        "jacobi_pcg": {"status": int(st_j), "batched_ms": round(j_batched_ms, 3),
+                       "iters_median": int(statistics.median(j_iters)), "iters_max": max(j_iters),
+                       "iters_total": int(sum(j_iters)),
+                       "rel_res_true_max": max(i["rel_res_true"] for i in j_infos)},
         "per_instance_gbs_alone": {"min": round(inst_gbs[0], 1), "median": round(statistics.median(inst_gbs), 1),
                                    "max": round(inst_gbs[-1], 1), "bytes_per_unknown_iter": 40},
         "slowest_alone": [{"shape": list(insts[k].shape), "kind": insts[k].factors[0].kind,
                            "iters": seq_infos[k]["iters"], "ms": round(1e3 * seq_infos[k]["seconds"], 2)}
                           for k in slowest],
-    }), flush=True)
+    }
+    # Whole-batch rate in the same 40 B per unknown and iteration convention.
+    out["batched_gbs"] = round(40.0 * sum(float(np.prod(i.shape)) * f["iters"] for i, f in zip(insts, infos))
+                               / batched_ms / 1e6, 1)
+    for pl in plans:
+        pl.close()
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 TRAIN_SHAPE = (64, 64, 64, 4)
 
 
-def run_learned(args, device):
+def run_learned(args, device, emit=True):
     """Learned initial guess: train the network on (A^T b, x) pairs that the plain solver produces on
     64x64x64x4 B-spline instances, then solve held-out 160x160x160x8 instances from x0 = s Net(A^T b / s)
     and compare with plain CG from zero at the same true relative residual (1e-6)."""
@@ -344,12 +377,16 @@ def run_learned(args, device):
         res["net_forward_ms"] = round(e0.elapsed_time(e1) / args.steps, 3)
         evals.append({"seed": seed, **res})
         plan.close()
-    print(json.dumps({
+    out = {
         "case": "learned", "train_pairs": npairs, "train_shape": list(TRAIN_SHAPE), "gen_s": round(t_gen, 2),
         "gen_iters_mean": round(gen_iters / max(npairs, 1), 1), "train_steps": steps,
         "train_s": round(t_train, 2), "train_ms_per_step": round(1e3 * t_train / max(steps, 1), 3),
         "loss": losses[:3] + losses[-3:], "eval_shape": list(SHAPE), "eval": evals,
-    }), flush=True)
+    }
+    net.close()
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def dist_setup(n_gpus):
@@ -460,6 +497,46 @@ def make_problem(shape, seed, device):
     torch.cuda.synchronize()
     del xt
     return inst, plan, b
+
+
+def timed_solve(plan, b, x, steps, stream, **kw):
+    """Mean device time (CUDA events on the solve's stream) of `steps` solves after one warm-up."""
+    import torch
+
+    plan.solve(b, x, rtol=RTOL, **kw)
+    torch.cuda.synchronize()
+    times, info = [], None
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = plan.solve(b, x, rtol=RTOL, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times), info
+
+
+def bf16_subvolume_error():
+    """The mixed-precision form's error against the FP64 oracle on the 40x40x40x8 instance of the
+    workload's generator (60^3 x 12 samples): relative L2 distance between the GPU's bfloat16 /
+    double-float solution and the oracle's CG solution (rtol 1e-12)."""
+    import torch
+
+    from oracle import tca_oracle as O
+    from paper_1001_5460_gb300 import synth, tca
+
+    inst = synth.instance_bspline(SUBVOL, seed=SEED, lam=LAM, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="bf16_ir")
+    x = torch.zeros(SUBVOL, dtype=torch.float32, device="cuda")
+    st, info = plan.solve(torch.from_numpy(b).cuda(), x, rtol=RTOL, inner_rtol=BF16_INNER)
+    got = x.cpu().numpy().astype(np.float64)
+    ref = O.solve(b.astype(np.float64), mats, inst.lam, rtol=1e-12).x
+    plan.close()
+    return {"shape": list(SUBVOL), "status": int(st),
+            "rel_l2_error": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "oracle_rel_residual": O.rel_residual(got, b.astype(np.float64), mats, inst.lam)}
 
 
 def time_sweeps(plan, inst, device, reps=20):
@@ -631,10 +708,57 @@ def run_tca(args, rank, world, local):
             "what": f"CG preconditioned by the separable tensor inverse (x)_k (G_k + {int(shift)} lambda L_k)^-1 "
                     "(dense TF32 mode products on the tensor cores), same tolerance on the FP64 true residual"}
 
+    # The same solve with the point-Jacobi preconditioner M = diag(K).
+    j_ms, j_info = timed_solve(plan, b, x, args.steps, s, precond="jacobi")
+    variants["jacobi_pcg"] = {
+        "ms": round(max_over_ranks(j_ms, world), 3), "cg_iters": j_info["iters"], "restarts": j_info["refinements"],
+        "rel_res_true": j_info["rel_res_true"],
+        "what": "CG preconditioned by point Jacobi, M = diag(K) = prod_k diag(G_k) + lambda sum_k diag(L_k)"}
+
+    # Mixed precision in bfloat16: the same problem, TCA_BF16_IR (bfloat16 inner CG on the
+    # tensor-core sweep, double-float refinement), tuned by tca_autotune.
+    peaks, peak_src = measured_peaks()
+    try:
+        bplan = tca.plan_from_instance(inst, precision="bf16_ir")
+        t0 = time.perf_counter()
+        bplan.autotune()
+        tune_s = time.perf_counter() - t0
+        bf_ms, bf_info = timed_solve(bplan, b, x, args.steps, s, inner_rtol=BF16_INNER)
+        _, bf_prof = bplan.solve(b, x, rtol=RTOL, inner_rtol=BF16_INNER, profile=True)
+        bf_sweep_ms = bf_prof["sweep_ms"] / max(bf_prof["sweep_launches"], 1)
+        bf_gbs = 4 * N * 2 / bf_sweep_ms / 1e6  # CG sweep: r, p_old in; p, q out (bfloat16)
+        variants["bf16_ir"] = {
+            "ms": round(max_over_ranks(bf_ms, world), 3), "inner_iters": bf_info["iters"],
+            "refinements": bf_info["refinements"], "rel_res_true": bf_info["rel_res_true"],
+            "inner_rtol": BF16_INNER, "autotune_s": round(tune_s, 3),
+            "autotuned": {"chunks": tca._lib.tca_autotuned_chunks(bplan.handle), "rows_per_thread": bplan.autotuned_rows()},
+            "sweep": {"kernel": "bfloat16 tensor-core CG sweep (tcgen05 kind::f16, FP32 accumulation)",
+                      "avg_launch_ms": round(bf_sweep_ms, 5), "launches": bf_prof["sweep_launches"],
+                      "algorithmic_bytes": 4 * N * 2, "achieved_gbs": round(bf_gbs, 1),
+                      "frac_of_measured_hbm": round(bf_gbs / peaks["hbm_gbs"], 4)},
+            "what": "iterative refinement: outer FP64-accurate (double-float) residual, inner CG with r, p, q in "
+                    "bfloat16 and the modes-3/4 contraction on the tensor cores (BF16 x BF16 -> FP32)"}
+        bplan.close()
+    except Exception as exc:  # reported, not fatal: the plain solve is the bench value
+        variants["bf16_ir"] = {"error": repr(exc)[:300]}
+
+    sub = argparse.Namespace(**vars(args))
+    sub.steps = max(1, min(args.steps, 3))
+    sub.warmup = 1
+    if not args.small:
+        try:
+            variants["batched"] = run_batched(sub, device, emit=False)
+        except Exception as exc:
+            variants["batched"] = {"error": repr(exc)[:300]}
+        if not args.no_learned:
+            try:
+                variants["learned"] = run_learned(sub, device, emit=False)
+            except Exception as exc:
+                variants["learned"] = {"error": repr(exc)[:300]}
+
     sweeps = time_sweeps(plan, inst, device)
     if rank != 0:
         return
-    peaks, peak_src = measured_peaks()
     k2_ms = sweep_ms / max(sweep_n, 1)
     k2_bytes = 4 * N * 4  # CG sweep: reads r and p_old, writes p_new and q (FP32)
     achieved = k2_bytes / k2_ms / 1e6
@@ -662,6 +786,12 @@ def run_tca(args, rank, world, local):
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline and not args.small:
+        # Oracle leg (CPU): the FP64 reference for the bfloat16 variant's error, then the timed sample.
+        if "error" not in variants.get("bf16_ir", {"error": 1}):
+            try:
+                line["variants"]["bf16_ir"]["err_vs_fp64_oracle"] = bf16_subvolume_error()
+            except Exception as exc:
+                line["variants"]["bf16_ir"]["err_vs_fp64_oracle"] = {"error": repr(exc)[:300]}
         r = oracle_sample(inst, b.cpu().numpy().astype(np.float64), last["iters"], os.cpu_count())
         line["cpu_baseline"] = {
             "value": round(r["value_ms"], 1), "unit": "ms", "cores": r["cores"], "kind": "oracle",
