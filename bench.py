@@ -208,6 +208,18 @@ def run_batched(args, device, emit=True):
     torch.cuda.synchronize()
     batched_ms = e0.elapsed_time(e1) / max(args.steps, 1)
     launches = (tca.kernel_launches() - launches0) // max(args.steps, 1)
+    # The autotuner's SM share for this batch (each candidate solved twice), then the tuned batch.
+    t0 = time.perf_counter()
+    share = tca.autotune_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
+    tune_s = time.perf_counter() - t0
+    tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        st_t, t_infos = tca.solve_batched(plans, bs, xs, rtol=RTOL, max_iter=20000)
+    e1.record()
+    torch.cuda.synchronize()
+    tuned_ms = e0.elapsed_time(e1) / max(args.steps, 1)
     # The same instances, one tca_solve each (each plan's own cached iteration graph).
     for plan, b, x in zip(plans, bs, xs):
         plan.solve(b, x, rtol=RTOL, max_iter=20000)
@@ -249,6 +261,9 @@ def run_batched(args, device, emit=True):
     out = {
         "case": "batched", "instances": BATCH, "unknowns": unknowns, "status": int(st),
         "batched_ms": round(batched_ms, 3), "sequential_ms": round(seq_ms, 3),
+        "autotuned": {"sm_share": f"1/{share}", "batched_ms": round(tuned_ms, 3), "status": int(st_t),
+                      "tune_s": round(tune_s, 2),
+                      "rel_res_true_max": max(i["rel_res_true"] for i in t_infos)},
         "speedup": round(seq_ms / batched_ms, 3), "first_call_s": round(first_s, 3),
         "iters_min": min(iters), "iters_median": int(statistics.median(iters)), "iters_max": max(iters),
         "iters_total": int(sum(iters)), "restarts": int(sum(i["refinements"] for i in infos)),

@@ -260,6 +260,21 @@ TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_
 TCA_API tca_status tca_solve_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
                                      const tca_solve_opts* opts, tca_solve_info* info, cudaStream_t stream);
 
+/* Autotune a batch for tca_solve_batched: solve it (opts as tca_solve_batched
+ * takes them) once per candidate SM share - every instance's kernels sized
+ * for 1/1, 1/2, 1/3, 1/4, 1/6 or 1/8 of the GPU's SMs, which sets each
+ * instance's tile counts (fused-sweep chunks, vector-kernel grids, persistent
+ * tensor-core and TMA-row CTAs) - time each graph launch on the device and
+ * keep the fastest share for this batch signature (the same plans, buffers
+ * and options), which later tca_solve_batched calls use; batches without a
+ * tuned share use a quarter.  Solves the batch 2 x 6 times (x is
+ * overwritten).  share_out (may be NULL) receives the share's denominator.
+ * The paper applies its method to one system at a time; this is the
+ * one-launch batch's tile choice made by measurement.  Synchronises the
+ * stream. */
+TCA_API tca_status tca_autotune_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
+                                        const tca_solve_opts* opts, int* share_out, cudaStream_t stream);
+
 /* Autotune the normal-operator sweep that the plan's CG iterations run (its
  * CG form: new direction, K p and <p, K p>): time it for a few tile extents
  * along mode 1 around the cost model's choice and, for TCA_BF16_IR plans,

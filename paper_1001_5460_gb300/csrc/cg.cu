@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -1150,22 +1151,16 @@ tca_status build_batch(int count, tca_plan_s** plans, const float* const* b, flo
 
 }  // namespace
 
-static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float* const* b, float* const* x,
-                                     const tca_solve_opts* o, tca_solve_info* info, cudaStream_t s) {
-  const auto t0 = std::chrono::steady_clock::now();
-  const double rtol = o ? o->rtol : 1e-6;
-  const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
-  const bool x0 = o && o->x0_given;
-  int every = (o && o->check_every > 0) ? o->check_every : 16;
-  every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
-  if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
-  for (int i = 0; i < count; ++i) {
-    TCA_TRY(ensure_solver_buffers<float>(plans[i]));
-    TCA_TRY(ensure_ws64_public(plans[i]));
-    TCA_TRY(setup_precond(plans[i], o));
-  }
-  std::lock_guard<std::mutex> lock(g_batch_mutex);
-  TCA_TRY(ensure_pool());
+// SM share of the batched graph: each instance's kernels are sized for
+// num_sms / share SMs.  tca_autotune_batched times candidate shares on a batch
+// and records the fastest per batch signature (plans, buffers, options);
+// batches it has not seen use a quarter.
+constexpr int kDefaultBatchShare = 4;
+std::map<std::vector<const void*>, int> g_batch_share;  // guarded by g_batch_mutex
+int g_batch_share_forced = 0;                           // autotuner's candidate (0: none)
+
+static std::vector<const void*> batch_signature(int count, tca_plan_s** plans, const float* const* b,
+                                                float* const* x, double rtol, int max_iter, bool x0, int every) {
   std::vector<const void*> key;
   key.push_back((const void*)(intptr_t)every);
   key.push_back((const void*)(intptr_t)max_iter);
@@ -1180,6 +1175,37 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
     key.push_back(b[i]);
     key.push_back(x[i]);
   }
+  return key;
+}
+
+static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float* const* b, float* const* x,
+                                     const tca_solve_opts* o, tca_solve_info* info, cudaStream_t s,
+                                     int* share_used = nullptr) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const double rtol = o ? o->rtol : 1e-6;
+  const int max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
+  const bool x0 = o && o->x0_given;
+  int every = (o && o->check_every > 0) ? o->check_every : 16;
+  every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
+  if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    TCA_TRY(ensure_solver_buffers<float>(plans[i]));
+    TCA_TRY(ensure_ws64_public(plans[i]));
+    TCA_TRY(setup_precond(plans[i], o));
+  }
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  TCA_TRY(ensure_pool());
+  const std::vector<const void*> sig = batch_signature(count, plans, b, x, rtol, max_iter, x0, every);
+  int share = kDefaultBatchShare;
+  if (g_batch_share_forced > 0) {
+    share = g_batch_share_forced;
+  } else {
+    auto it = g_batch_share.find(sig);
+    if (it != g_batch_share.end()) share = it->second;
+  }
+  if (share_used) *share_used = share;
+  std::vector<const void*> key = sig;
+  key.push_back((const void*)(intptr_t)share);
   if (key != g_batch.key || !g_batch.exec) {
     if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
     g_batch.exec = nullptr;
@@ -1194,7 +1220,7 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
     // iteration: 0.98 s with a half, 0.90 s with a third, 0.86 s with a
     // quarter, 0.84 s with a sixth, while the slowest instance alone in a
     // batch goes from 0.16 to 0.33 s - a quarter keeps the critical path short.
-    const int budget = std::max(8, plans[0]->num_sms / 4);
+    const int budget = std::max(8, plans[0]->num_sms / share);
     std::vector<int> saved_sms(count), saved_chunks(count);
     auto set_cap = [](tca_plan_s* p, int cap) {
       for (int k = 0; k < p->d; ++k) {
@@ -1269,6 +1295,63 @@ extern "C" tca_status tca_solve_batched(int count, tca_plan_t* plans, const void
                                            reinterpret_cast<float* const*>(x), opts, info, stream);
   const tca_status tw = check_wait_timeout(stream);
   return tw != TCA_OK ? tw : st;
+}
+
+extern "C" tca_status tca_autotune_batched(int count, tca_plan_t* plans, const void* const* b, void* const* x,
+                                           const tca_solve_opts* opts, int* share_out, cudaStream_t stream) {
+  if (count <= 0 || !plans || !b || !x) return TCA_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !b[i] || !x[i]) return TCA_ERR_INVALID_ARG;
+    if (plans[i]->prec != TCA_F32) return TCA_ERR_UNSUPPORTED;
+    if (!is_device_ptr(b[i]) || !is_device_ptr(x[i]) || (uintptr_t)x[i] % 16 != 0) return TCA_ERR_UNSUPPORTED;
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == plans[i]) return TCA_ERR_INVALID_ARG;
+  }
+  const float* const* bb = reinterpret_cast<const float* const*>(b);
+  float* const* xx = reinterpret_cast<float* const*>(x);
+  const int num_sms = plans[0]->num_sms;
+  cudaEvent_t e0, e1;
+  TCA_CUDA_TRY(cudaEventCreate(&e0));
+  TCA_CUDA_TRY(cudaEventCreate(&e1));
+  int best = kDefaultBatchShare;
+  float best_ms = 1e30f;
+  tca_status st = TCA_OK;
+  for (int share : {1, 2, 3, 4, 6, 8}) {
+    if (num_sms / share < 8) continue;
+    {
+      std::lock_guard<std::mutex> lock(g_batch_mutex);
+      g_batch_share_forced = share;
+    }
+    // First call captures the graph for this share, the second is timed.
+    st = solve_batched_impl(count, plans, bb, xx, opts, nullptr, stream);
+    if (st == TCA_OK || st == TCA_ERR_NOT_CONVERGED) {
+      cudaEventRecord(e0, stream);
+      st = solve_batched_impl(count, plans, bb, xx, opts, nullptr, stream);
+      cudaEventRecord(e1, stream);
+      cudaEventSynchronize(e1);
+    }
+    if (st != TCA_OK && st != TCA_ERR_NOT_CONVERGED) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = share;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  g_batch_share_forced = 0;
+  if (st != TCA_OK && st != TCA_ERR_NOT_CONVERGED) return st;
+  // Record the choice under the signature the solves will look up.
+  double rtol = opts ? opts->rtol : 1e-6;
+  const int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 10000;
+  int every = (opts && opts->check_every > 0) ? opts->check_every : 16;
+  every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
+  g_batch_share[batch_signature(count, plans, bb, xx, rtol, max_iter, opts && opts->x0_given, every)] = best;
+  if (share_out) *share_out = best;
+  const tca_status tw = check_wait_timeout(stream);
+  return tw;
 }
 
 extern "C" tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,

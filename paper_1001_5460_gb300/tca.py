@@ -94,6 +94,9 @@ _lib.tca_solve.restype = ctypes.c_int
 _lib.tca_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                    ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info), _vp]
 _lib.tca_solve_batched.restype = ctypes.c_int
+_lib.tca_autotune_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                      ctypes.POINTER(tca_solve_opts), ctypes.POINTER(ctypes.c_int), _vp]
+_lib.tca_autotune_batched.restype = ctypes.c_int
 _lib.tca_autotune.argtypes = [_vp, _vp]
 _lib.tca_autotune.restype = ctypes.c_int
 _lib.tca_autotuned_chunks.argtypes = [_vp]
@@ -239,7 +242,7 @@ def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
 
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",
@@ -373,6 +376,24 @@ def solve_batched(plans, bs, xs, rtol: float = 1e-6, max_iter: int = 10000, x0_g
     if raise_on_error:
         _check(st, "tca_solve_batched", ok=(OK, ERR_NOT_CONVERGED))
     return st, [_info_dict(i) for i in infos]
+
+
+def autotune_batched(plans, bs, xs, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
+                     check_every: int = 16, stream=None, precond=None, precond_shift: float = 0.0) -> int:
+    """Time the batch at each SM share and keep the fastest for these plans, buffers and options
+    (later solve_batched calls with the same arguments use it); returns the share's denominator."""
+    count = len(plans)
+    if not (len(bs) == count == len(xs)) or count == 0:
+        raise ValueError("plans, bs and xs must be non-empty and of equal length")
+    hp = (_vp * count)(*[p.handle for p in plans])
+    bp = (_vp * count)(*[_ptr(b) for b in bs])
+    xp = (_vp * count)(*[_ptr(x) for x in xs])
+    opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, 0.0, 0, int(check_every), 0,
+                          _precond_code(precond), float(precond_shift))
+    share = ctypes.c_int(0)
+    _check(_lib.tca_autotune_batched(count, hp, bp, xp, ctypes.byref(opts), ctypes.byref(share), _stream(stream)),
+           "tca_autotune_batched")
+    return int(share.value)
 
 
 def plan_from_instance(inst, precision="f32", reg_mask=None, stream=None) -> Plan:

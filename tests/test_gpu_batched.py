@@ -120,3 +120,26 @@ def test_autotune_keeps_parity(shape):
     plan.apply_normal(to_dev(x, np.float32), y)
     ref = O.normal_apply(x.astype(np.float32).astype(np.float64), mats, inst.lam)
     assert rel_l2(y.cpu().numpy(), ref) < TOL_F32
+
+
+def test_autotune_batched_picks_a_share_and_keeps_the_results():
+    """tca_autotune_batched times the batch at every SM share and records the fastest for this
+    batch; the tuned solve still meets the tolerance by the oracle, and a later call with the same
+    arguments replays the same graph (identical iterates)."""
+    tca = lib()
+    insts, bs = _batch(6, 520)
+    plans = [tca.plan_from_instance(inst, precision="f32") for inst in insts]
+    bd = [to_dev(b, np.float32) for b in bs]
+    xs = [empty_dev(inst.shape, np.float32) for inst in insts]
+    share = tca.autotune_batched(plans, bd, xs, rtol=1e-6, max_iter=20000)
+    assert share in (1, 2, 3, 4, 6, 8)
+    st, infos = tca.solve_batched(plans, bd, xs, rtol=1e-6, max_iter=20000)
+    assert st == tca.OK
+    first = [x.clone() for x in xs]
+    for inst, b, x in zip(insts, bs, xs):
+        mats = [f.dense() for f in inst.factors]
+        assert O.rel_residual(x.cpu().numpy(), b.astype(np.float64), mats, inst.lam) <= 1.5e-6
+    st2, infos2 = tca.solve_batched(plans, bd, xs, rtol=1e-6, max_iter=20000)
+    for a, b_, i1, i2 in zip(first, xs, infos, infos2):
+        assert i1["iters"] == i2["iters"]
+        assert bool((a == b_).all())
