@@ -318,6 +318,20 @@ TCA_API int tca_autotuned_rows(tca_plan_t plan);
 TCA_API tca_status tca_rel_residual_noalloc(const double* rhs, const double* kx, int64_t n, double* out,
                                             cudaStream_t stream);
 
+/* Vector steps of Fig. 2's iteration (Sec. 4.1) on caller-owned float device
+ * vectors of length n, for callers that drive CG themselves - the
+ * slab-partitioned solve, where each rank owns a contiguous run of mode-1
+ * planes, applies K to its slab with its own plan (factor 1 restricted to the
+ * slab's columns) and combines inner products across ranks.
+ *   tca_vec_axpby: y = a x + b y (C += alpha P, R -= alpha Q, P = R + beta P);
+ *   tca_vec_dot:   *out = sum_i a[i] b[i], FP32 products summed in FP64; out is
+ *                  one device double, zeroed and then accumulated on the stream
+ *                  (block sums combined by FP64 atomics: the last bits of the
+ *                  sum may vary from run to run).
+ * Asynchronous on the stream; host pointers give TCA_ERR_UNSUPPORTED. */
+TCA_API tca_status tca_vec_axpby(float* y, const float* x, double a, double b, int64_t n, cudaStream_t stream);
+TCA_API tca_status tca_vec_dot(const float* a, const float* b, int64_t n, double* out, cudaStream_t stream);
+
 /* Synchronise the stream, then report whether any bounded device wait (TMA
  * and tensor-core pipelines) gave up since the last check: TCA_ERR_TIMEOUT,
  * clearing the flag, or TCA_OK.  The flag is per process, not per plan. */

@@ -128,6 +128,10 @@ _lib.tca_net_destroy.argtypes = [_vp]
 _lib.tca_net_destroy.restype = None
 _lib.tca_rel_residual_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
 _lib.tca_rel_residual_noalloc.restype = ctypes.c_int
+_lib.tca_vec_axpby.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int64, _vp]
+_lib.tca_vec_axpby.restype = ctypes.c_int
+_lib.tca_vec_dot.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+_lib.tca_vec_dot.restype = ctypes.c_int
 _lib.tca_destroy.argtypes = [_vp]
 _lib.tca_destroy.restype = None
 _lib.tca_status_string.argtypes = [ctypes.c_int]
@@ -240,13 +244,30 @@ def rel_residual_noalloc(rhs, kx, out, stream=None) -> int:
                   "tca_rel_residual_noalloc")
 
 
+def vec_axpby(y, x, a: float, b: float, stream=None):
+    """y = a x + b y on float32 CUDA tensors of equal length (one library kernel)."""
+    if y.numel() != x.numel():
+        raise ValueError("x and y differ in length")
+    _check(_lib.tca_vec_axpby(_ptr(y), _ptr(x), float(a), float(b), int(y.numel()), _stream(stream)), "tca_vec_axpby")
+    return y
+
+
+def vec_dot(a, b, out, stream=None):
+    """out[0] = <a, b> (FP64 sum of FP32 products) for float32 CUDA tensors; out: a float64 CUDA tensor."""
+    if a.numel() != b.numel() or out.numel() < 1:
+        raise ValueError("a and b differ in length, or out is empty")
+    _check(_lib.tca_vec_dot(_ptr(a), _ptr(b), int(a.numel()), _ptr(out), _stream(stream)), "tca_vec_dot")
+    return out
+
+
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
             "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",
-            "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version"]
+            "tca_status_string", "tca_last_error_string", "tca_kernel_launches", "tca_version", "tca_vec_axpby",
+            "tca_vec_dot"]
 
 
 class Factor:
