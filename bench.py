@@ -50,7 +50,7 @@ RTOL = 1e-6
 # DRAM bytes (read + written) of one launch of the CG sweep kernel at this workload,
 # counted by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the current kernel;
 # to be re-measured (or set to None) whenever that kernel changes.
-K2_TRAFFIC_BYTES = 511_530_000
+K2_TRAFFIC_BYTES = 510_850_000
 SUBVOL = (40, 40, 40, 8)  # iteration-count probe for the oracle arm (same generator)
 BF16_INNER = 3e-2  # inner relative tolerance of the bfloat16 refinement variant
 WORKLOAD = ("bspline4d: unknowns 160x160x160x8 (32.8M) FP32, cubic B-spline factors on 240x240x240x12 "
@@ -65,12 +65,14 @@ def parse():
     ap.add_argument("--impl", default="tca", choices=["tca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess variant (training)")
+    ap.add_argument("--no-variants", action="store_true", help="plain solve only (launch lists under a profiler)")
     ap.add_argument("--small", action="store_true", help="quick 64x64x64x8 run (not a bench line)")
     ap.add_argument("--shape", default=None, help="sweep cases: tensor shape n1,n2,n3,n4 (profiling runs)")
     ap.add_argument("--train-instances", type=int, default=100, help="learned case: training instances (64^3 x 4)")
     ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
     ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
-    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "dense", "batched", "learned", "netfwd"],
+    ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "bf16sweep", "dense", "batched", "learned",
+                             "netfwd"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -139,6 +141,16 @@ def run_case(args, local):
     plan = tca.plan_from_instance(inst, precision="f32")
     x = torch.randn(shape, dtype=torch.float32, device=device)
     N = x.numel()
+    if args.case == "bf16sweep":
+        # A few iterations of the bfloat16 inner CG: the tensor-core CG sweep in its solve context.
+        bplan = tca.plan_from_instance(inst, precision="bf16_ir")
+        b = torch.randn(inst.sample_shape, dtype=torch.float32, device=device)
+        for _ in range(args.warmup + args.steps):
+            st, info = bplan.solve(b, x, rtol=1e-30, inner_rtol=1e-30, max_iter=4, raise_on_error=False,
+                                   profile=True)
+        ms = info["sweep_ms"] / max(info["sweep_launches"], 1)
+        print(json.dumps({"case": args.case, "ms": round(ms, 5), "gbs": round(4 * N * 2 / ms / 1e6, 1)}), flush=True)
+        return
     if args.case == "cgsweep":
         # A few CG iterations on random data: the CG-mode fused sweep in its solve context.
         b = torch.randn(inst.sample_shape, dtype=torch.float32, device=device)
@@ -647,6 +659,59 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_variants(args, plan, inst, b, x, s, N, world, device, peaks, variants):
+    """The variants of the bench line (see the module docstring), after the plain timing."""
+    from paper_1001_5460_gb300 import tca
+
+    # The same solve with the point-Jacobi preconditioner M = diag(K).
+    j_ms, j_info = timed_solve(plan, b, x, args.steps, s, precond="jacobi")
+    variants["jacobi_pcg"] = {
+        "ms": round(max_over_ranks(j_ms, world), 3), "cg_iters": j_info["iters"], "restarts": j_info["refinements"],
+        "rel_res_true": j_info["rel_res_true"],
+        "what": "CG preconditioned by point Jacobi, M = diag(K) = prod_k diag(G_k) + lambda sum_k diag(L_k)"}
+
+    # Mixed precision in bfloat16: the same problem, TCA_BF16_IR (bfloat16 inner CG on the
+    # tensor-core sweep, double-float refinement), tuned by tca_autotune.
+    try:
+        bplan = tca.plan_from_instance(inst, precision="bf16_ir")
+        t0 = time.perf_counter()
+        bplan.autotune()
+        tune_s = time.perf_counter() - t0
+        bf_ms, bf_info = timed_solve(bplan, b, x, args.steps, s, inner_rtol=BF16_INNER)
+        _, bf_prof = bplan.solve(b, x, rtol=RTOL, inner_rtol=BF16_INNER, profile=True)
+        bf_sweep_ms = bf_prof["sweep_ms"] / max(bf_prof["sweep_launches"], 1)
+        bf_gbs = 4 * N * 2 / bf_sweep_ms / 1e6  # CG sweep: r, p_old in; p, q out (bfloat16)
+        variants["bf16_ir"] = {
+            "ms": round(max_over_ranks(bf_ms, world), 3), "inner_iters": bf_info["iters"],
+            "refinements": bf_info["refinements"], "rel_res_true": bf_info["rel_res_true"],
+            "inner_rtol": BF16_INNER, "autotune_s": round(tune_s, 3),
+            "autotuned": {"chunks": tca._lib.tca_autotuned_chunks(bplan.handle), "rows_per_thread": bplan.autotuned_rows()},
+            "sweep": {"kernel": "bfloat16 tensor-core CG sweep (tcgen05 kind::f16, FP32 accumulation)",
+                      "avg_launch_ms": round(bf_sweep_ms, 5), "launches": bf_prof["sweep_launches"],
+                      "algorithmic_bytes": 4 * N * 2, "achieved_gbs": round(bf_gbs, 1),
+                      "frac_of_measured_hbm": round(bf_gbs / peaks["hbm_gbs"], 4)},
+            "what": "iterative refinement: outer FP64-accurate (double-float) residual, inner CG with r, p, q in "
+                    "bfloat16 and the modes-3/4 contraction on the tensor cores (BF16 x BF16 -> FP32)"}
+        bplan.close()
+    except Exception as exc:  # reported, not fatal: the plain solve is the bench value
+        variants["bf16_ir"] = {"error": repr(exc)[:300]}
+
+    sub = argparse.Namespace(**vars(args))
+    sub.steps = max(1, min(args.steps, 3))
+    sub.warmup = 1
+    if not args.small:
+        try:
+            variants["batched"] = run_batched(sub, device, emit=False)
+        except Exception as exc:
+            variants["batched"] = {"error": repr(exc)[:300]}
+        if not args.no_learned:
+            try:
+                variants["learned"] = run_learned(sub, device, emit=False)
+            except Exception as exc:
+                variants["learned"] = {"error": repr(exc)[:300]}
+
+
+
 def run_tca(args, rank, world, local):
     import torch
 
@@ -705,7 +770,7 @@ def run_tca(args, rank, world, local):
     # (device buffers, same timing) at the default shift and at twice it;
     # `value` stays the plain CG of Fig. 2.
     variants = {}
-    for shift in (16.0, 32.0):
+    for shift in (() if args.no_variants else (16.0, 32.0)):
         plan.solve(b, x, rtol=RTOL, precond="separable", precond_shift=shift)
         torch.cuda.synchronize()
         pc_times, pc_info = [], None
@@ -723,54 +788,9 @@ def run_tca(args, rank, world, local):
             "what": f"CG preconditioned by the separable tensor inverse (x)_k (G_k + {int(shift)} lambda L_k)^-1 "
                     "(dense TF32 mode products on the tensor cores), same tolerance on the FP64 true residual"}
 
-    # The same solve with the point-Jacobi preconditioner M = diag(K).
-    j_ms, j_info = timed_solve(plan, b, x, args.steps, s, precond="jacobi")
-    variants["jacobi_pcg"] = {
-        "ms": round(max_over_ranks(j_ms, world), 3), "cg_iters": j_info["iters"], "restarts": j_info["refinements"],
-        "rel_res_true": j_info["rel_res_true"],
-        "what": "CG preconditioned by point Jacobi, M = diag(K) = prod_k diag(G_k) + lambda sum_k diag(L_k)"}
-
-    # Mixed precision in bfloat16: the same problem, TCA_BF16_IR (bfloat16 inner CG on the
-    # tensor-core sweep, double-float refinement), tuned by tca_autotune.
     peaks, peak_src = measured_peaks()
-    try:
-        bplan = tca.plan_from_instance(inst, precision="bf16_ir")
-        t0 = time.perf_counter()
-        bplan.autotune()
-        tune_s = time.perf_counter() - t0
-        bf_ms, bf_info = timed_solve(bplan, b, x, args.steps, s, inner_rtol=BF16_INNER)
-        _, bf_prof = bplan.solve(b, x, rtol=RTOL, inner_rtol=BF16_INNER, profile=True)
-        bf_sweep_ms = bf_prof["sweep_ms"] / max(bf_prof["sweep_launches"], 1)
-        bf_gbs = 4 * N * 2 / bf_sweep_ms / 1e6  # CG sweep: r, p_old in; p, q out (bfloat16)
-        variants["bf16_ir"] = {
-            "ms": round(max_over_ranks(bf_ms, world), 3), "inner_iters": bf_info["iters"],
-            "refinements": bf_info["refinements"], "rel_res_true": bf_info["rel_res_true"],
-            "inner_rtol": BF16_INNER, "autotune_s": round(tune_s, 3),
-            "autotuned": {"chunks": tca._lib.tca_autotuned_chunks(bplan.handle), "rows_per_thread": bplan.autotuned_rows()},
-            "sweep": {"kernel": "bfloat16 tensor-core CG sweep (tcgen05 kind::f16, FP32 accumulation)",
-                      "avg_launch_ms": round(bf_sweep_ms, 5), "launches": bf_prof["sweep_launches"],
-                      "algorithmic_bytes": 4 * N * 2, "achieved_gbs": round(bf_gbs, 1),
-                      "frac_of_measured_hbm": round(bf_gbs / peaks["hbm_gbs"], 4)},
-            "what": "iterative refinement: outer FP64-accurate (double-float) residual, inner CG with r, p, q in "
-                    "bfloat16 and the modes-3/4 contraction on the tensor cores (BF16 x BF16 -> FP32)"}
-        bplan.close()
-    except Exception as exc:  # reported, not fatal: the plain solve is the bench value
-        variants["bf16_ir"] = {"error": repr(exc)[:300]}
-
-    sub = argparse.Namespace(**vars(args))
-    sub.steps = max(1, min(args.steps, 3))
-    sub.warmup = 1
-    if not args.small:
-        try:
-            variants["batched"] = run_batched(sub, device, emit=False)
-        except Exception as exc:
-            variants["batched"] = {"error": repr(exc)[:300]}
-        if not args.no_learned:
-            try:
-                variants["learned"] = run_learned(sub, device, emit=False)
-            except Exception as exc:
-                variants["learned"] = {"error": repr(exc)[:300]}
-
+    if not args.no_variants:
+        run_variants(args, plan, inst, b, x, s, N, world, device, peaks, variants)
     sweeps = time_sweeps(plan, inst, device)
     if rank != 0:
         return
