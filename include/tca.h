@@ -171,7 +171,11 @@ typedef struct {
   int32_t precond;      /* TCA_PRECOND_NONE: the CG of Fig. 2; TCA_PRECOND_SEPARABLE: the same CG with
                            Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d);
                            TCA_PRECOND_JACOBI: M = diag(K) (see below) */
-  double precond_shift; /* s, the regulariser weight folded into each mode of M (0: default 16) */
+  double precond_shift; /* s, the regulariser weight folded into each mode of M (0: 16).  The best s
+                           depends on lambda and the factors (s = 32 beats 16 for the B-spline
+                           workload at lambda = 1e-3 and loses for lambda above ~4e-3); 16 is a
+                           middle value tuned for no problem in particular: pass s when the
+                           problem is known. */
 } tca_solve_opts;
 
 /* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_JACOBI is point
@@ -191,7 +195,9 @@ typedef struct {
  * P = Z + beta P; the stop test stays on ||R|| / ||A^T b|| and on the FP64
  * true residual, so the result meets the same tolerance.  The paper fixes no
  * preconditioner; this one is an addition.  Costs d dense mode products and
- * one inner product per iteration, and one n_k x n_k dense factor per mode. */
+ * one inner product per iteration, and one n_k x n_k dense factor per mode;
+ * the tensor-core products of an iteration that starts after the stop flags
+ * are set return at entry, like the CG kernels. */
 enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1, TCA_PRECOND_JACOBI = 2 };
 
 typedef struct {

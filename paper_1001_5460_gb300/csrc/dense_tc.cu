@@ -101,7 +101,11 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, int parity, volatile int* 
 // Loading tile t + 1 overlaps the MMAs of tile t and the epilogue of t - 1.
 __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(const float* __restrict__ x, float* __restrict__ y,
                                                                  const float* __restrict__ a, TcGeom g,
-                                                                 int* __restrict__ timeout_flag) {
+                                                                 int* __restrict__ timeout_flag,
+                                                                 const Scalars* __restrict__ stop) {
+  // A CG preconditioner product after the iteration's stop flags are set
+  // does no work (before any barrier or tensor-memory allocation).
+  if (stop && cg_done(stop)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -310,7 +314,7 @@ int dense_tc_max_split(int64_t n_in, int64_t n_out) {
 }
 
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
-                           cudaStream_t s, int sm_cap) {
+                           cudaStream_t s, int sm_cap, const Scalars* stop) {
   const int n_in = (int)d.n_in, n_out = (int)d.n_out;
   if (!d.a32 || n_in <= 0 || n_out <= 0) return TCA_ERR_UNSUPPORTED;
   if ((uintptr_t)x % 16 != 0) return TCA_ERR_UNSUPPORTED;
@@ -340,7 +344,7 @@ tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, 
   // for Np <= 128) or the second waits for the first to free its columns.
   const int64_t grid = std::min<int64_t>(g.tiles, (int64_t)(sm_cap > 0 ? std::min(sm_cap, tc_sm_count()) : tc_sm_count()));
   dense_tc_kernel<<<(unsigned)std::max<int64_t>(grid, 1), kTcThreads, bytes, s>>>(x, y, d.a32, g,
-                                                                                  wait_timeout_flag());
+                                                                                  wait_timeout_flag(), stop);
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }

@@ -300,7 +300,8 @@ tca_status launch_mode_op(const ModeOp& op, const Tin* x, Tout* y, int64_t O, in
       const tca_status st = launch_band_fast(op.band, (const float*)x, (float*)y, O, I, s, op.sm_cap);
       if (st != TCA_ERR_UNSUPPORTED) return st;
     } else if (op.tc_split > 0) {
-      const tca_status st = launch_dense_tc(op.dense, (const float*)x, (float*)y, O, I, op.tc_split, s, op.sm_cap);
+      const tca_status st =
+          launch_dense_tc(op.dense, (const float*)x, (float*)y, O, I, op.tc_split, s, op.sm_cap, op.stop);
       if (st != TCA_ERR_UNSUPPORTED) return st;
     }
   }

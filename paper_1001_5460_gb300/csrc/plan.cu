@@ -396,6 +396,7 @@ tca_status ensure_precond(tca_plan_s* p, double shift) {
     // preconditioner needs no more); reduced-precision plans TF32; FP64 native.
     const int split = dense_tc_max_split(n, n);
     op.tc_split = p->prec == TCA_F64 ? 0 : (p->prec == TCA_F32 ? split : std::min(split, 1));
+    op.stop = p->scal;  // products after the stop flags are set skip their work
   }
   if (!p->z) {
     cudaError_t e = cudaMalloc(&p->z, elem_size(p) * (size_t)p->N);

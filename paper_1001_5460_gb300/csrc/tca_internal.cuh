@@ -51,6 +51,8 @@ struct ModeOp {
   Dense dense;
   int tc_split = 0;  // dense FP32 products on tensor cores: 0 off, 1 TF32, 2 3xTF32
   int sm_cap = 0;    // SMs its persistent kernels may fill (0: the whole GPU; set by batched solves)
+  const struct Scalars* stop = nullptr;  // preconditioner factors: the tensor-core product returns at
+                                         // entry once these CG stop flags are set
   int64_t n_out() const { return kind == OP_BAND ? band.n_out : dense.n_out; }
   int64_t n_in() const { return kind == OP_BAND ? band.n_in : dense.n_in; }
 };
@@ -288,7 +290,7 @@ tca_status launch_band_fast(const Band& band, const float* x, float* y, int64_t 
 int rows_per_chunk(const int32_t* start_host, int64_t n_out, int W);
 // Dense mode product on tcgen05 tensor cores (dense_tc.cu); split 1 = TF32, 2 = 3xTF32.
 tca_status launch_dense_tc(const Dense& d, const float* x, float* y, int64_t O, int64_t I, int split,
-                           cudaStream_t s, int sm_cap = 0);
+                           cudaStream_t s, int sm_cap = 0, const Scalars* stop = nullptr);
 // Device address of the wait-timeout flag (for kernels in other translation units).
 int* wait_timeout_flag();
 // Synchronise s; TCA_ERR_TIMEOUT (and clear the flag) if a bounded wait gave up.
