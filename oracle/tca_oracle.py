@@ -36,6 +36,13 @@ Structured Problems with Computational Tensor Algebra"):
   mode by mode.  The approximation keeps the Gram part of K exactly and spreads
   the regulariser over the modes with weight s (a reading: the paper fixes no
   preconditioner).
+* ``scattered_apply`` / ``scattered_apply_T`` / ``scattered_normal_apply`` - the
+  system tensor of scattered (off-grid) samples (Sec. 2.2, repeated indices; the
+  real 4D problem of Sec. 5): sample s weights unknown (i_1..i_d) by the product
+  of its per-mode weights A_k[s, i_k], i.e. the rows of A are the Kronecker
+  products of the rows of the A_k (the row-wise, face-splitting product), and
+  A^T A is a sum over samples of rank-1 tensor products.  Written out term by
+  term over each sample's non-zero window.
 * ``kron_matrix`` / ``dense_normal_matrix`` / ``direct_solve`` - the
   equivalent matrix form of a tensor equation "with proper reshaping" (Sec. 3,
   after Eq. TensorEq), solved by a direct (Cholesky) method - the direct-solver
@@ -73,6 +80,11 @@ __all__ = [
     "dense_normal_matrix",
     "direct_solve",
     "CGResult",
+    "scattered_apply",
+    "scattered_apply_T",
+    "scattered_normal_apply",
+    "scattered_rows_matrix",
+    "jacobi_diagonal",
 ]
 
 
@@ -312,6 +324,72 @@ def rel_residual(x: np.ndarray, b: np.ndarray, mats, lam: float) -> float:
     rhs = apply_T(b, mats)
     r = rhs - normal_apply(x, mats, lam)
     return float(np.sqrt(inner(r, r)) / np.sqrt(inner(rhs, rhs)))
+
+
+def _window_terms(col0s, ws, shape):
+    """For each combination of per-mode taps (a_1..a_d): the weight product over samples and the
+    flat grid index (-1 where a tap falls outside the grid)."""
+    d = len(shape)
+    m = col0s[0].shape[0]
+    width = [w.shape[1] for w in ws]
+    for taps in itertools.product(*[range(t) for t in width]):
+        wt = np.ones(m)
+        flat = np.zeros(m, dtype=np.int64)
+        ok = np.ones(m, dtype=bool)
+        for k in range(d):
+            idx = np.asarray(col0s[k], dtype=np.int64) + taps[k]
+            wt = wt * np.asarray(ws[k], dtype=np.float64)[:, taps[k]]
+            ok &= (idx >= 0) & (idx < shape[k])
+            flat = flat * shape[k] + np.where(ok, idx, 0)
+        yield wt, np.where(ok, flat, -1)
+
+
+def scattered_apply(x: np.ndarray, col0s, ws) -> np.ndarray:
+    """(A x)_s = sum over the taps a_k of prod_k w_k[s, a_k] * x[col0_1[s] + a_1, ..., col0_d[s] + a_d]
+    for scattered samples: mode k's weights of sample s sit in columns col0_k[s] .. col0_k[s] + 3
+    (a row of an m x n_k ELL-4 matrix); taps outside the grid are dropped."""
+    x = np.asarray(x, dtype=np.float64)
+    xf = x.ravel()
+    y = np.zeros(col0s[0].shape[0])
+    for wt, flat in _window_terms(col0s, ws, x.shape):
+        ok = flat >= 0
+        y[ok] += wt[ok] * xf[flat[ok]]
+    return y
+
+
+def scattered_apply_T(y: np.ndarray, col0s, ws, shape) -> np.ndarray:
+    """x = A^T y for scattered samples: every sample adds y_s times its weight product to each
+    unknown of its window."""
+    y = np.asarray(y, dtype=np.float64)
+    xf = np.zeros(int(np.prod(shape)))
+    for wt, flat in _window_terms(col0s, ws, shape):
+        ok = flat >= 0
+        np.add.at(xf, flat[ok], wt[ok] * y[ok])
+    return xf.reshape(shape)
+
+
+def scattered_normal_apply(x: np.ndarray, col0s, ws, lam: float) -> np.ndarray:
+    """(A^T A + lam R) x for scattered samples, through sample space (as ``normal_apply``)."""
+    x = np.asarray(x, dtype=np.float64)
+    return scattered_apply_T(scattered_apply(x, col0s, ws), col0s, ws, x.shape) + regulariser(x, lam)
+
+
+def scattered_rows_matrix(col0s, ws, shape) -> np.ndarray:
+    """Explicit m x N matrix of the scattered system tensor: row s is the Kronecker product of
+    the samples' dense per-mode rows (tiny cases only)."""
+    m = col0s[0].shape[0]
+    rows = []
+    for s_ in range(m):
+        dense_rows = []
+        for k, n in enumerate(shape):
+            r = np.zeros(n)
+            for a in range(ws[k].shape[1]):
+                j = int(col0s[k][s_]) + a
+                if 0 <= j < n:
+                    r[j] += ws[k][s_, a]
+            dense_rows.append(r)
+        rows.append(functools.reduce(np.kron, dense_rows))
+    return np.array(rows)
 
 
 def kron_matrix(mats) -> np.ndarray:

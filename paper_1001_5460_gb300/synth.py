@@ -236,6 +236,43 @@ def instance_batched(index: int, base_seed: int = 100, lo: int = 24, hi: int = 9
     return Instance(tuple(dims), factors, x_true, noise, lam, seed)
 
 
+@dataclasses.dataclass
+class ScatteredInstance:
+    """Samples at scattered positions: per mode k the ELL-4 rows (col0[k], w[k]) of an
+    m x n_k matrix (row s: the cubic B-spline weights of sample s along mode k)."""
+
+    shape: tuple
+    col0: list
+    w: list
+    x_true: np.ndarray
+    noise: np.ndarray
+    lam: float
+    seed: int
+
+    @property
+    def m(self) -> int:
+        return int(self.col0[0].shape[0])
+
+
+def instance_scattered(shape, m: int, seed: int, lam: float = 1e-3, sigma: float = 4.0) -> ScatteredInstance:
+    """m samples at independent uniform positions in the grid box [0, n_k - 1] per axis (off the
+    grid, in random order), cubic B-spline weights per mode with the truncated basis; x_true a
+    smooth random field (unit RMS), noise N(0, 0.01^2).  Draw order: positions (m x d), field, noise."""
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(0.0, 1.0, size=(m, len(shape))) * (np.asarray(shape, dtype=np.float64) - 1.0)
+    col0, w = [], []
+    for k, n in enumerate(shape):
+        c0 = np.floor(t[:, k]).astype(np.int64) - 1
+        cols = c0[:, None] + np.arange(4)[None, :]
+        wk = bspline3(t[:, k][:, None] - cols)
+        wk[(cols < 0) | (cols >= n)] = 0.0
+        col0.append(c0.astype(np.int32))
+        w.append(wk)
+    x_true = smooth_random_field(tuple(shape), sigma, rng, dtype=np.float64)
+    noise = 0.01 * rng.standard_normal(m)
+    return ScatteredInstance(tuple(shape), col0, w, x_true, noise, lam, seed)
+
+
 NET_LAYERS = ((1, 32), (32, 32), (32, 32), (32, 1))  # (c_in, c_out) of the 4 convolution layers
 
 

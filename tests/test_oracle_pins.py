@@ -500,3 +500,54 @@ def test_sampled_oracle_matches_full():
     kx = O.normal_apply(x, mats, 0.3)
     for i in [(0, 0, 0), (3, 2, 4), (1, 1, 2)]:
         assert O.normal_apply_at(x, mats, 0.3, i) == pytest.approx(kx[i], rel=1e-12)
+
+
+# ---- scattered samples (row-wise / face-splitting product of the per-mode rows) ----
+
+@pytest.mark.parametrize("shape,m", [((5, 4, 6), 37), ((4, 5, 3, 4), 29)])
+def test_scattered_apply_equals_explicit_kronecker_rows(shape, m):
+    """Row s of the scattered system tensor is the Kronecker product of the sample's dense
+    per-mode rows; the windowed sums equal that explicit matrix, and the transpose is its
+    adjoint."""
+    inst = synth.instance_scattered(shape, m, seed=40 + m)
+    a = O.scattered_rows_matrix(inst.col0, inst.w, shape)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(shape)
+    y = rng.standard_normal(m)
+    np.testing.assert_allclose(O.scattered_apply(x, inst.col0, inst.w), a @ x.ravel(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(O.scattered_apply_T(y, inst.col0, inst.w, shape).ravel(), a.T @ y,
+                               rtol=1e-12, atol=1e-13)
+    k = a.T @ a + O.dense_normal_matrix([np.zeros((1, n)) for n in shape], inst.lam, shape)
+    np.testing.assert_allclose(O.scattered_normal_apply(x, inst.col0, inst.w, inst.lam).ravel(), k @ x.ravel(),
+                               rtol=1e-11, atol=1e-12)
+
+
+def test_scattered_on_a_tensor_grid_equals_the_separable_operator():
+    """Samples that lie on a tensor grid of per-mode positions are the rows of A_1 x ... x A_d:
+    the scattered operator must then equal the separable one (Eq. separable_transf)."""
+    rng = np.random.default_rng(12)
+    shape = (6, 5, 7, 4)
+    facs = [synth.bspline_factor_ell4(n, int(round(1.5 * n)), rng) for n in shape]
+    mats = [synth.ell4_to_dense(c0, w, n) for (c0, w, _), n in zip(facs, shape)]
+    ms = [f[0].shape[0] for f in facs]
+    grid = np.array(list(itertools.product(*[range(mm) for mm in ms])))  # C order of the sample tensor
+    col0s = [facs[k][0][grid[:, k]] for k in range(4)]
+    ws = [facs[k][1][grid[:, k]] for k in range(4)]
+    x = rng.standard_normal(shape)
+    np.testing.assert_allclose(O.scattered_apply(x, col0s, ws), O.apply(x, mats).ravel(), rtol=1e-12, atol=1e-13)
+    y = rng.standard_normal(len(grid))
+    np.testing.assert_allclose(O.scattered_apply_T(y, col0s, ws, shape), O.apply_T(y.reshape(ms), mats),
+                               rtol=1e-12, atol=1e-13)
+
+
+def test_scattered_cg_matches_direct_solve():
+    shape = (5, 6, 4)
+    inst = synth.instance_scattered(shape, 300, seed=9, lam=1e-2)
+    a = O.scattered_rows_matrix(inst.col0, inst.w, shape)
+    b = a @ inst.x_true.ravel() + inst.noise
+    k = a.T @ a + O.dense_normal_matrix([np.zeros((1, n)) for n in shape], inst.lam, shape)
+    ref = np.linalg.solve(k, a.T @ b).reshape(shape)
+    res = O.cg(lambda v: O.scattered_normal_apply(v, inst.col0, inst.w, inst.lam),
+               O.scattered_apply_T(b, inst.col0, inst.w, shape), rtol=1e-12)
+    assert res.converged
+    np.testing.assert_allclose(res.x, ref, rtol=1e-8, atol=1e-9)
