@@ -134,6 +134,26 @@ typedef struct tca_plan_s* tca_plan_t;
 TCA_API tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, const tca_factor* factors,
                     const tca_reg* reg, tca_precision prec, cudaStream_t stream);
 
+/* Build a plan for scattered (off-grid) samples: the same unknown grid
+ * (sizes n[0..order-1]) and regulariser, but a system tensor whose rows are
+ * Kronecker products of per-sample, per-mode rows - sample s weights unknown
+ * (i_1..i_d) by prod_k A_k[s][i_k] (the row-wise or face-splitting product of
+ * the A_k; a tensor multiplication with a repeated index, Sec. 2.2, and the
+ * structure of the paper's 4D reconstruction from scattered measurements,
+ * Sec. 5).  rows[k]: an ELL4 factor with m rows (one per sample, the same
+ * sample order in every mode) and n[k] columns, in host memory (copied).
+ * The data tensor is a vector of m samples in that order.  A^T A is a sum of
+ * rank-1 tensor products, not separable: tca_apply gathers each sample's
+ * 4^d window, tca_apply_T scatters it back (FP64 atomic additions, so the
+ * last bits of a sum may vary between runs), tca_apply_normal and the CG
+ * iterations of tca_solve go through sample space, and the regulariser is
+ * the separable one of tca_plan.  prec must be TCA_F64
+ * (TCA_ERR_UNSUPPORTED otherwise); no preconditioner, no tca_apply_mode, no
+ * batched solve.  Returns TCA_ERR_SHAPE if a factor's m or n does not match. */
+TCA_API tca_status tca_plan_scattered(tca_plan_t* out, int order, const int64_t* n, int64_t m,
+                                      const tca_factor* rows, const tca_reg* reg, tca_precision prec,
+                                      cudaStream_t stream);
+
 /* y = A x = X x_1 A_1 ... x_d A_d (Sec. 2.1, Eq. separable_transf).
  * x: n-shaped, y: m-shaped, both C-order, element type of the plan. */
 TCA_API tca_status tca_apply(tca_plan_t plan, const void* x, void* y, cudaStream_t stream);

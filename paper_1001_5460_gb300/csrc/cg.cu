@@ -403,6 +403,10 @@ static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
   p->pc_kind = TCA_PRECOND_NONE;
   const int kind = o ? o->precond : TCA_PRECOND_NONE;
   if (kind == TCA_PRECOND_NONE) return TCA_OK;
+  if (p->scattered) {
+    set_error_message("scattered-sample plans take no preconditioner");
+    return TCA_ERR_UNSUPPORTED;
+  }
   if (kind == TCA_PRECOND_JACOBI) {
     TCA_TRY(ensure_jacobi(p));
   } else {

@@ -420,6 +420,14 @@ static void dims4_of(const tca_plan_s* p, int64_t* d4) {
 template <typename Tin, typename Tout, typename Tc>
 tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, void* const* ws,
                        int64_t ws_elems, cudaStream_t s) {
+  if (p->scattered) {
+    // Scattered samples: one gather (A x) or one scatter-add (A^T y), FP64 only.
+    if constexpr (sizeof(Tin) == 8 && sizeof(Tout) == 8) {
+      return transpose ? scattered_scatter(p, (const double*)x, (double*)y, true, s)
+                       : scattered_gather(p, (const double*)x, (double*)y, true, s);
+    }
+    return TCA_ERR_UNSUPPORTED;
+  }
   const int d = p->d;
   int64_t cur[kMaxModes];
   for (int k = 0; k < d; ++k) cur[k] = transpose ? p->m[k] : p->n[k];
@@ -451,6 +459,17 @@ tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, voi
 // With dot, the regulariser pass also forms <x, y> and alpha (CG sweep).
 template <typename T>
 tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const RegDot* dot) {
+  int64_t d4[kMaxModes];
+  dims4_of(p, d4);
+  if (p->scattered) {
+    // A^T (A x) through sample space, then lambda R x (and <x, y>) as for separable plans.
+    if constexpr (sizeof(T) == 8) {
+      TCA_TRY(scattered_gather(p, (const double*)x, p->sc_tmp, false, s));
+      TCA_TRY(scattered_scatter(p, p->sc_tmp, (double*)y, false, s));
+      return launch_reg_add_impl<T, T>(p, x, y, d4, 1, dot, s);
+    }
+    return TCA_ERR_UNSUPPORTED;
+  }
   const int d = p->d;
   const void* src = x;
   for (int k = 0; k < d; ++k) {
@@ -461,8 +480,6 @@ tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const
     TCA_TRY((launch_mode_op<T, T, T>(p->mode[k].gram, (const T*)src, (T*)dst, O, I, s)));
     src = dst;
   }
-  int64_t d4[kMaxModes];
-  dims4_of(p, d4);
   return launch_reg_add_impl<T, T>(p, x, y, d4, 1, dot, s);
 }
 
@@ -502,6 +519,10 @@ static tca_status ensure_ws64(tca_plan_s* p) {
 template <typename Tin>
 tca_status normal_fp64(tca_plan_s* p, const Tin* x, double* y, cudaStream_t s) {
   TCA_TRY(ensure_ws64(p));
+  if (p->scattered) {
+    if constexpr (sizeof(Tin) == 8) return normal_generic<double>(p, (const double*)x, y, s, nullptr);
+    return TCA_ERR_UNSUPPORTED;
+  }
   const int d = p->d;
   const void* src = x;
   for (int k = 0; k < d; ++k) {
@@ -622,6 +643,7 @@ extern "C" tca_status tca_apply_mode(tca_plan_t plan, int mode, int op, const in
                                      void* y, cudaStream_t stream) {
   if (!plan || !dims || !x || !y || x == y) return TCA_ERR_INVALID_ARG;
   tca_plan_s* p = plan;
+  if (p->scattered) return TCA_ERR_UNSUPPORTED;  // no per-mode factors
   if (mode < 0 || mode >= p->d) return TCA_ERR_INVALID_ARG;
   const Mode& md = p->mode[mode];
   const ModeOp* mop = op == TCA_OP_FACTOR ? &md.fwd : op == TCA_OP_FACTOR_T ? &md.bwd : op == TCA_OP_GRAM ? &md.gram : nullptr;

@@ -551,6 +551,7 @@ static void destroy_plan(tca_plan_s* p) {
   for (cudaEvent_t& ev : p->sweep_ev)
     if (ev) cudaEventDestroy(ev);
   bf16_release(p);
+  scattered_release(p);
   cudaFree(p->scal);
   if (p->scal_host) cudaFreeHost(p->scal_host);
   cudaFree(p->red.partials);

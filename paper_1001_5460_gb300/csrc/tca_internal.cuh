@@ -171,6 +171,14 @@ struct tca_plan_s {
   cudaEvent_t chunk_ev[8] = {};
 
   tca::Bf16State bf;             // TCA_BF16_IR plans
+  // Scattered samples (tca_plan_scattered): sample rows sorted by their first
+  // window cell; M = sc_m.
+  bool scattered = false;
+  int64_t sc_m = 0;
+  int32_t* sc_col0 = nullptr;  // [k][s]
+  double* sc_w = nullptr;      // [k][s][4]
+  int32_t* sc_perm = nullptr;  // sorted position -> caller's sample index
+  double* sc_tmp = nullptr;    // sample-space vector of the normal operator
   tca::Scalars* scal = nullptr;  // device
   tca::Scalars* scal_host = nullptr;  // pinned mirror
   tca::Reduce red;
@@ -318,6 +326,12 @@ tca_status bf16_flush(tca_plan_s* p, float* d, Reduce red, cudaStream_t s);
 // Solver buffers and scalars set so that a CG-mode sweep runs in full outside
 // a solve (the autotuner times the sweep that solves run).
 tca_status prepare_sweep_timing(tca_plan_s* p, cudaStream_t s);
+
+// Scattered samples (scattered.cu): y = A x (gather) and x = A^T y (scatter-add,
+// x zeroed first); perm: y in the caller's sample order.
+tca_status scattered_gather(const tca_plan_s* p, const double* x, double* y, bool perm, cudaStream_t s);
+tca_status scattered_scatter(const tca_plan_s* p, const double* y, double* x, bool perm, cudaStream_t s);
+void scattered_release(tca_plan_s* p);
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);

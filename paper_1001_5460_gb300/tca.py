@@ -87,6 +87,9 @@ _lib.tca_plan.restype = ctypes.c_int
 for _name in ("tca_apply", "tca_apply_T", "tca_apply_normal"):
     getattr(_lib, _name).argtypes = [_vp, _vp, _vp, _vp]
     getattr(_lib, _name).restype = ctypes.c_int
+_lib.tca_plan_scattered.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64p, ctypes.c_int64,
+                                    ctypes.POINTER(tca_factor), ctypes.POINTER(tca_reg), ctypes.c_int, _vp]
+_lib.tca_plan_scattered.restype = ctypes.c_int
 _lib.tca_apply_mode.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _i64p, _vp, _vp, _vp]
 _lib.tca_apply_mode.restype = ctypes.c_int
 _lib.tca_solve.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), ctypes.POINTER(tca_solve_info), _vp]
@@ -261,7 +264,7 @@ def vec_dot(a, b, out, stream=None):
 
 
 def exported_symbols() -> list[str]:
-    return ["tca_plan", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
+    return ["tca_plan", "tca_plan_scattered", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
             "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
@@ -372,6 +375,40 @@ class Plan:
     def autotuned_rows(self) -> int:
         """Core rows per worker thread the autotuner chose for a bfloat16 plan (0: not tuned)."""
         return int(_lib.tca_autotuned_rows(self._h))
+
+
+class ScatteredPlan(Plan):
+    """A plan for scattered samples: per mode k the m x n_k ELL-4 rows (col0s[k], ws[k]) of the
+    samples' weights; the system tensor's rows are the Kronecker products of those rows."""
+
+    def __init__(self, shape, col0s, ws, lam: float = 0.0, reg_mask: int | None = None, precision="f64",
+                 stream=None):
+        self.shape = tuple(int(v) for v in shape)
+        self.order = len(self.shape)
+        m = int(np.asarray(col0s[0]).shape[0])
+        self.factors = []
+        for c, w, n in zip(col0s, ws, self.shape):
+            c = np.asarray(c, dtype=np.int32)
+            w = np.asarray(w, dtype=np.float64)
+            if w.shape != (c.shape[0], 4):
+                raise ValueError(f"ELL-4 weights of shape {w.shape} for {c.shape[0]} rows")
+            # each mode carries its own row count; the library checks they all equal m
+            self.factors.append(Factor(FACTOR_ELL4, c.shape[0], n, w, c))
+        self.sample_shape = (m,)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.dtype = np.float64 if self.precision == F64 else np.float32
+        arr = (tca_factor * self.order)()
+        for k, f in enumerate(self.factors):
+            arr[k].kind, arr[k].reserved, arr[k].m, arr[k].n = f.kind, 0, f.m, f.n
+            arr[k].values = f.values.ctypes.data
+            arr[k].col0 = f.col0.ctypes.data
+        n = (ctypes.c_int64 * self.order)(*self.shape)
+        reg = tca_reg(float(lam), (1 << self.order) - 1 if reg_mask is None else int(reg_mask), 0)
+        h = _vp()
+        _check(_lib.tca_plan_scattered(ctypes.byref(h), self.order, n, m, arr, ctypes.byref(reg), self.precision,
+                                       _stream(stream)), "tca_plan_scattered")
+        self._h = h
+        self.lam = float(lam)
 
 
 def _info_dict(info) -> dict:
