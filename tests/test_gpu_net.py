@@ -140,38 +140,56 @@ def _pair(tca, inst, plan, device_solve=True):
 
 
 def test_training_reduces_loss_and_solve_from_net_guess():
-    """Train on solver-generated pairs; the learned x0 must help CG on a held-out instance."""
+    """Train on solver-generated pairs (12 instances, 400 Adam steps, cosine-decayed rate); on
+    three held-out instances the network's x0 = s Net(A^T b / s) must show its gain: relative
+    error to the CG solution at most 0.35 (x0 = 0 has 1; measured 0.16-0.21), true relative
+    residual at most 0.2 (x0 = 0 has 1; measured 0.09-0.10), and CG from it reaching 1e-6 (by
+    the oracle) in at least one iteration fewer than from zero (measured: 2 fewer on each).
+    That the iteration gain is small next to the error reduction is the finding: what the
+    network removes are the smooth components CG removes cheaply anyway."""
     tca = lib()
     torch = need_cuda()
     shape = (24, 24, 24, 4)
     train = []
-    for k in range(6):
+    for k in range(12):
         inst = synth.instance_bspline(shape, seed=1000 + k)
         plan = tca.plan_from_instance(inst)
         train.append(_pair(tca, inst, plan)[1:])
     net = tca.Net(synth.net_init_params(5))
     losses = []
-    for step in range(150):
+    steps = 400
+    for step in range(steps):
         u, t = train[step % len(train)]
         net.accumulate(u, t)
         losses.append(net.take_loss())
-        net.adam(2e-3)
-    first, last = np.mean(losses[:6]), np.mean(losses[-6:])
+        net.adam(2e-3 * 0.5 * (1 + np.cos(np.pi * step / steps)))
+    first, last = np.mean(losses[:12]), np.mean(losses[-12:])
     assert last < 0.5 * first, (first, last)
-    # Held-out instance: x0 = s Net(A^T b / s), then CG to 1e-6.
-    inst = synth.instance_bspline(shape, seed=2000, dtype=np.float64)
-    plan = tca.plan_from_instance(inst)
-    b, _, _ = _pair(tca, inst, plan)
-    x_plain = torch.empty(shape, dtype=torch.float32, device="cuda")
-    _, info_plain = plan.solve(b, x_plain, rtol=1e-6)
-    x_net = torch.empty_like(x_plain)
-    st, info_net = net.solve(plan, b, x_net, rtol=1e-6)
-    assert st == tca.OK
-    mats = [f.dense() for f in inst.factors]
-    bh = b.cpu().numpy().astype(np.float64)
-    rel = O.rel_residual(x_net.cpu().numpy(), bh, mats, inst.lam)
-    assert rel <= 1.5e-6, (rel, info_net)
-    assert info_net["iters"] <= info_plain["iters"], (info_net, info_plain)
+    for seed in (2000, 2001, 2002):
+        inst = synth.instance_bspline(shape, seed=seed, dtype=np.float64)
+        plan = tca.plan_from_instance(inst)
+        b, u, xs = _pair(tca, inst, plan)
+        mats = [f.dense() for f in inst.factors]
+        bh = b.cpu().numpy().astype(np.float64)
+        # x0 in the caller's units: the solve's own scaling, taken from A^T b.
+        atb = torch.empty(shape, dtype=torch.float32, device="cuda")
+        plan.apply_T(b, atb)
+        s = float(torch.sqrt(torch.mean(atb.double() ** 2)))
+        y = torch.empty_like(u)
+        net.forward(u, y)
+        x0 = (y * s).cpu().numpy().astype(np.float64)
+        xstar = (xs * s).cpu().numpy().astype(np.float64)
+        err0 = np.linalg.norm(x0 - xstar) / np.linalg.norm(xstar)
+        res0 = O.rel_residual(x0, bh, mats, inst.lam)
+        assert err0 <= 0.35 and res0 <= 0.2, (seed, err0, res0)
+        x_plain = torch.empty(shape, dtype=torch.float32, device="cuda")
+        _, info_plain = plan.solve(b, x_plain, rtol=1e-6)
+        x_net = torch.empty_like(x_plain)
+        st, info_net = net.solve(plan, b, x_net, rtol=1e-6)
+        assert st == tca.OK
+        rel = O.rel_residual(x_net.cpu().numpy(), bh, mats, inst.lam)
+        assert rel <= 1.5e-6, (rel, info_net)
+        assert info_net["iters"] <= info_plain["iters"] - 1, (seed, info_net, info_plain)
     # The network as a preconditioner step every 8 iterations: CG still judges the error.
     x_pc = torch.empty_like(x_plain)
     st, info_pc = net.solve(plan, b, x_pc, rtol=1e-6, net_every=8)
