@@ -190,7 +190,8 @@ typedef struct {
   int32_t profile;      /* 1: time every normal-operator sweep with CUDA events (info->sweep_*) */
   int32_t precond;      /* TCA_PRECOND_NONE: the CG of Fig. 2; TCA_PRECOND_SEPARABLE: the same CG with
                            Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d);
-                           TCA_PRECOND_JACOBI: M = diag(K) (see below) */
+                           TCA_PRECOND_JACOBI: M = diag(K); TCA_PRECOND_SEPARABLE_BANDED: the
+                           separable inverse cut to 7-band factors (see below) */
   double precond_shift; /* s, the regulariser weight folded into each mode of M (0: 16).  The best s
                            depends on lambda and the factors (s = 32 beats 16 for the B-spline
                            workload at lambda = 1e-3 and loses for lambda above ~4e-3); 16 is a
@@ -198,7 +199,15 @@ typedef struct {
                            problem is known. */
 } tca_solve_opts;
 
-/* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_JACOBI is point
+/* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_SEPARABLE_BANDED
+ * is the separable preconditioner below with each per-mode inverse
+ * (G_k + s lambda L_k)^-1 cut to its 7 central diagonals (|i - j| <= 3; the
+ * inverses of these banded SPD matrices decay away from the diagonal, and the
+ * cut matrices are checked positive definite, TCA_ERR_UNSUPPORTED otherwise):
+ * M^-1 = B_1 kron .. kron B_d then has the structure of the fused
+ * normal-operator sweep with zero regulariser bands, so z costs one sweep
+ * (8 B per unknown) instead of d dense mode products; plans without the fused
+ * sweep apply it as band mode products.  TCA_PRECOND_JACOBI is point
  * Jacobi, M = diag(K), the diagonally scaled CG of the paper's Fig. 1 solver
  * family: diag(K) = prod_k diag(G_k) + lambda sum_k diag(L_k) is formed once
  * per plan from the per-mode diagonals (FP64, stored as 1 / diag(K) in the
@@ -218,7 +227,7 @@ typedef struct {
  * one inner product per iteration, and one n_k x n_k dense factor per mode;
  * the tensor-core products of an iteration that starts after the stop flags
  * are set return at entry, like the CG kernels. */
-enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1, TCA_PRECOND_JACOBI = 2 };
+enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1, TCA_PRECOND_JACOBI = 2, TCA_PRECOND_SEPARABLE_BANDED = 3 };
 
 typedef struct {
   int32_t iters;             /* CG iterations run (all inner solves summed) */

@@ -410,8 +410,11 @@ static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
   if (kind == TCA_PRECOND_JACOBI) {
     TCA_TRY(ensure_jacobi(p));
   } else {
-    if (kind != TCA_PRECOND_SEPARABLE || o->precond_shift < 0.0) return TCA_ERR_INVALID_ARG;
-    TCA_TRY(ensure_precond(p, o->precond_shift > 0.0 ? o->precond_shift : kDefaultPrecondShift));
+    if ((kind != TCA_PRECOND_SEPARABLE && kind != TCA_PRECOND_SEPARABLE_BANDED) || o->precond_shift < 0.0)
+      return TCA_ERR_INVALID_ARG;
+    const double shift = o->precond_shift > 0.0 ? o->precond_shift : kDefaultPrecondShift;
+    if (kind == TCA_PRECOND_SEPARABLE) TCA_TRY(ensure_precond(p, shift));
+    else TCA_TRY(ensure_precond_banded(p, shift));
   }
   p->pc_on = true;
   p->pc_kind = kind;
@@ -1172,6 +1175,7 @@ static std::vector<const void*> batch_signature(int count, tca_plan_s** plans, c
   key.push_back(reinterpret_cast<const void*>((uintptr_t)(rtol * 1e15)));
   key.push_back((const void*)(intptr_t)(plans[0]->pc_on ? plans[0]->pc_kind : 0));
   key.push_back(reinterpret_cast<const void*>((uintptr_t)(plans[0]->pc_shift * 1e6)));
+  key.push_back(reinterpret_cast<const void*>((uintptr_t)(plans[0]->pcb_shift * 1e6)));
   for (int i = 0; i < count; ++i) {
     key.push_back(plans[i]);
     key.push_back((const void*)(uintptr_t)plans[i]->generation);

@@ -486,8 +486,17 @@ tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const
 // z = M^-1 r for the separable-inverse preconditioner: one dense mode product
 // per mode with the factors (G_k + s lambda L_k)^-1, through the ping-pong
 // workspace.
+// The banded form applies B_1 kron .. kron B_d (7-band truncated inverses): one
+// plain fused sweep with zero regulariser bands where the plan has the fused
+// sweep (it returns at entry once the CG stop flags are set), band mode
+// products otherwise.
 template <typename T>
 tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s) {
+  const bool banded = p->pc_kind == TCA_PRECOND_SEPARABLE_BANDED;
+  if constexpr (sizeof(T) == 4) {
+    if (banded && p->fused_ok && (uintptr_t)r % 16 == 0)
+      return normal_fused_f32(p, nullptr, (const float*)r, nullptr, (float*)z, false, s, &p->pcb_fused, p->scal);
+  }
   const int d = p->d;
   const void* src = r;
   for (int k = 0; k < d; ++k) {
@@ -495,7 +504,7 @@ tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s) {
     for (int a = 0; a < k; ++a) O *= p->n[a];
     for (int a = k + 1; a < d; ++a) I *= p->n[a];
     void* dst = (k == d - 1) ? (void*)z : p->ws[k % 2];
-    TCA_TRY((launch_mode_op<T, T, T>(p->pc[k], (const T*)src, (T*)dst, O, I, s)));
+    TCA_TRY((launch_mode_op<T, T, T>(banded ? p->pcb[k] : p->pc[k], (const T*)src, (T*)dst, O, I, s)));
     src = dst;
   }
   return TCA_OK;

@@ -61,6 +61,7 @@ struct FusedArgs {
   CUtensorMap tm_r;
   CUtensorMap tm_p;
   int* timeout_flag;
+  const Scalars* stop;  // plain sweep as a CG preconditioner: no work once these stop flags are set
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -170,6 +171,8 @@ __global__ void __launch_bounds__(NT, 1) fused_normal_kernel(FusedArgs a) {
 
   if constexpr (CG) {
     if (cg_done(a.scal)) return;
+  } else {
+    if (a.stop && cg_done(a.stop)) return;
   }
   const float beta = CG ? (float)a.scal->beta : 0.f;
 
@@ -650,6 +653,8 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
 
   if constexpr (CG) {
     if (cg_done(a.scal)) return;
+  } else {
+    if (a.stop && cg_done(a.stop)) return;
   }
   const float beta = CG ? (float)a.scal->beta : 0.f;
 
@@ -1301,7 +1306,7 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
 }  // namespace
 
 tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, float* p_new, float* q,
-                            bool cg_mode, cudaStream_t s) {
+                            bool cg_mode, cudaStream_t s, const FusedBands* bands, const Scalars* stop) {
   if (!p->fused_ok) return TCA_ERR_UNSUPPORTED;
   FusedArgs a{};
   a.r = r;
@@ -1312,9 +1317,10 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
   int64_t dims[4];
   for (int k = 0; k < 4; ++k) dims[k] = k < d ? p->n[k] : 1;
   for (int k = 0; k < d; ++k) {
-    a.g[k] = p->mode[k].gram.band.w32;
-    a.l[k] = p->mode[k].lap.w32;
+    a.g[k] = bands ? bands->g[k] : p->mode[k].gram.band.w32;
+    a.l[k] = bands ? bands->l[k] : p->mode[k].lap.w32;
   }
+  a.stop = stop;
   for (int k = d; k < 4; ++k) {
     a.g[k] = nullptr;
     a.l[k] = nullptr;
@@ -1327,9 +1333,11 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
   a.red = p->red;
   const int64_t n4 = dims[3];
   if (n4 == 8) {
+    const float* g4 = bands ? bands->g4 : p->ws_g4;
+    const float* l4 = bands ? bands->l4 : p->ws_l4;
     for (int i4 = 0; i4 < 8; ++i4) {
-      for (int e = 0; e < 7; ++e) a.g4c[e * 8 + i4] = p->ws_g4[i4 * 7 + e];
-      for (int e = 0; e < 5; ++e) a.l4c[e * 8 + i4] = p->ws_l4[i4 * 5 + e];
+      for (int e = 0; e < 7; ++e) a.g4c[e * 8 + i4] = g4[i4 * 7 + e];
+      for (int e = 0; e < 5; ++e) a.l4c[e * 8 + i4] = l4[i4 * 5 + e];
     }
     return cg_mode ? launch_ws<true>(p, a, s) : launch_ws<false>(p, a, s);
   } else if (n4 == 4) {

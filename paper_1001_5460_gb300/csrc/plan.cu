@@ -338,22 +338,12 @@ static bool spd_inverse(std::vector<double>& a, int64_t n) {
   return true;
 }
 
-tca_status ensure_precond(tca_plan_s* p, double shift) {
-  if (!(shift >= 0.0) || !std::isfinite(shift)) return TCA_ERR_INVALID_ARG;
-  if (p->pc_shift == shift && p->z) return TCA_OK;
-  // A cached iteration graph holds the old factors' addresses: drop it.
-  TCA_CUDA_TRY(cudaDeviceSynchronize());
-  if (p->graph_exec) {
-    cudaGraphExecDestroy(p->graph_exec);
-    p->graph_exec = nullptr;
-  }
-  ++p->pc_generation;
-  for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
-  p->pc_shift = 0.0;
-  for (int k = 0; k < p->d; ++k) {
+// M_k = G_k + s (lambda L_k), dense n x n in FP64 on the host, inverted in place.
+static tca_status precond_inverse_host(const tca_plan_s* p, int k, double shift, std::vector<double>& a) {
+  {
     const Mode& md = p->mode[k];
     const int64_t n = md.n;
-    std::vector<double> a((size_t)(n * n), 0.0);
+    a.assign((size_t)(n * n), 0.0);
     if (md.gram.kind == OP_DENSE) {
       TCA_CUDA_TRY(cudaMemcpy(a.data(), md.gram.dense.a64, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
     } else {
@@ -383,6 +373,41 @@ tca_status ensure_precond(tca_plan_s* p, double shift) {
       set_error_message("separable preconditioner: G_k + s lambda L_k is not positive definite");
       return TCA_ERR_UNSUPPORTED;
     }
+  }
+  return TCA_OK;
+}
+
+// Drop a cached iteration graph (it holds the old preconditioner's addresses).
+static tca_status drop_graph(tca_plan_s* p) {
+  TCA_CUDA_TRY(cudaDeviceSynchronize());
+  if (p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  ++p->pc_generation;
+  return TCA_OK;
+}
+
+static tca_status ensure_z(tca_plan_s* p) {
+  if (p->z) return TCA_OK;
+  cudaError_t e = cudaMalloc(&p->z, elem_size(p) * (size_t)p->N);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return TCA_ERR_ALLOC;
+  }
+  return TCA_OK;
+}
+
+tca_status ensure_precond(tca_plan_s* p, double shift) {
+  if (!(shift >= 0.0) || !std::isfinite(shift)) return TCA_ERR_INVALID_ARG;
+  if (p->pc_shift == shift && p->z) return TCA_OK;
+  TCA_TRY(drop_graph(p));
+  for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
+  p->pc_shift = 0.0;
+  for (int k = 0; k < p->d; ++k) {
+    const int64_t n = p->mode[k].n;
+    std::vector<double> a;
+    TCA_TRY(precond_inverse_host(p, k, shift, a));
     ModeOp& op = p->pc[k];
     op.kind = OP_DENSE;
     op.dense.n_out = n;
@@ -398,15 +423,74 @@ tca_status ensure_precond(tca_plan_s* p, double shift) {
     op.tc_split = p->prec == TCA_F64 ? 0 : (p->prec == TCA_F32 ? split : std::min(split, 1));
     op.stop = p->scal;  // products after the stop flags are set skip their work
   }
-  if (!p->z) {
-    cudaError_t e = cudaMalloc(&p->z, elem_size(p) * (size_t)p->N);
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      return TCA_ERR_ALLOC;
-    }
-  }
+  TCA_TRY(ensure_z(p));
   TCA_CUDA_TRY(cudaDeviceSynchronize());
   p->pc_shift = shift;
+  return TCA_OK;
+}
+
+// Banded separable preconditioner: each (G_k + s lambda L_k)^-1 keeps its
+// entries with |i - j| <= 3 (the inverses of these banded SPD matrices decay
+// away from the diagonal), checked positive definite, stored as a 7-band in
+// the Gram band's layout.  M^-1 = B_1 kron .. kron B_d then has exactly the
+// structure of the fused sweep with zero regulariser bands.
+tca_status ensure_precond_banded(tca_plan_s* p, double shift) {
+  if (!(shift >= 0.0) || !std::isfinite(shift)) return TCA_ERR_INVALID_ARG;
+  if (p->pcb_shift == shift && p->z) return TCA_OK;
+  TCA_TRY(drop_graph(p));
+  for (int k = 0; k < kMaxModes; ++k) free_op(p->pcb[k]);
+  cudaFree(p->pcb_zero);
+  p->pcb_zero = nullptr;
+  p->pcb_fused = FusedBands();
+  p->pcb_shift = 0.0;
+  int64_t nmax = 1;
+  for (int k = 0; k < p->d; ++k) nmax = std::max(nmax, p->n[k]);
+  TCA_TRY(dmalloc(&p->pcb_zero, nmax * 5));
+  TCA_CUDA_TRY(cudaMemset(p->pcb_zero, 0, sizeof(float) * (size_t)(nmax * 5)));
+  for (int k = 0; k < p->d; ++k) {
+    const int64_t n = p->n[k];
+    std::vector<double> a;
+    TCA_TRY(precond_inverse_host(p, k, shift, a));
+    std::vector<double> band((size_t)(n * 7), 0.0), trunc((size_t)(n * n), 0.0);
+    std::vector<float> band32((size_t)(n * 7));
+    std::vector<int32_t> start((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+      start[(size_t)i] = (int32_t)(i - kGramHalf);
+      for (int e = 0; e < 7; ++e) {
+        const int64_t j = i - kGramHalf + e;
+        if (j < 0 || j >= n) continue;
+        const double v = 0.5 * (a[i * n + j] + a[j * n + i]);  // symmetric by construction
+        band[(size_t)(i * 7 + e)] = v;
+        trunc[(size_t)(i * n + j)] = v;
+      }
+    }
+    for (size_t t = 0; t < band.size(); ++t) band32[t] = (float)band[t];
+    if (!spd_inverse(trunc, n)) {
+      set_error_message("banded separable preconditioner: a truncated inverse is not positive definite");
+      return TCA_ERR_UNSUPPORTED;
+    }
+    ModeOp& op = p->pcb[k];
+    op.kind = OP_BAND;
+    Band& b = op.band;
+    b.n_out = n;
+    b.n_in = n;
+    b.W = 7;
+    b.rows32 = (int)std::min<int64_t>(n, 32) - 1 + b.W;
+    b.unit = true;
+    TCA_TRY(dmalloc(&b.start, n));
+    TCA_TRY(dmalloc(&b.w64, n * 7));
+    TCA_TRY(dmalloc(&b.w32, n * 7));
+    TCA_CUDA_TRY(cudaMemcpy(b.start, start.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    TCA_CUDA_TRY(cudaMemcpy(b.w64, band.data(), sizeof(double) * n * 7, cudaMemcpyHostToDevice));
+    TCA_CUDA_TRY(cudaMemcpy(b.w32, band32.data(), sizeof(float) * n * 7, cudaMemcpyHostToDevice));
+    p->pcb_fused.g[k] = b.w32;
+    p->pcb_fused.l[k] = p->pcb_zero;
+    if (k == 3 && n == 8)
+      for (int t = 0; t < 8 * 7; ++t) p->pcb_fused.g4[t] = band32[(size_t)t];
+  }
+  TCA_TRY(ensure_z(p));
+  TCA_CUDA_TRY(cudaDeviceSynchronize());
+  p->pcb_shift = shift;
   return TCA_OK;
 }
 
@@ -522,6 +606,8 @@ static int64_t chain_peak(const int64_t* start, const int64_t* end, const int* o
 static void destroy_plan(tca_plan_s* p) {
   if (!p) return;
   for (int k = 0; k < kMaxModes; ++k) free_op(p->pc[k]);
+  for (int k = 0; k < kMaxModes; ++k) free_op(p->pcb[k]);
+  cudaFree(p->pcb_zero);
   cudaFree(p->z);
   cudaFree(p->pc_dinv);
   for (int k = 0; k < kMaxModes; ++k) {

@@ -103,6 +103,17 @@ struct Reduce {
   int max_blocks = 0;
 };
 
+// Alternative coefficients for the fused sweep: the same kernel applies any
+// operator of the form (B_1 kron .. kron B_d) + sum_k (I .. C_k .. I) with
+// 7-band B_k and 5-band C_k (the banded separable preconditioner: B_k the
+// truncated inverses, C_k zero).
+struct FusedBands {
+  const float* g[kMaxModes] = {};
+  const float* l[kMaxModes] = {};
+  float g4[8 * 7] = {};  // n4 = 8 plans: B_4 and C_4 by [i4][tap] (kernel parameters)
+  float l4[8 * 5] = {};
+};
+
 // State of a TCA_BF16_IR plan's inner CG (normal_bf16.cu): the inner axis
 // c = (i3, i4) of length nc split into tiles of 128, each with its W = G_3 kron
 // G_4 and R = lambda (L_3 kron I + I kron L_4) operand tiles (bfloat16,
@@ -162,7 +173,14 @@ struct tca_plan_s {
   uint64_t pc_generation = 0;  // bumped whenever the factors are rebuilt (graph cache keys)
   void* z = nullptr;
   bool pc_on = false;       // the iteration being built or run is preconditioned
-  int pc_kind = 0;          // TCA_PRECOND_SEPARABLE or TCA_PRECOND_JACOBI while pc_on
+  int pc_kind = 0;          // TCA_PRECOND_SEPARABLE(_BANDED) or TCA_PRECOND_JACOBI while pc_on
+  // Banded separable preconditioner: 7-band truncations of (G_k + s lambda L_k)^-1,
+  // for shift pcb_shift (0: not built); applied by the fused sweep (pcb_fused) or
+  // as band mode products (pcb).
+  tca::ModeOp pcb[tca::kMaxModes];
+  tca::FusedBands pcb_fused;
+  float* pcb_zero = nullptr;  // zero 5-bands
+  double pcb_shift = 0.0;
   void* pc_dinv = nullptr;  // Jacobi: 1 / diag(K), n-shaped, element type of the plan (built on first use)
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
@@ -253,6 +271,9 @@ struct RegDot {
 tca_status ensure_precond(tca_plan_s* p, double shift);
 // Point-Jacobi preconditioner: build (once) 1 / diag(K) and the z buffer.
 tca_status ensure_jacobi(tca_plan_s* p);
+// Banded separable preconditioner for shift s: build (or keep) the 7-band
+// truncated inverses and the z buffer.
+tca_status ensure_precond_banded(tca_plan_s* p, double shift);
 template <typename T>
 tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s);
 // Largest 3xTF32 / TF32 split the tensor-core dense kernel takes for an
@@ -276,7 +297,8 @@ tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, voi
 // Fused FP32 sweep (fused_ok): optionally p_new = r + beta p_old, q = K p_new,
 // <p_new, q> reduced to alpha.  Returns TCA_ERR_UNSUPPORTED if not applicable.
 tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, float* p_new,
-                            float* q, bool cg_mode, cudaStream_t s);
+                            float* q, bool cg_mode, cudaStream_t s, const FusedBands* bands = nullptr,
+                            const Scalars* stop = nullptr);
 
 // Blocks used by grid-stride vector kernels.
 int vector_grid(const tca_plan_s* p, int64_t n);

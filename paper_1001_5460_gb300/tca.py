@@ -58,18 +58,21 @@ class tca_solve_opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_shift", ctypes.c_double)]
 
 
-PRECOND_NONE, PRECOND_SEPARABLE, PRECOND_JACOBI = 0, 1, 2
+PRECOND_NONE, PRECOND_SEPARABLE, PRECOND_JACOBI, PRECOND_SEPARABLE_BANDED = 0, 1, 2, 3
 
 
 def _precond_code(precond) -> int:
     """None / "none" -> plain CG (Fig. 2); "separable" -> CG with the separable tensor-inverse
-    preconditioner; "jacobi" -> CG with the point-Jacobi preconditioner diag(K)."""
+    preconditioner; "separable_banded" -> the same with 7-band truncated factors (one fused
+    sweep per application); "jacobi" -> CG with the point-Jacobi preconditioner diag(K)."""
     if precond in (None, "none", PRECOND_NONE):
         return PRECOND_NONE
     if precond in ("separable", PRECOND_SEPARABLE):
         return PRECOND_SEPARABLE
     if precond in ("jacobi", PRECOND_JACOBI):
         return PRECOND_JACOBI
+    if precond in ("separable_banded", PRECOND_SEPARABLE_BANDED):
+        return PRECOND_SEPARABLE_BANDED
     raise ValueError(f"unknown preconditioner {precond!r}")
 
 

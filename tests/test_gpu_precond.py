@@ -182,3 +182,79 @@ def test_pcg_argument_checks():
     st, info = plan.solve(z, x, rtol=1e-6, precond="separable")
     assert st == tca.OK and info["iters"] == 0
     assert float(x.abs().max()) == 0.0
+
+
+BANDED_CASES = [
+    ("bspline", (20, 18, 16, 8), "f32"),    # the plain fused sweep applies M^-1 (n4 = 8, warp-specialised)
+    ("bspline", (33, 41, 30), "f32"),       # fused sweep, order 3
+    ("bspline", (23, 26, 21, 4), "f32"),    # fused sweep, n4 = 4
+    ("bspline", (12, 13, 11, 16), "f32"),   # band mode products (no fused sweep)
+    ("bspline", (17, 14, 19, 3), "f64"),    # FP64 band mode products
+]
+
+
+@pytest.mark.parametrize("kind,shape,prec", BANDED_CASES)
+def test_banded_pcg_iterates_match_oracle(kind, shape, prec):
+    """precond="separable_banded": the separable inverse factors cut to |i - j| <= 3, applied as one
+    fused sweep (or band products); iterates k = 1..7 against the oracle's pcg with
+    separable_inverse_factors(..., half_band=3) at the default shift."""
+    tca = lib()
+    dt = np.float32 if prec == "f32" else np.float64
+    tol = 1e-4 if prec == "f32" else 1e-10
+    inst = _inst(kind, shape, 770, 1e-3)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(dt)
+    plan = tca.plan_from_instance(inst, precision=prec)
+    rhs = O.apply_T(b.astype(np.float64), mats)
+    kop = lambda v: O.normal_apply(v, mats, inst.lam)
+    inv = O.separable_inverse_factors(mats, inst.lam, SHIFT, half_band=3)
+    minv = lambda r: O.apply_separable(r, inv)
+    for k in (1, 2, 3, 4, 5, 7):
+        x = empty_dev(inst.shape, dt)
+        st, info = plan.solve(to_dev(b, dt), x, rtol=1e-14, max_iter=k, raise_on_error=False,
+                              precond="separable_banded")
+        assert st == tca.ERR_NOT_CONVERGED and info["iters"] == k
+        ref = O.pcg(kop, minv, rhs, rtol=0.0, max_iter=k).x
+        assert rel_l2(x.cpu().numpy(), ref) < tol, k
+
+
+@pytest.mark.parametrize("shift", [16.0, 32.0])
+def test_banded_pcg_solves_in_fewer_iterations(shift):
+    tca = lib()
+    inst = synth.instance_bspline((40, 36, 32, 8), seed=780, dtype=np.float64)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-6, precond="separable_banded", precond_shift=shift)
+    assert st == tca.OK, info
+    assert O.rel_residual(x.cpu().numpy(), b.astype(np.float64), mats, inst.lam) <= 1.5e-6
+    x0 = empty_dev(inst.shape, np.float32)
+    st0, info0 = plan.solve(to_dev(b, np.float32), x0, rtol=1e-6)
+    assert info["iters"] * 2 < info0["iters"], (info["iters"], info0["iters"])
+    # Switching to the dense-factor form and back rebuilds graph and factors: same result.
+    x1 = empty_dev(inst.shape, np.float32)
+    plan.solve(to_dev(b, np.float32), x1, rtol=1e-6, precond="separable", precond_shift=shift)
+    x2 = empty_dev(inst.shape, np.float32)
+    st2, info2 = plan.solve(to_dev(b, np.float32), x2, rtol=1e-6, precond="separable_banded", precond_shift=shift)
+    assert info2["iters"] == info["iters"]
+    np.testing.assert_array_equal(x2.cpu().numpy(), x.cpu().numpy())
+
+
+def test_banded_pcg_batched_matches_single_solves():
+    tca = lib()
+    insts = [synth.instance_batched(2 * i + 1, lo=16, hi=28) for i in range(4)]  # B-spline instances
+    plans = [tca.plan_from_instance(inst, precision="f32") for inst in insts]
+    bs, xs = [], []
+    for inst in insts:
+        mats = [f.dense() for f in inst.factors]
+        bs.append(to_dev((O.apply(inst.x_true, mats) + inst.noise).astype(np.float32), np.float32))
+        xs.append(empty_dev(inst.shape, np.float32))
+    st, infos = tca.solve_batched(plans, bs, xs, rtol=1e-6, max_iter=5000, precond="separable_banded")
+    assert st == tca.OK
+    for i, (inst, plan) in enumerate(zip(insts, plans)):
+        mats = [f.dense() for f in inst.factors]
+        assert O.rel_residual(xs[i].cpu().numpy(), bs[i].cpu().numpy().astype(np.float64), mats, inst.lam) <= 1.5e-6
+        xr = empty_dev(inst.shape, np.float32)
+        st1, info1 = plan.solve(bs[i], xr, rtol=1e-6, max_iter=5000, precond="separable_banded")
+        assert st1 == tca.OK and abs(infos[i]["iters"] - info1["iters"]) <= 3
