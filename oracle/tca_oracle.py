@@ -43,6 +43,10 @@ Structured Problems with Computational Tensor Algebra"):
   products of the rows of the A_k (the row-wise, face-splitting product), and
   A^T A is a sum over samples of rank-1 tensor products.  Written out term by
   term over each sample's non-zero window.
+* ``tmg_prolongation`` / ``tmg_vcycle`` - a two-grid tensor multigrid cycle as a CG
+  preconditioner (Sec. 4.2, Fig. 3): separable linear-interpolation transfers (Table 1
+  upsampling and its transpose), Galerkin coarse operator, Chebyshev smoothing on the
+  Jacobi-scaled operator (the smoother is a reading: the paper names none).
 * ``kron_matrix`` / ``dense_normal_matrix`` / ``direct_solve`` - the
   equivalent matrix form of a tensor equation "with proper reshaping" (Sec. 3,
   after Eq. TensorEq), solved by a direct (Cholesky) method - the direct-solver
@@ -85,6 +89,8 @@ __all__ = [
     "scattered_normal_apply",
     "scattered_rows_matrix",
     "jacobi_diagonal",
+    "tmg_prolongation",
+    "tmg_vcycle",
 ]
 
 
@@ -390,6 +396,52 @@ def scattered_rows_matrix(col0s, ws, shape) -> np.ndarray:
             dense_rows.append(r)
         rows.append(functools.reduce(np.kron, dense_rows))
     return np.array(rows)
+
+
+def tmg_prolongation(n: int) -> np.ndarray:
+    """Linear interpolation from ceil(n / 2) coarse points (the even fine points) to n fine points:
+    the upsampling building block of Table 1; its transpose is the restriction."""
+    nc = (n + 1) // 2
+    p = np.zeros((n, nc))
+    for i in range(nc):
+        p[2 * i, i] = 1.0
+        if 2 * i + 1 < n:
+            p[2 * i + 1, i] += 0.5
+            if i + 1 < nc:
+                p[2 * i + 1, i + 1] += 0.5
+    return p
+
+
+def tmg_vcycle(r: np.ndarray, kop, diag: np.ndarray, prolongs, nu: int, lam_lo: float, lam_hi: float,
+               coarse_rtol: float = 1e-12) -> np.ndarray:
+    """One two-grid tensor multigrid cycle (Sec. 4.2, Fig. 3) as a CG preconditioner z = V r.
+
+    The transfers are separable (P = P_1 x ... x P_d, one one-dimensional interpolation per mode;
+    restriction = P^T), the coarse operator is Galerkin, K_c = P^T K P (applied matrix-free), and
+    the coarse system is solved to coarse_rtol by ``cg``.  Smoothing: nu steps of Chebyshev
+    iteration on D^-1 K (D = diag(K)) over the interval [lam_lo, lam_hi], before and after the
+    coarse correction (the same polynomial, so V is symmetric).
+    """
+    def smooth(z):
+        theta, delta = 0.5 * (lam_hi + lam_lo), 0.5 * (lam_hi - lam_lo)
+        res = r - kop(z)
+        d = res / diag / theta
+        z = z + d
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        for _ in range(nu - 1):
+            res = r - kop(z)
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            d = rho_new * rho * d + (2.0 * rho_new / delta) * (res / diag)
+            z = z + d
+            rho = rho_new
+        return z
+
+    z = smooth(np.zeros_like(r)) if nu > 0 else np.zeros_like(r)
+    rc = apply_T(r - kop(z), prolongs)
+    zc = cg(lambda v: apply_T(kop(apply(v, prolongs)), prolongs), rc, rtol=coarse_rtol, max_iter=100000).x
+    z = z + apply(zc, prolongs)
+    return smooth(z) if nu > 0 else z
 
 
 def kron_matrix(mats) -> np.ndarray:
