@@ -25,8 +25,9 @@ the solve's stream (one graph pass per launch, the host reading the events).
                             FP64 oracle on the 40x40x40x8 instance of the generator;
   batched                   64 uneven instances in one graph launch (plain,
                             separable and Jacobi), against one solve after another;
-  scattered                 a 64x64x64x4 grid with 0.27 random off-grid samples per
-                            unknown (the paper's 4D problem's ratio), FP64 CG;
+  scattered                 the paper's own 4D problem at its size: a 128x128x128x16
+                            grid (33.5M unknowns) with 9.06M random off-grid samples,
+                            FP32 and FP64 CG through sample space;
   learned                   the network initial guess trained on solver pairs,
                             evaluated on held-out 160x160x160x8 instances.
 """
@@ -312,53 +313,85 @@ def run_batched(args, device, emit=True):
     return out
 
 
-SCATTER_SHAPE = (64, 64, 64, 4)
-SCATTER_FRACTION = 0.27  # samples per unknown, the paper's 4D problem's ratio (~9M samples, 33.5M unknowns)
+# The paper's 4D spline reconstruction (Sec. 5): a 128 x 128 x 128 x 16 grid and about 9M
+# scattered measurements, solved there in under 60 minutes on a multicore PC (tolerance not stated).
+SCATTER_SHAPE = (128, 128, 128, 16)
+SCATTER_FRACTION = 0.27  # samples per unknown: 9.06M samples on that grid
 
 
-def run_scattered(args, device, emit=True):
+def run_scattered(args, device, emit=True, shape=None, precisions=("f32", "f64")):
     """Scattered-sample reconstruction: samples at random off-grid positions (0.27 per unknown, as
-    in the paper's 4D problem), cubic B-spline rows per mode, FP64 CG to 1e-6 through sample
-    space (gather + scatter-add per iteration)."""
-    import torch
+    in the paper's 4D problem), cubic B-spline rows per mode, CG to 1e-6 through sample space
+    (gather + scatter-add per iteration), for each precision (FP32: FP32 iterations with the
+    FP64 operator for A^T b and the true residual; FP64 throughout)."""
+    from paper_1001_5460_gb300 import synth
 
-    from paper_1001_5460_gb300 import synth, tca
-
-    n_unknowns = int(np.prod(SCATTER_SHAPE))
-    m = int(SCATTER_FRACTION * n_unknowns)
-    inst = synth.instance_scattered(SCATTER_SHAPE, m, seed=SEED, lam=LAM)
+    shape = tuple(shape or SCATTER_SHAPE)
+    m = int(SCATTER_FRACTION * int(np.prod(shape)))
     t0 = time.perf_counter()
-    plan = tca.ScatteredPlan(inst.shape, inst.col0, inst.w, lam=inst.lam)
-    plan_s = time.perf_counter() - t0
-    xt = torch.from_numpy(inst.x_true).to(device)
-    b = torch.empty(m, dtype=torch.float64, device=device)
-    plan.apply(xt, b)
-    b += torch.from_numpy(inst.noise).to(device)
-    x = torch.zeros(SCATTER_SHAPE, dtype=torch.float64, device=device)
-    s = torch.cuda.current_stream()
-    ms, info = timed_solve(plan, b, x, max(1, min(args.steps, 3)), s, max_iter=20000)
-    # One normal-operator application alone: gather, scatter-add, regulariser.
-    y = torch.empty_like(x)
-    for _ in range(3):
-        plan.apply_normal(x, y)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(10):
-        plan.apply_normal(x, y)
-    e1.record(s)
-    torch.cuda.synchronize()
-    k_ms = e0.elapsed_time(e1) / 10
-    taps = m * 4 ** len(SCATTER_SHAPE)
-    out = {"case": "scattered", "shape": list(SCATTER_SHAPE), "samples": m, "precision": "f64",
-           "ms": round(ms, 3), "cg_iters": info["iters"], "restarts": info["refinements"],
-           "rel_res_true": info["rel_res_true"], "plan_s": round(plan_s, 3),
-           "normal_apply_ms": round(k_ms, 4), "taps_per_s": round(2 * taps / k_ms / 1e6, 1),
+    inst = synth.instance_scattered(shape, m, seed=SEED, lam=LAM)
+    gen_s = time.perf_counter() - t0
+    out = {"case": "scattered", "shape": list(shape), "samples": m, "generate_s": round(gen_s, 1),
+           "paper_context": "Sec. 5: 128x128x128x16 unknowns, about 9M measurements, under 60 min on a "
+                            "multicore PC with 2 GB (tolerance not stated)",
            "what": "rows = Kronecker products of per-sample cubic B-spline rows; K applied through sample "
-                   "space (gather of 4^4 taps, scatter-add with FP64 atomics) + separable regulariser"}
-    plan.close()
+                   "space (samples grouped by grid tile; gather of 4^d taps from a shared-memory image of "
+                   "the tile's region, scatter-add into it with shared-memory atomics, one global atomic "
+                   "per region cell) + separable regulariser"}
+    b64 = None
+    for prec in precisions:
+        out[prec], b64 = _scattered_one(args, device, inst, shape, m, prec, b64)
     if emit:
         print(json.dumps(out), flush=True)
     return out
+
+
+def _scattered_one(args, device, inst, shape, m, prec, b64):
+    """One precision of the scattered case: the timed solves, then the normal operator, the
+    gather and the scatter-add alone (CUDA events), on the solution."""
+    import torch
+
+    from paper_1001_5460_gb300 import tca
+
+    dt = torch.float64 if prec == "f64" else torch.float32
+    t0 = time.perf_counter()
+    plan = tca.ScatteredPlan(inst.shape, inst.col0, inst.w, lam=inst.lam, precision=prec)
+    plan_s = time.perf_counter() - t0
+    if b64 is None:
+        # b = A x_true + noise by the FP64 gather (a plan of its own when this one is FP32)
+        gen = plan if prec == "f64" else tca.ScatteredPlan(inst.shape, inst.col0, inst.w, lam=inst.lam)
+        b64 = torch.empty(m, dtype=torch.float64, device=device)
+        gen.apply(torch.from_numpy(inst.x_true).to(device), b64)
+        b64 += torch.from_numpy(inst.noise).to(device)
+        if gen is not plan:
+            gen.close()
+    b = b64.to(dt)
+    x = torch.zeros(shape, dtype=dt, device=device)
+    s = torch.cuda.current_stream()
+    ms, info = timed_solve(plan, b, x, max(1, min(args.steps, 3)), s, max_iter=20000)
+    y = torch.empty_like(x)
+    ys = torch.empty(m, dtype=dt, device=device)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    k_ms = timed(lambda: plan.apply_normal(x, y))
+    g_ms = timed(lambda: plan.apply(x, ys))
+    t_ms = timed(lambda: plan.apply_T(ys, y))
+    taps = m * 4 ** len(shape)
+    plan.close()
+    return {"precision": prec, "ms": round(ms, 3), "cg_iters": info["iters"], "restarts": info["refinements"],
+            "rel_res_true": info["rel_res_true"], "plan_s": round(plan_s, 3),
+            "normal_apply_ms": round(k_ms, 4), "gather_ms": round(g_ms, 4), "scatter_ms": round(t_ms, 4),
+            "taps_per_s_G": round(2 * taps / k_ms / 1e6, 1)}, b64
 
 
 TRAIN_SHAPE = (64, 64, 64, 4)

@@ -144,11 +144,16 @@ TCA_API tca_status tca_plan(tca_plan_t* out, int order, const int64_t* n, const 
  * sample order in every mode) and n[k] columns, in host memory (copied).
  * The data tensor is a vector of m samples in that order.  A^T A is a sum of
  * rank-1 tensor products, not separable: tca_apply gathers each sample's
- * 4^d window, tca_apply_T scatters it back (FP64 atomic additions, so the
- * last bits of a sum may vary between runs), tca_apply_normal and the CG
+ * 4^d window, tca_apply_T scatters it back (atomic additions, so the last
+ * bits of a sum may vary between runs), tca_apply_normal and the CG
  * iterations of tca_solve go through sample space, and the regulariser is
- * the separable one of tca_plan.  prec must be TCA_F64
- * (TCA_ERR_UNSUPPORTED otherwise); no preconditioner, no tca_apply_mode, no
+ * the separable one of tca_plan.  The samples are grouped on the device by
+ * the grid tile that holds their window (the caller's order is kept at the
+ * boundary).  prec: TCA_F64 (FP64 data and arithmetic) or TCA_F32 (FP32
+ * data and arithmetic; tca_solve forms A^T b and checks the true residual
+ * with the FP64 operator, so its stopping test is FP64-accurate as for
+ * separable FP32 plans; the plan holds the weights in both precisions);
+ * TCA_ERR_UNSUPPORTED otherwise.  No preconditioner, no tca_apply_mode, no
  * batched solve.  Returns TCA_ERR_SHAPE if a factor's m or n does not match. */
 TCA_API tca_status tca_plan_scattered(tca_plan_t* out, int order, const int64_t* n, int64_t m,
                                       const tca_factor* rows, const tca_reg* reg, tca_precision prec,

@@ -328,6 +328,13 @@ __global__ void __launch_bounds__(kVecThreads) true_residual_kernel(const double
   }
 }
 
+// b = (Tout) a, element by element (FP32 -> FP64 widening is exact).
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin* __restrict__ a, Tout* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (Tout)a[i];
+}
+
 // Every element of x set to the bit pattern v.
 template <typename U>
 __global__ void fill_bits_kernel(U* __restrict__ x, U v, int64_t n) {
@@ -670,9 +677,24 @@ static tca_status get_graph(tca_plan_s* p, T* x, int iters, bool profile, cudaSt
 // FP64 true relative residual of x into p->scal->aux; optionally r = residual.
 // FP32 plans use double-float arithmetic on the FP32 pipes (residual_ff.cu);
 // FP64 plans use native FP64.
+// Scattered FP32 plans: the FP64 operator (gather, scatter-add, regulariser)
+// on the widened iterate, against A^T b kept in FP64.
 template <typename T>
 static tca_status true_residual(tca_plan_s* p, const T* x, bool write_r, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (p->scattered) {
+      TCA_TRY(ensure_ws64_public(p));
+      double* x64 = p->ws64[0];
+      convert_kernel<float, double><<<vector_grid(p, p->N), kVecThreads, 0, s>>>((const float*)x, x64, p->N);
+      TCA_LAUNCH_CHECK();
+      TCA_TRY(normal_generic<double>(p, x64, p->res64, s, nullptr));
+      const int grid = std::min(vector_grid(p, p->N), first_reduce(p).max_blocks - 1);
+      true_residual_kernel<float><<<grid, kVecThreads, 0, s>>>((const double*)p->rhs64, p->res64,
+                                                               write_r ? (float*)p->r : nullptr, p->N, p->scal,
+                                                               first_reduce(p), second_reduce(p));
+      TCA_LAUNCH_CHECK();
+      return TCA_OK;
+    }
     return residual_ff(p, (const float*)x, reinterpret_cast<const float2*>(p->rhs64),
                        reinterpret_cast<float2*>(p->res64), write_r ? (float*)p->r : nullptr, first_reduce(p),
                        second_reduce(p), s);
@@ -871,7 +893,24 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   if constexpr (sizeof(T) == 4) {
     TCA_TRY(ensure_ws64_public(p));
     tca_status up = TCA_ERR_UNSUPPORTED;
-    if (b_host) {
+    if (p->scattered) {
+      // Scattered samples: A^T b by the FP64 scatter-add of the widened b (kept
+      // in FP64 for the true residual), rounded once for the iteration.
+      if (b_host) {
+        TCA_CUDA_TRY(cudaMemcpyAsync(p->stage_b, b_host, sizeof(float) * (size_t)p->M, cudaMemcpyHostToDevice, s));
+        b_in = p->stage_b;
+      }
+      const int64_t M = p->M;
+      if (M > 0) {
+        convert_kernel<float, double><<<vector_grid(p, M), kVecThreads, 0, s>>>((const float*)b_in, p->sc_tmp, M);
+        TCA_LAUNCH_CHECK();
+      }
+      TCA_TRY(scattered_scatter<double>(p, p->sc_tmp, (double*)p->rhs64, true, s));
+      convert_kernel<double, float><<<vector_grid(p, N), kVecThreads, 0, s>>>((const double*)p->rhs64,
+                                                                               (float*)p->rhs, N);
+      TCA_LAUNCH_CHECK();
+      up = TCA_OK;
+    } else if (b_host) {
       // b from the host: uploaded in row runs under A^T b's first mode product.
       TCA_TRY(ensure_copy_stream(p));
       up = chain_ff_rhs_from_host(p, (const float*)b_host, (float*)p->stage_b, reinterpret_cast<float2*>(p->rhs64),
@@ -1294,7 +1333,7 @@ extern "C" tca_status tca_solve_batched(int count, tca_plan_t* plans, const void
   if (count <= 0 || !plans || !b || !x) return TCA_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     if (!plans[i] || !b[i] || !x[i]) return TCA_ERR_INVALID_ARG;
-    if (plans[i]->prec != TCA_F32) return TCA_ERR_UNSUPPORTED;
+    if (plans[i]->prec != TCA_F32 || plans[i]->scattered) return TCA_ERR_UNSUPPORTED;
     if (!is_device_ptr(b[i]) || !is_device_ptr(x[i]) || (uintptr_t)x[i] % 16 != 0) return TCA_ERR_UNSUPPORTED;
     for (int k = 0; k < i; ++k)
       if (plans[k] == plans[i]) return TCA_ERR_INVALID_ARG;  // each instance needs its own plan
@@ -1310,7 +1349,7 @@ extern "C" tca_status tca_autotune_batched(int count, tca_plan_t* plans, const v
   if (count <= 0 || !plans || !b || !x) return TCA_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     if (!plans[i] || !b[i] || !x[i]) return TCA_ERR_INVALID_ARG;
-    if (plans[i]->prec != TCA_F32) return TCA_ERR_UNSUPPORTED;
+    if (plans[i]->prec != TCA_F32 || plans[i]->scattered) return TCA_ERR_UNSUPPORTED;
     if (!is_device_ptr(b[i]) || !is_device_ptr(x[i]) || (uintptr_t)x[i] % 16 != 0) return TCA_ERR_UNSUPPORTED;
     for (int k = 0; k < i; ++k)
       if (plans[k] == plans[i]) return TCA_ERR_INVALID_ARG;

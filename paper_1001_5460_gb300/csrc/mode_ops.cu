@@ -421,10 +421,11 @@ template <typename Tin, typename Tout, typename Tc>
 tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, void* const* ws,
                        int64_t ws_elems, cudaStream_t s) {
   if (p->scattered) {
-    // Scattered samples: one gather (A x) or one scatter-add (A^T y), FP64 only.
-    if constexpr (sizeof(Tin) == 8 && sizeof(Tout) == 8) {
-      return transpose ? scattered_scatter(p, (const double*)x, (double*)y, true, s)
-                       : scattered_gather(p, (const double*)x, (double*)y, true, s);
+    // Scattered samples: one gather (A x) or one scatter-add (A^T y) in the plan's type.
+    if constexpr (sizeof(Tin) == sizeof(Tout)) {
+      using T = Tout;
+      return transpose ? scattered_scatter<T>(p, (const T*)x, (T*)y, true, s)
+                       : scattered_gather<T>(p, (const T*)x, (T*)y, true, s);
     }
     return TCA_ERR_UNSUPPORTED;
   }
@@ -462,13 +463,12 @@ tca_status normal_generic(tca_plan_s* p, const T* x, T* y, cudaStream_t s, const
   int64_t d4[kMaxModes];
   dims4_of(p, d4);
   if (p->scattered) {
-    // A^T (A x) through sample space, then lambda R x (and <x, y>) as for separable plans.
-    if constexpr (sizeof(T) == 8) {
-      TCA_TRY(scattered_gather(p, (const double*)x, p->sc_tmp, false, s));
-      TCA_TRY(scattered_scatter(p, p->sc_tmp, (double*)y, false, s));
-      return launch_reg_add_impl<T, T>(p, x, y, d4, 1, dot, s);
-    }
-    return TCA_ERR_UNSUPPORTED;
+    // A^T (A x) through sample space (grouped sample order), then lambda R x
+    // (and <x, y>) as for separable plans.
+    T* tmp = reinterpret_cast<T*>(p->sc_tmp);
+    TCA_TRY(scattered_gather<T>(p, x, tmp, false, s));
+    TCA_TRY(scattered_scatter<T>(p, tmp, y, false, s));
+    return launch_reg_add_impl<T, T>(p, x, y, d4, 1, dot, s);
   }
   const int d = p->d;
   const void* src = x;

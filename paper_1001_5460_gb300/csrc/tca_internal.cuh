@@ -189,14 +189,20 @@ struct tca_plan_s {
   cudaEvent_t chunk_ev[8] = {};
 
   tca::Bf16State bf;             // TCA_BF16_IR plans
-  // Scattered samples (tca_plan_scattered): sample rows sorted by their first
-  // window cell; M = sc_m.
+  // Scattered samples (tca_plan_scattered): sample rows grouped by the tile
+  // of the unknown grid that holds their window's anchor cell; M = sc_m.
   bool scattered = false;
   int64_t sc_m = 0;
-  int32_t* sc_col0 = nullptr;  // [k][s]
-  double* sc_w = nullptr;      // [k][s][4]
-  int32_t* sc_perm = nullptr;  // sorted position -> caller's sample index
-  double* sc_tmp = nullptr;    // sample-space vector of the normal operator
+  int32_t* sc_col0 = nullptr;        // [k][s]
+  double* sc_w = nullptr;            // [k][s][4] (every scattered plan: FP64 operators and true residual)
+  float* sc_w32 = nullptr;           // [k][s][4] (TCA_F32 plans)
+  int32_t* sc_perm = nullptr;        // grouped position -> caller's sample index
+  int32_t* sc_tile_start = nullptr;  // [tiles + 1]: first grouped sample of each tile
+  double* sc_tmp = nullptr;          // sample-space vector of the normal operator (m doubles)
+  int sc_ts[tca::kMaxModes] = {};    // tile extent per mode (anchor cells)
+  int sc_nt[tca::kMaxModes] = {};    // tiles per mode
+  int64_t sc_tiles = 0;
+  int64_t sc_region = 0;             // largest shared-memory region of a tile (elements)
   tca::Scalars* scal = nullptr;  // device
   tca::Scalars* scal_host = nullptr;  // pinned mirror
   tca::Reduce red;
@@ -350,9 +356,12 @@ tca_status bf16_flush(tca_plan_s* p, float* d, Reduce red, cudaStream_t s);
 tca_status prepare_sweep_timing(tca_plan_s* p, cudaStream_t s);
 
 // Scattered samples (scattered.cu): y = A x (gather) and x = A^T y (scatter-add,
-// x zeroed first); perm: y in the caller's sample order.
-tca_status scattered_gather(const tca_plan_s* p, const double* x, double* y, bool perm, cudaStream_t s);
-tca_status scattered_scatter(const tca_plan_s* p, const double* y, double* x, bool perm, cudaStream_t s);
+// x zeroed first); perm: y in the caller's sample order.  T = double on every
+// scattered plan, T = float on TCA_F32 plans.
+template <typename T>
+tca_status scattered_gather(const tca_plan_s* p, const T* x, T* y, bool perm, cudaStream_t s);
+template <typename T>
+tca_status scattered_scatter(const tca_plan_s* p, const T* y, T* x, bool perm, cudaStream_t s);
 void scattered_release(tca_plan_s* p);
 
 bool is_device_ptr(const void* ptr);
