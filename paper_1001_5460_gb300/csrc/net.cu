@@ -144,10 +144,24 @@ constexpr int kThreads = 128;
 // ---- 1 -> 32 channels ------------------------------------------------------
 // Forward (layer 1): out = relu(sum_t w[t][co] * in[v + off t] * in_scale + b).
 // Input gradient of layer 4 (MASK): out = (sum_t w4b[t][ci] g[v + off t]) * (h3 > 0).
-// Register blocking: a thread owns four consecutive voxels and half of the 32
-// channels (64 accumulators), so each tap costs four input loads and four
-// 128-bit weight loads for 64 FMAs.
-constexpr int kV1 = 4;  // voxels per thread
+// A job is 256 consecutive voxels of one row (z, y) of the volume (the
+// flattened (x, n) index, L = W B voxels).  Its nine input rows
+// (z + a - 1, y + b - 1) over those voxels and B voxels on each side (the x
+// neighbours) are copied into shared memory by cp.async, zeros off the
+// volume, one job ahead of the arithmetic (two buffers).  Thread t owns
+// voxels (t >> 1) + 64 u (u = 0..3) of the job and the channels
+// 16 (t & 1) .. + 15, so that for each u a warp's 16-byte stores cover
+// contiguous voxels.  Per channel the taps accumulate in tap order (bias, then
+// t = 0 .. 26; each input scaled as it is used), two channels per packed FMA.
+constexpr int kRowVox = 256;  // voxels of a row per job
+
+// Shared memory of the 1 -> 32 kernel for a 4th-mode extent B: two buffers of nine rows.
+size_t conv1to32_smem(int B) { return sizeof(float) * 2 * 9 * (size_t)(kRowVox + 2 * B); }
+
+__device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
 
 template <bool MASK>
 __global__ void __launch_bounds__(kThreads) conv1to32_kernel(const float* __restrict__ in,
@@ -155,55 +169,88 @@ __global__ void __launch_bounds__(kThreads) conv1to32_kernel(const float* __rest
                                                              const float* __restrict__ w, const float* __restrict__ bias,
                                                              const __nv_bfloat16* __restrict__ mask_src,
                                                              __nv_bfloat16* __restrict__ out, Dims d) {
+  static_assert(kThreads * 2 == kRowVox, "two threads per voxel column, four voxels each");
   __shared__ __align__(16) float sw[T * C];
   __shared__ float sb[C];
+  extern __shared__ float srow[];  // [2][9][kRowVox + 2 B]
   for (int i = threadIdx.x; i < T * C; i += blockDim.x) sw[i] = w[i];
   if (threadIdx.x < C) sb[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
-  __syncthreads();
   const float inv = scale_dev ? 1.f / *scale_dev : 1.f;
-  const int64_t nq = (d.V + kV1 - 1) / kV1;  // voxel quads
-  for (int64_t job = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; job < 2 * nq;
-       job += (int64_t)gridDim.x * blockDim.x) {
-    const int half = (int)(job & 1);  // channels 16 half .. 16 half + 15
-    const int64_t v0 = (job >> 1) * kV1;
-    unsigned m[kV1];
-#pragma unroll
-    for (int u = 0; u < kV1; ++u) {
-      m[u] = 0u;
-      if (v0 + u < d.V) {
-        int z, y, x;
-        decode(v0 + u, d, z, y, x);
-        m[u] = tap_mask(z, y, x, d);
+  const int L = d.W * d.B;
+  const int SW = kRowVox + 2 * d.B;
+  const int chunks = (L + kRowVox - 1) / kRowVox;
+  const int64_t jobs = (int64_t)d.D * d.H * chunks;
+  const int half = threadIdx.x & 1;
+  const int vl = threadIdx.x >> 1;
+  // Copies of job `job`'s nine rows into buffer `buf` (one commit group).
+  auto stage = [&](int64_t job, int buf) {
+    if (job < jobs) {
+      const int64_t row = job / chunks;
+      const int rb = (int)(job - row * chunks) * kRowVox;
+      const int z = (int)(row / d.H), y = (int)(row - (int64_t)z * d.H);
+      float* dst = srow + (size_t)buf * 9 * SW;
+      for (int ab = 0; ab < 9; ++ab) {
+        const int zz = z + ab / 3 - 1, yy = y + ab % 3 - 1;
+        const bool rok = zz >= 0 && zz < d.D && yy >= 0 && yy < d.H;
+        const float* base = in + (rok ? ((int64_t)zz * d.H + yy) * L : 0);
+        for (int k = threadIdx.x; k < SW; k += blockDim.x) {
+          const int rs = rb - d.B + k;
+          const bool ok = rok && (unsigned)rs < (unsigned)L;
+          cp_async4_zfill(dst + ab * SW + k, ok ? base + rs : in, ok);
+        }
       }
     }
-    float acc[kV1][16];
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int buf = 0;
+  stage(blockIdx.x, 0);
+  for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x, buf ^= 1) {
+    // The other buffer was last read by the previous job (every thread is past it).
+    __syncthreads();
+    stage(job + gridDim.x, buf ^ 1);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();  // this job's rows (and the weights) are in
+    const int64_t row = job / chunks;
+    const int rb = (int)(job - row * chunks) * kRowVox;
+    float2 acc[4][8];
 #pragma unroll
-    for (int u = 0; u < kV1; ++u)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc[u][c] = sb[16 * half + c];
-#pragma unroll 9
-    for (int t = 0; t < T; ++t) {
-      const int64_t off = tap_offset(t, d);
-      float val[kV1];
+      for (int c = 0; c < 8; ++c) acc[u][c] = make_float2(sb[16 * half + 2 * c], sb[16 * half + 2 * c + 1]);
+#pragma unroll 1
+    for (int ab = 0; ab < 9; ++ab) {
+      const float* sr = srow + ((size_t)buf * 9 + ab) * SW + vl;
 #pragma unroll
-      for (int u = 0; u < kV1; ++u) val[u] = (m[u] >> t & 1u) ? __ldg(in + v0 + u + off) * inv : 0.f;
-      const float4* w4 = reinterpret_cast<const float4*>(sw + t * C + 16 * half);
+      for (int e = 0; e < 3; ++e) {
+        const int t = 3 * ab + e;
+        float val[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 ww = w4[q];
+        for (int u = 0; u < 4; ++u) val[u] = sr[64 * u + e * d.B] * inv;
+        const float4* w4 = reinterpret_cast<const float4*>(sw + t * C + 16 * half);
 #pragma unroll
-        for (int u = 0; u < kV1; ++u) {
-          acc[u][4 * q + 0] = fmaf(ww.x, val[u], acc[u][4 * q + 0]);
-          acc[u][4 * q + 1] = fmaf(ww.y, val[u], acc[u][4 * q + 1]);
-          acc[u][4 * q + 2] = fmaf(ww.z, val[u], acc[u][4 * q + 2]);
-          acc[u][4 * q + 3] = fmaf(ww.w, val[u], acc[u][4 * q + 3]);
+        for (int q = 0; q < 4; ++q) {
+          const float4 ww = w4[q];
+          const float2 w01 = make_float2(ww.x, ww.y), w23 = make_float2(ww.z, ww.w);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 v2 = make_float2(val[u], val[u]);
+            acc[u][2 * q] = __ffma2_rn(w01, v2, acc[u][2 * q]);
+            acc[u][2 * q + 1] = __ffma2_rn(w23, v2, acc[u][2 * q + 1]);
+          }
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < kV1; ++u) {
-      if (v0 + u >= d.V) break;
-      const int64_t v = v0 + u;
+    for (int u = 0; u < 4; ++u) {
+      const int r = rb + vl + 64 * u;
+      if (r >= L) continue;
+      const int64_t v = row * L + r;
+      float a[16];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        a[2 * c] = acc[u][c].x;
+        a[2 * c + 1] = acc[u][c].y;
+      }
       if constexpr (MASK) {
         const uint4* hs = reinterpret_cast<const uint4*>(mask_src + v * C + 16 * half);
 #pragma unroll
@@ -211,27 +258,28 @@ __global__ void __launch_bounds__(kThreads) conv1to32_kernel(const float* __rest
           const uint4 hw = __ldg(hs + q);
           const uint32_t hv[4] = {hw.x, hw.y, hw.z, hw.w};
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            if (!(bf_lo(hv[r]) > 0.f)) acc[u][8 * q + 2 * r] = 0.f;
-            if (!(bf_hi(hv[r]) > 0.f)) acc[u][8 * q + 2 * r + 1] = 0.f;
+          for (int k = 0; k < 4; ++k) {
+            if (!(bf_lo(hv[k]) > 0.f)) a[8 * q + 2 * k] = 0.f;
+            if (!(bf_hi(hv[k]) > 0.f)) a[8 * q + 2 * k + 1] = 0.f;
           }
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[u][c] = fmaxf(acc[u][c], 0.f);
+        for (int c = 0; c < 16; ++c) a[c] = fmaxf(a[c], 0.f);
       }
       uint4* dst = reinterpret_cast<uint4*>(out + v * C + 16 * half);
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         uint4 o;
-        o.x = pack2(acc[u][8 * q + 0], acc[u][8 * q + 1]);
-        o.y = pack2(acc[u][8 * q + 2], acc[u][8 * q + 3]);
-        o.z = pack2(acc[u][8 * q + 4], acc[u][8 * q + 5]);
-        o.w = pack2(acc[u][8 * q + 6], acc[u][8 * q + 7]);
+        o.x = pack2(a[8 * q + 0], a[8 * q + 1]);
+        o.y = pack2(a[8 * q + 2], a[8 * q + 3]);
+        o.z = pack2(a[8 * q + 4], a[8 * q + 5]);
+        o.w = pack2(a[8 * q + 6], a[8 * q + 7]);
         dst[q] = o;
       }
     }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // ---- 32 -> 1 channel (layer 4 forward) ---------------------------------------
@@ -951,6 +999,31 @@ int grid_for(const tca_net_s* n, int64_t V, int per_sm) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)n->num_sms * per_sm));
 }
 
+// Launch of the row-structured 1 -> 32 kernel: one job per 256 voxels of a row.
+template <bool MASK>
+tca_status launch_1to32(const tca_net_s* n, const float* in, const float* scale, const float* w, const float* bias,
+                        const __nv_bfloat16* mask, __nv_bfloat16* out, const Dims& d, cudaStream_t s) {
+  const size_t smem = conv1to32_smem(d.B);
+  if (smem > 160 * 1024) {
+    set_error_message("network: the fourth mode is too long for the first layer's row tiles");
+    return TCA_ERR_UNSUPPORTED;
+  }
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(conv1to32_kernel<MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return TCA_ERR_CUDA;
+    }
+  }
+  const int64_t L = (int64_t)d.W * d.B;
+  const int64_t jobs = (int64_t)d.D * d.H * ((L + kRowVox - 1) / kRowVox);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(jobs, (int64_t)n->num_sms * 8));
+  conv1to32_kernel<MASK><<<grid, kThreads, smem, s>>>(in, scale, w, bias, mask, out, d);
+  TCA_LAUNCH_CHECK();
+  return TCA_OK;
+}
+
 tca_status prep(tca_net_s* n, cudaStream_t s) {
   prep_kernel<<<(T * C * C + 255) / 256, 256, 0, s>>>(n->params, n->dw);
   TCA_LAUNCH_CHECK();
@@ -1026,9 +1099,7 @@ tca_status conv32(tca_net_s* n, const __nv_bfloat16* in, const __nv_bfloat16* w,
 // Forward pass into n->h[0..2] and y (y = s Net(u / s) when scaled).
 tca_status forward(tca_net_s* n, const float* u, float* y, const Dims& d, bool scaled, cudaStream_t s) {
   const int grid = grid_for(n, d.V, 8);
-  conv1to32_kernel<false><<<grid, kThreads, 0, s>>>(u, scaled ? n->scale : nullptr, DW(n, w1f), DW(n, b1), nullptr,
-                                                     n->h[0], d);
-  TCA_LAUNCH_CHECK();
+  TCA_TRY(launch_1to32<false>(n, u, scaled ? n->scale : nullptr, DW(n, w1f), DW(n, b1), nullptr, n->h[0], d, s));
   TCA_TRY(conv32(n, n->h[0], DW(n, w2f), DW(n, w2f_tc), DW(n, b2), nullptr, n->h[1], d, s));
   TCA_TRY(conv32(n, n->h[1], DW(n, w3f), DW(n, w3f_tc), DW(n, b3), nullptr, n->h[2], d, s));
   if (tc_supported(d) && !n->force_cuda_cores) {
@@ -1166,9 +1237,7 @@ extern "C" tca_status tca_net_accumulate(tca_net_t n, const int64_t* dims, const
   TCA_LAUNCH_CHECK();
   // Layer 4: dW4 from g and h3; input gradient dh3 = conv(g, W4 flipped) masked by h3 > 0.
   TCA_TRY((wgrad<1, C>(n, n->g, n->h[2], d, 1, C, kW4, kB4, s)));
-  const int grid = grid_for(n, d.V, 8);
-  conv1to32_kernel<true><<<grid, kThreads, 0, s>>>(n->g, nullptr, DW(n, w4b), nullptr, n->h[2], n->gbuf[0], d);
-  TCA_LAUNCH_CHECK();
+  TCA_TRY(launch_1to32<true>(n, n->g, nullptr, DW(n, w4b), nullptr, n->h[2], n->gbuf[0], d, s));
   // Layer 3: dW3 from dz3 = gbuf[0] and h2; dh2 = conv(dz3, W3^T flipped) masked by h2 > 0.
   TCA_TRY((wgrad<C, C>(n, n->gbuf[0], n->h[1], d, C, C, kW3, kB3, s)));
   TCA_TRY(conv32(n, n->gbuf[0], DW(n, w3b), DW(n, w3b_tc), nullptr, n->h[1], n->gbuf[1], d, s));
