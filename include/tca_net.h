@@ -5,8 +5,8 @@
  * has no learned component; this part of the library adds one around that
  * method.  A small 3D convolutional network, trained on (right-hand side,
  * solution) pairs that the CG solver itself produces, maps A^T b to an
- * initial guess x0; CG then runs from x0 and stays the judge of the error (it
- * stops on the same true relative residual as tca_solve).
+ * initial guess x0; CG then runs from x0 and still decides when the error is
+ * small enough (it stops on the same true relative residual as tca_solve).
  *
  * Network (4 layers, 3x3x3 kernels, 32 channels, ReLU):
  *   h1 = relu(conv(u, W1) + b1)    1 -> 32
@@ -80,7 +80,7 @@ TCA_API tca_status tca_net_adam(tca_net_t net, float lr, float beta1, float beta
  * the network is also applied as a preconditioner step: after every
  * net_every CG iterations that did not converge, x += s' Net(r / s') with r
  * the true residual A^T b - K x and s' its RMS, and CG restarts from x.  CG
- * stays the judge of the error: the solve stops on the same true relative
+ * still decides when the error is small enough: the solve stops on the same true relative
  * residual as tca_solve.  info->iters counts all CG iterations,
  * info->refinements the preconditioner steps.  The plan must be FP32 or an
  * _IR precision, of order 3 (B = 1) or 4.  b and x: device pointers.

@@ -957,8 +957,8 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
     TCA_TRY(cg_iterate(p, rtol, max_iter, every, profile, &sweep_ms, &sweep_n, s));
     TCA_TRY(flush_pending_x<T>(p, x, s));
     if (x_host) {
-      // x is final for this round: copy it to the host on a side stream while
-      // the true residual is computed (a restart re-copies after its round).
+      // x is final for this pass: copy it to the host on a side stream while
+      // the true residual is computed (a restart re-copies after its pass).
       TCA_TRY(ensure_copy_stream(p));
       TCA_CUDA_TRY(cudaEventRecord(p->copy_ev, s));
       TCA_CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->copy_ev, 0));
