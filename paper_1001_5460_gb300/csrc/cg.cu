@@ -185,17 +185,42 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(const T* __restri
   double a_rr = 0.0, a_bb = 0.0;
   T p_rr = T(0), p_bb = T(0);  // short runs in T, FP64 beyond (the FP64 pipe is the slow one)
   int cnt = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T b = rhs[i];
-    const T v = kx ? (T)(b - kx[i]) : b;
-    r[i] = v;
-    p_rr += v * v;
-    p_bb += b * b;
-    if (++cnt == 16) {
+  // 16-byte vectors (the buffers are allocation-aligned), the scalar tail by block 0.
+  using VT = typename V2<T>::t;
+  constexpr int VN = V2<T>::n;
+  const int64_t nv = n / VN;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const VT bv = reinterpret_cast<const VT*>(rhs)[i];
+    VT vv = bv;
+    if (kx) {
+      const VT kv = reinterpret_cast<const VT*>(kx)[i];
+      T* vs = reinterpret_cast<T*>(&vv);
+      const T* ks = reinterpret_cast<const T*>(&kv);
+#pragma unroll
+      for (int c = 0; c < VN; ++c) vs[c] = (T)(vs[c] - ks[c]);
+    }
+    reinterpret_cast<VT*>(r)[i] = vv;
+    const T* vs = reinterpret_cast<const T*>(&vv);
+    const T* bs = reinterpret_cast<const T*>(&bv);
+#pragma unroll
+    for (int c = 0; c < VN; ++c) {
+      p_rr += vs[c] * vs[c];
+      p_bb += bs[c] * bs[c];
+    }
+    if (++cnt == 16 / VN) {
       a_rr += (double)p_rr;
       a_bb += (double)p_bb;
       p_rr = p_bb = T(0);
       cnt = 0;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) {
+      const T b = rhs[i];
+      const T v = kx ? (T)(b - kx[i]) : b;
+      r[i] = v;
+      p_rr += v * v;
+      p_bb += b * b;
     }
   }
   a_rr += (double)p_rr;
