@@ -494,7 +494,10 @@ tca_status scattered_attach(tca_plan_s* p, int64_t m, const tca_factor* rows) {
   for (int64_t s = 0; s < m; ++s) {
     const int64_t src = perm[(size_t)s];
     for (int k = 0; k < d; ++k) {
-      c0[(size_t)(k * m + s)] = rows[k].col0[src];
+      // A window that starts at or below -4, or at or past n, has no tap in the
+      // grid: clamping its start to [-4, n] changes nothing and keeps every
+      // index the kernels form from it small.
+      c0[(size_t)(k * m + s)] = (int32_t)std::min<int64_t>(std::max<int64_t>(rows[k].col0[src], -4), p->n[k]);
       for (int a = 0; a < 4; ++a) w[(size_t)((k * m + s) * 4 + a)] = rows[k].values[src * 4 + a];
     }
   }

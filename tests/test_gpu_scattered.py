@@ -65,17 +65,21 @@ def test_scattered_operators_match_oracle(shape, m, prec, dt, tol):
 @pytest.mark.parametrize("shape", [(23, 19, 30, 6), (41, 9, 27)])
 def test_scattered_rows_with_windows_outside_the_grid(shape, prec, dt, tol):
     """General ELL-4 rows: random weights, first columns from far below 0 to past the last
-    column (windows partly or wholly outside the grid, whose taps are dropped)."""
+    column and at the ends of the int32 range (windows partly or wholly outside the grid,
+    whose taps are dropped)."""
     tca = lib()
     rng = np.random.default_rng(sum(shape))
     m = 5000
     col0 = [rng.integers(-6, n + 3, size=m).astype(np.int32) for n in shape]
+    for c in col0:  # and first columns at the ends of the int32 range
+        c[:4] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, -(10 ** 9), 10 ** 9]
     w = [rng.standard_normal((m, 4)) for _ in shape]
     plan = tca.ScatteredPlan(shape, col0, w, lam=2e-3, precision=prec)
     _, ax = _check_operators(tca, plan, col0, w, shape, 2e-3, dt, tol, seed=9)
     # A sample whose window misses the grid in some mode has A x = 0 exactly.
     outside = np.zeros(m, dtype=bool)
     for c, n in zip(col0, shape):
+        c = c.astype(np.int64)
         outside |= (c + 3 < 0) | (c >= n)
     assert outside.any() and np.all(ax.cpu().numpy()[outside] == 0.0)
 
