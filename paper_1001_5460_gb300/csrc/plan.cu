@@ -166,6 +166,12 @@ static tca_status ingest_mode(tca_plan_s* p, int k, const tca_factor& f, bool re
     std::vector<int32_t> c0(f.col0, f.col0 + m);
     for (int64_t r = 0; r < m; ++r) {
       if (r > 0 && c0[r] < c0[r - 1]) return TCA_ERR_INVALID_ARG;  // must be non-decreasing
+    }
+    for (int64_t r = 0; r < m; ++r) {
+      // A row whose window starts at or below -4, or at or past n, has no column in
+      // the grid: clamping its start to [-4, n] keeps the order and every index
+      // the kernels form from it small.
+      c0[r] = (int32_t)std::min<int64_t>(std::max<int64_t>(c0[r], -4), n);
       for (int c = 0; c < 4; ++c) {
         const int64_t col = (int64_t)c0[r] + c;
         w[r * 4 + c] = (col >= 0 && col < n) ? f.values[r * 4 + c] : 0.0;

@@ -139,3 +139,33 @@ def test_dft_along_one_mode_as_two_real_factors(axis):
     ref = np.fft.fft(x.astype(np.float64), axis=axis)
     assert rel_l2(parts[0], ref.real) < TOL_F32
     assert rel_l2(parts[1], ref.imag) < TOL_F32
+
+
+@pytest.mark.parametrize("prec,dt,tol", [("f32", np.float32, TOL_F32), ("f64", np.float64, 1e-12)])
+def test_ell4_rows_starting_far_outside_the_grid(prec, dt, tol):
+    """An ELL-4 factor whose first and last rows start at the ends of the int32 range (no column
+    of theirs is in the grid) and whose other rows start anywhere from below 0 to past the last
+    column: the operator equals the dense matrix with those weights dropped."""
+    tca = lib()
+    shape = (20, 17, 12, 4)
+    rng = np.random.default_rng(31)
+    n = shape[0]
+    m = 30
+    mid = np.sort(rng.integers(-6, n + 3, size=m - 6))
+    col0 = np.concatenate([[np.iinfo(np.int32).min] * 3, mid, [np.iinfo(np.int32).max] * 3]).astype(np.int32)
+    w = rng.standard_normal((m, 4))
+    facs = [tca.Factor(tca.FACTOR_ELL4, m, n, w, col0)] + [_identity(tca, k) for k in shape[1:]]
+    lam = 3e-3
+    plan = tca.Plan(shape, facs, lam=lam, precision=prec)
+    mats = [synth.ell4_to_dense(col0, w, n)] + [np.eye(k) for k in shape[1:]]
+    x = rng.standard_normal(shape).astype(dt)
+    y = rng.standard_normal((m,) + shape[1:]).astype(dt)
+    ax = empty_dev((m,) + shape[1:], dt)
+    plan.apply(to_dev(x, dt), ax)
+    assert rel_l2(ax.cpu().numpy(), O.apply(x.astype(np.float64), mats)) < tol
+    aty = empty_dev(shape, dt)
+    plan.apply_T(to_dev(y, dt), aty)
+    assert rel_l2(aty.cpu().numpy(), O.apply_T(y.astype(np.float64), mats)) < tol
+    kx = empty_dev(shape, dt)
+    plan.apply_normal(to_dev(x, dt), kx)
+    assert rel_l2(kx.cpu().numpy(), O.normal_apply(x.astype(np.float64), mats, lam)) < tol
