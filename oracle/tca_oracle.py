@@ -43,6 +43,11 @@ Structured Problems with Computational Tensor Algebra"):
   products of the rows of the A_k (the row-wise, face-splitting product), and
   A^T A is a sum over samples of rank-1 tensor products.  Written out term by
   term over each sample's non-zero window.
+* ``corner_model_shift`` - the shift s of that preconditioner from a model of the
+  spectrum of M^-1 K (a reading: the paper fixes no preconditioner): each mode
+  either at its smooth corner (Gram at its top eigenvalue, regulariser at zero)
+  or at its rough corner (Gram at its bottom eigenvalue, regulariser at its
+  top), and s minimises the spread max/min of K/M over the 2^d corners.
 * ``tmg_prolongation`` / ``tmg_vcycle`` - a two-grid tensor multigrid cycle as a CG
   preconditioner (Sec. 4.2, Fig. 3): separable linear-interpolation transfers (Table 1
   upsampling and its transpose), Galerkin coarse operator, Chebyshev smoothing on the
@@ -89,6 +94,7 @@ __all__ = [
     "scattered_normal_apply",
     "scattered_rows_matrix",
     "jacobi_diagonal",
+    "corner_model_shift",
     "tmg_prolongation",
     "tmg_vcycle",
 ]
@@ -237,6 +243,43 @@ def separable_inverse_factors(mats, lam: float, shift: float, half_band: int | N
             inv = np.where(np.abs(idx[:, None] - idx[None, :]) <= half_band, inv, 0.0)
         out.append(inv)
     return out
+
+
+def corner_model_shift(mats, lam: float, steps: int = 16) -> float:
+    """The shift s of M = (x)_k (G_k + s lam L_k) (``separable_inverse_factors``) chosen on the
+    grid s = 2^(j/2), j = 0 .. steps, from a corner model of the spectrum of M^-1 K.
+
+    Mode k contributes one of two corners: (g_max, 0), its Gram G_k = A_k^T A_k at its top
+    eigenvalue and the regulariser at zero (smooth components), or (g_min, lam l_max), the
+    Gram at its bottom eigenvalue and lam L_k = lam D2^T D2 at its top (rough components; a
+    mode with n_k < 3 has l_max = 0).  At a corner c the operator K = (x)G_k + lam sum L_k
+    is modelled by prod g + sum l and M by prod (g + s l); s minimises
+    max_c (K_c / M_c) / min_c (K_c / M_c) (the first grid point of the minimum; corners with
+    M_c = 0 are left out).
+    """
+    corners = []
+    for a in mats:
+        a = np.asarray(a, dtype=np.float64)
+        n = a.shape[1]
+        g = np.linalg.eigvalsh(a.T @ a)
+        l_max = 0.0
+        if n >= 3:
+            d2 = second_difference(n)
+            l_max = float(np.linalg.eigvalsh(d2.T @ d2)[-1])
+        corners.append(((float(g[-1]), 0.0), (float(g[0]), lam * l_max)))
+    best_s, best_k = 1.0, None
+    for j in range(steps + 1):
+        shift = 2.0 ** (j / 2)
+        ratios = []
+        for c in itertools.product(*corners):
+            k_c = float(np.prod([g for g, _ in c])) + sum(l for _, l in c)
+            m_c = float(np.prod([g + shift * l for g, l in c]))
+            if m_c > 0.0:
+                ratios.append(k_c / m_c)
+        spread = max(ratios) / min(ratios)
+        if best_k is None or spread < best_k:
+            best_s, best_k = shift, spread
+    return best_s
 
 
 def jacobi_diagonal(mats, lam: float, shape) -> np.ndarray:

@@ -613,3 +613,40 @@ def test_tmg_vcycle_is_symmetric_positive_and_preconditions():
     assert pc.converged
     np.testing.assert_allclose(pc.x, ref, rtol=1e-7, atol=1e-8)
     assert pc.iters < plain.iters, (pc.iters, plain.iters)
+
+
+# ---- corner model of the preconditioner's shift ------------------------------------
+
+def test_corner_model_shift_special_cases():
+    """One mode: every corner's ratio K/M is 1 at s = 1, the first grid point; lambda = 0: K = M at
+    every corner for every s, so the first grid point again."""
+    rng = np.random.default_rng(40)
+    a = rng.standard_normal((9, 7))
+    assert O.corner_model_shift([a], 1e-2) == 1.0
+    mats = [rng.standard_normal((m, n)) for m, n in ((8, 6), (7, 5), (9, 4))]
+    assert O.corner_model_shift(mats, 0.0) == 1.0
+
+
+def _pcg_iters(mats, lam, shift, rhs):
+    f = O.separable_inverse_factors(mats, lam, shift)
+    res = O.pcg(lambda v: O.normal_apply(v, mats, lam), lambda r: O.apply_separable(r, f), rhs, rtol=1e-6,
+                max_iter=4000)
+    assert res.converged
+    return res.iters
+
+
+@pytest.mark.parametrize("kind,lam", [("bspline", 1e-4), ("bspline", 1e-3), ("bspline", 1e-2), ("dense", 1e-3)])
+def test_corner_model_shift_is_near_the_best_shift(kind, lam):
+    """The model's shift takes at most two PCG iterations more than the best shift of the grid
+    s = 1, 2, 4, .. 256 (oracle PCG to 1e-6), on B-spline instances over two decades of lambda
+    (the best shift moves from 8 to 128 there) and on a dense instance."""
+    if kind == "bspline":
+        inst = synth.instance_bspline((16, 16, 16, 4), seed=3, lam=lam)
+    else:
+        inst = synth.instance_dense_3d(seed=1, n=12, m=18, lam=lam)
+    mats = [f.dense() for f in inst.factors]
+    b = O.apply(inst.x_true, mats) + inst.noise.reshape(tuple(m.shape[0] for m in mats))
+    rhs = O.apply_T(b, mats)
+    s_model = O.corner_model_shift(mats, lam)
+    best = min(_pcg_iters(mats, lam, 2.0 ** j, rhs) for j in range(9))
+    assert _pcg_iters(mats, lam, s_model, rhs) <= best + 2
