@@ -17,7 +17,8 @@ each timed one: the same solve with every CG sweep bracketed by CUDA events on
 the solve's stream (one graph pass per launch, the host reading the events).
 ``variants`` (after the plain timing, same workload unless stated):
   separable_pcg_s16 / _s32  the separable tensor-inverse preconditioner;
-  separable_banded_pcg_*    the same with 7-band truncated factors (one fused sweep);
+  separable_banded_pcg_*    the same with 7-band truncated factors (one fused sweep),
+                            at s = 16, 32 and at the plan's corner-model default;
   jacobi_pcg                point Jacobi, M = diag(K);
   bf16_ir                   the bfloat16 mixed-precision form (tensor-core sweep,
                             double-float refinement), autotuned, with its sweep's
@@ -863,7 +864,8 @@ def run_tca(args, rank, world, local):
     # `value` stays the plain CG of Fig. 2.
     variants = {}
     for kind, shift in (() if args.no_variants else (("separable", 16.0), ("separable", 32.0),
-                                                      ("separable_banded", 16.0), ("separable_banded", 32.0))):
+                                                      ("separable_banded", 16.0), ("separable_banded", 32.0),
+                                                      ("separable_banded", 0.0))):
         plan.solve(b, x, rtol=RTOL, precond=kind, precond_shift=shift)
         torch.cuda.synchronize()
         pc_times, pc_info = [], None
@@ -877,11 +879,14 @@ def run_tca(args, rank, world, local):
         pc_ms = max_over_ranks(statistics.mean(pc_times), world)
         how = ("dense TF32 mode products on the tensor cores" if kind == "separable" else
                "each factor cut to its 7 central diagonals, applied as one plain fused sweep")
-        variants[f"{kind}_pcg_s{int(shift)}"] = {
+        used = shift if shift > 0 else plan.precond_default_shift()
+        name = f"{kind}_pcg_s{int(shift)}" if shift > 0 else f"{kind}_pcg_default_shift"
+        variants[name] = {
             "ms": round(pc_ms, 3), "cg_iters": pc_info["iters"], "restarts": pc_info["refinements"],
-            "rel_res_true": pc_info["rel_res_true"], "shift": shift,
-            "what": f"CG preconditioned by the separable tensor inverse (x)_k (G_k + {int(shift)} lambda L_k)^-1 "
-                    f"({how}), same tolerance on the FP64 true residual"}
+            "rel_res_true": pc_info["rel_res_true"], "shift": used,
+            "what": f"CG preconditioned by the separable tensor inverse (x)_k (G_k + s lambda L_k)^-1, s = {used:g}"
+                    + (" (the plan's corner-model default)" if shift <= 0 else "")
+                    + f" ({how}), same tolerance on the FP64 true residual"}
 
     peaks, peak_src = measured_peaks()
     if not args.no_variants:

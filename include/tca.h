@@ -197,11 +197,10 @@ typedef struct {
                            Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d);
                            TCA_PRECOND_JACOBI: M = diag(K); TCA_PRECOND_SEPARABLE_BANDED: the
                            separable inverse cut to 7-band factors (see below) */
-  double precond_shift; /* s, the regulariser weight folded into each mode of M (0: 16).  The best s
-                           depends on lambda and the factors (s = 32 beats 16 for the B-spline
-                           workload at lambda = 1e-3 and loses for lambda above ~4e-3); 16 is a
-                           middle value tuned for no problem in particular: pass s when the
-                           problem is known. */
+  double precond_shift; /* s, the regulariser weight folded into each mode of M (0: the plan's
+                           tca_precond_default_shift).  The best s depends on lambda and the
+                           factors (32 for the B-spline workload at lambda = 1e-3, 128 at 1e-4,
+                           8 at 1e-2). */
 } tca_solve_opts;
 
 /* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_SEPARABLE_BANDED
@@ -270,6 +269,20 @@ typedef struct {
  * selects the optional preconditioner (TCA_PRECOND_* above).  info may be NULL.  Synchronises the stream. */
 TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_solve_opts* opts,
                      tca_solve_info* info, cudaStream_t stream);
+
+/* The shift s that the separable preconditioners take when
+ * tca_solve_opts.precond_shift is 0, from a model of the spectrum of M^-1 K
+ * (the paper fixes no preconditioner; this is a heuristic of this library):
+ * each mode k either at its smooth corner (G_k at its largest eigenvalue, the
+ * regulariser at zero) or at its rough corner (G_k at its smallest eigenvalue,
+ * lambda L_k at its largest); at a corner K is taken as prod g + sum l and M as
+ * prod (g + s l), and s, on the grid 2^(j/2) for j = 0 .. 16 (1 to 256),
+ * minimises max / min of K / M over the 2^d corners.  The eigenvalues come from
+ * host copies of the plan's FP64 bands (Jacobi rotations); formed on the first
+ * call and kept with the plan.  Modes longer than 512 are not modelled: 16.
+ * Synchronises the device (copies of the bands).  TCA_ERR_UNSUPPORTED for
+ * scattered-sample plans. */
+TCA_API tca_status tca_precond_default_shift(tca_plan_t plan, double* shift);
 
 /* Solve `count` independent systems (A_i^T A_i + lambda_i R_i) x_i = A_i^T b_i,
  * each by the CG of Sec. 4.1, Fig. 2, in one CUDA graph launch.  Many small

@@ -427,9 +427,8 @@ static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
 }
 
 // The preconditioner a solve asks for: validates the options, builds the
-// factors for the shift (default 16) and marks the plan's iteration as
-// preconditioned (or not).
-constexpr double kDefaultPrecondShift = 16.0;
+// factors for the shift (by default the plan's corner-model shift) and marks
+// the plan's iteration as preconditioned (or not).
 static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
   p->pc_on = false;
   p->pc_kind = TCA_PRECOND_NONE;
@@ -444,7 +443,8 @@ static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
   } else {
     if ((kind != TCA_PRECOND_SEPARABLE && kind != TCA_PRECOND_SEPARABLE_BANDED) || o->precond_shift < 0.0)
       return TCA_ERR_INVALID_ARG;
-    const double shift = o->precond_shift > 0.0 ? o->precond_shift : kDefaultPrecondShift;
+    double shift = o->precond_shift;
+    if (!(shift > 0.0)) TCA_TRY(precond_model_shift(p, &shift));
     if (kind == TCA_PRECOND_SEPARABLE) TCA_TRY(ensure_precond(p, shift));
     else TCA_TRY(ensure_precond_banded(p, shift));
   }

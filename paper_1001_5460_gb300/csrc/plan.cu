@@ -344,6 +344,143 @@ static bool spd_inverse(std::vector<double>& a, int64_t n) {
   return true;
 }
 
+// G_k and lambda L_k of mode k as dense n x n FP64 matrices on the host, from
+// the plan's FP64 Gram and regulariser bands.
+static tca_status mode_dense_host(const tca_plan_s* p, int k, std::vector<double>& a, std::vector<double>& lap) {
+  const Mode& md = p->mode[k];
+  const int64_t n = md.n;
+  a.assign((size_t)(n * n), 0.0);
+  lap.assign((size_t)(n * n), 0.0);
+  if (md.gram.kind == OP_DENSE) {
+    TCA_CUDA_TRY(cudaMemcpy(a.data(), md.gram.dense.a64, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+  } else {
+    const Band& gb = md.gram.band;
+    std::vector<double> g((size_t)(n * gb.W));
+    std::vector<int32_t> st((size_t)n);
+    TCA_CUDA_TRY(cudaMemcpy(g.data(), gb.w64, sizeof(double) * n * gb.W, cudaMemcpyDeviceToHost));
+    TCA_CUDA_TRY(cudaMemcpy(st.data(), gb.start, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i)
+      for (int e = 0; e < gb.W; ++e) {
+        const int64_t c = (int64_t)st[i] + e;
+        if (c >= 0 && c < n) a[i * n + c] += g[i * gb.W + e];
+      }
+  }
+  const Band& lb = md.lap;
+  std::vector<double> l((size_t)(n * lb.W));
+  TCA_CUDA_TRY(cudaMemcpy(l.data(), lb.w64, sizeof(double) * n * lb.W, cudaMemcpyDeviceToHost));
+  const int half = lb.W / 2;
+  for (int64_t i = 0; i < n; ++i)
+    for (int e = 0; e < lb.W; ++e) {
+      const int64_t c = i - half + e;
+      if (c >= 0 && c < n) lap[i * n + c] += l[i * lb.W + e];
+    }
+  return TCA_OK;
+}
+
+// Smallest and largest eigenvalue of the symmetric n x n matrix a (destroyed):
+// cyclic Jacobi rotations until the off-diagonal mass is below 1e-24 of the
+// total (or 60 sweeps).
+static void sym_eig_extremes(std::vector<double>& a, int64_t n, double* lo, double* hi) {
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        const double v = a[i * n + j] * a[i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (!(off > 1e-24 * tot)) break;
+    for (int64_t pp = 0; pp < n; ++pp)
+      for (int64_t q = pp + 1; q < n; ++q) {
+        const double apq = a[pp * n + q];
+        if (apq == 0.0) continue;
+        const double theta = (a[q * n + q] - a[pp * n + pp]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int64_t k = 0; k < n; ++k) {  // columns pp, q
+          const double akp = a[k * n + pp], akq = a[k * n + q];
+          a[k * n + pp] = c * akp - s * akq;
+          a[k * n + q] = s * akp + c * akq;
+        }
+        for (int64_t k = 0; k < n; ++k) {  // rows pp, q
+          const double apk = a[pp * n + k], aqk = a[q * n + k];
+          a[pp * n + k] = c * apk - s * aqk;
+          a[q * n + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  *lo = *hi = a[0];
+  for (int64_t i = 1; i < n; ++i) {
+    *lo = std::min(*lo, a[i * n + i]);
+    *hi = std::max(*hi, a[i * n + i]);
+  }
+}
+
+// Corner model of the spectrum of M^-1 K for M = (x)_k (G_k + s lambda L_k):
+// mode k at its smooth corner (g_max, 0) or its rough corner
+// (g_min, lambda l_max); at a corner K is modelled by prod g + sum l and M by
+// prod (g + s l); s on the grid 2^(j/2), j = 0 .. 16, minimises the spread
+// max / min of K / M over the 2^d corners (the first grid point of the
+// minimum).  Modes longer than 512 are not modelled: the default shift 16.
+constexpr double kFallbackShift = 16.0;
+tca_status precond_model_shift(tca_plan_s* p, double* shift) {
+  if (p->pc_model_shift > 0.0) {
+    *shift = p->pc_model_shift;
+    return TCA_OK;
+  }
+  const int d = p->d;
+  double gs[kMaxModes][2], ls[kMaxModes][2];
+  bool ok = true;
+  for (int k = 0; k < d && ok; ++k) {
+    const int64_t n = p->mode[k].n;
+    if (n > 512) {
+      ok = false;
+      break;
+    }
+    std::vector<double> a, lap;
+    TCA_TRY(mode_dense_host(p, k, a, lap));
+    double gmin, gmax, lmin, lmax;
+    sym_eig_extremes(a, n, &gmin, &gmax);
+    sym_eig_extremes(lap, n, &lmin, &lmax);
+    gs[k][0] = gmax;
+    ls[k][0] = 0.0;
+    gs[k][1] = std::max(gmin, 0.0);
+    ls[k][1] = std::max(lmax, 0.0);
+  }
+  double best = kFallbackShift;
+  if (ok) {
+    double best_spread = -1.0;
+    for (int j = 0; j <= 16; ++j) {
+      const double s = std::pow(2.0, j / 2.0);
+      double rmin = 0.0, rmax = 0.0;
+      bool any = false;
+      for (int c = 0; c < (1 << d); ++c) {
+        double prod_g = 1.0, sum_l = 0.0, m = 1.0;
+        for (int k = 0; k < d; ++k) {
+          const int side = (c >> k) & 1;
+          prod_g *= gs[k][side];
+          sum_l += ls[k][side];
+          m *= gs[k][side] + s * ls[k][side];
+        }
+        if (!(m > 0.0)) continue;
+        const double r = (prod_g + sum_l) / m;
+        if (!any || r < rmin) rmin = r;
+        if (!any || r > rmax) rmax = r;
+        any = true;
+      }
+      if (!any || !(rmin > 0.0)) continue;
+      const double spread = rmax / rmin;
+      if (best_spread < 0.0 || spread < best_spread) {
+        best_spread = spread;
+        best = s;
+      }
+    }
+  }
+  p->pc_model_shift = best;
+  *shift = best;
+  return TCA_OK;
+}
+
 // M_k = G_k + s (lambda L_k), dense n x n in FP64 on the host, inverted in place.
 static tca_status precond_inverse_host(const tca_plan_s* p, int k, double shift, std::vector<double>& a) {
   {
@@ -775,6 +912,12 @@ extern "C" const char* tca_status_string(tca_status s) {
     case TCA_ERR_TIMEOUT: return "device wait timed out";
   }
   return "unknown status";
+}
+
+extern "C" tca_status tca_precond_default_shift(tca_plan_t plan, double* shift) {
+  if (!plan || !shift) return TCA_ERR_INVALID_ARG;
+  if (plan->scattered) return TCA_ERR_UNSUPPORTED;
+  return tca::precond_model_shift(plan, shift);
 }
 
 extern "C" const char* tca_last_error_string(void) { return tca::g_last_error; }

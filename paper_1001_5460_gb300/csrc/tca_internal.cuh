@@ -181,6 +181,7 @@ struct tca_plan_s {
   tca::FusedBands pcb_fused;
   float* pcb_zero = nullptr;  // zero 5-bands
   double pcb_shift = 0.0;
+  double pc_model_shift = 0.0;  // corner-model shift of the separable preconditioners (0: not yet formed)
   void* pc_dinv = nullptr;  // Jacobi: 1 / diag(K), n-shaped, element type of the plan (built on first use)
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
@@ -275,6 +276,9 @@ struct RegDot {
 // Separable-inverse preconditioner for shift s: build (or keep) the per-mode
 // factors and the z buffer; apply_precond writes z = M^-1 r (element type T).
 tca_status ensure_precond(tca_plan_s* p, double shift);
+// The separable preconditioners' default shift: the corner model of the
+// spectrum of M^-1 K (formed on the host once per plan).
+tca_status precond_model_shift(tca_plan_s* p, double* shift);
 // Point-Jacobi preconditioner: build (once) 1 / diag(K) and the z buffer.
 tca_status ensure_jacobi(tca_plan_s* p);
 // Banded separable preconditioner for shift s: build (or keep) the 7-band

@@ -109,6 +109,8 @@ _lib.tca_autotuned_chunks.argtypes = [_vp]
 _lib.tca_autotuned_chunks.restype = ctypes.c_int
 _lib.tca_autotuned_rows.argtypes = [_vp]
 _lib.tca_autotuned_rows.restype = ctypes.c_int
+_lib.tca_precond_default_shift.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+_lib.tca_precond_default_shift.restype = ctypes.c_int
 _lib.tca_net_param_count.argtypes = []
 _lib.tca_net_param_count.restype = ctypes.c_int64
 _lib.tca_net_create.argtypes = [ctypes.POINTER(_vp), _vp, _vp]
@@ -268,7 +270,7 @@ def vec_dot(a, b, out, stream=None):
 
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_plan_scattered", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",
@@ -359,7 +361,7 @@ class Plan:
         """Solve (A^T A + lambda R) x = A^T b; returns (status, info dict).
 
         precond: None (the CG of Fig. 2) or "separable" (the separable tensor-inverse
-        preconditioner, shift ``precond_shift``, 0 for the default)."""
+        preconditioner, shift ``precond_shift``, 0 for the plan's corner-model default)."""
         opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, float(inner_rtol),
                               int(max_refine), int(check_every), 1 if profile else 0, _precond_code(precond),
                               float(precond_shift))
@@ -378,6 +380,12 @@ class Plan:
     def autotuned_rows(self) -> int:
         """Core rows per worker thread the autotuner chose for a bfloat16 plan (0: not tuned)."""
         return int(_lib.tca_autotuned_rows(self._h))
+
+    def precond_default_shift(self) -> float:
+        """The shift the separable preconditioners take when none is given (the plan's corner model)."""
+        v = ctypes.c_double(0.0)
+        _check(_lib.tca_precond_default_shift(self._h, ctypes.byref(v)), "tca_precond_default_shift")
+        return float(v.value)
 
 
 class ScatteredPlan(Plan):

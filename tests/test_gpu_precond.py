@@ -1,8 +1,8 @@
 """Parity of the preconditioned CG (separable tensor-inverse preconditioner) with the oracle.
 
 The GPU solve with precond="separable" is compared with ``oracle.pcg`` driven by
-``oracle.separable_inverse_factors`` (shift 16, the library's default) on the same
-seeded inputs: iterate by iterate for the first steps (every position of the
+``oracle.separable_inverse_factors`` (at the library's default shift, the plan's corner-model
+shift, checked equal to ``oracle.corner_model_shift``) on the same seeded inputs: iterate by iterate for the first steps (every position of the
 four-iteration solution-update group), then the converged solution against the
 oracle's own verdict.  FP32 plans apply the preconditioner's dense factors on the
 tensor cores in 3xTF32 at these sizes (about 2^-21 relative per product), FP64
@@ -19,7 +19,6 @@ from tests.gpu_common import empty_dev, lib, rel_l2, to_dev
 
 pytestmark = pytest.mark.gpu
 
-SHIFT = 16.0
 
 
 def _dense(shape, seed, lam):
@@ -66,7 +65,9 @@ def test_pcg_partial_iterates_match_oracle(kind, shape, prec, lam):
     plan = tca.plan_from_instance(inst, precision=prec)
     rhs = O.apply_T(b.astype(np.float64), mats)
     kop = lambda v: O.normal_apply(v, mats, inst.lam)
-    inv = O.separable_inverse_factors(mats, inst.lam, SHIFT)
+    shift = plan.precond_default_shift()
+    assert shift == O.corner_model_shift(mats, inst.lam)
+    inv = O.separable_inverse_factors(mats, inst.lam, shift)
     minv = lambda r: O.apply_separable(r, inv)
     for k in (1, 2, 3, 4, 5, 7):
         x = empty_dev(inst.shape, dt)
@@ -207,7 +208,9 @@ def test_banded_pcg_iterates_match_oracle(kind, shape, prec):
     plan = tca.plan_from_instance(inst, precision=prec)
     rhs = O.apply_T(b.astype(np.float64), mats)
     kop = lambda v: O.normal_apply(v, mats, inst.lam)
-    inv = O.separable_inverse_factors(mats, inst.lam, SHIFT, half_band=3)
+    shift = plan.precond_default_shift()
+    assert shift == O.corner_model_shift(mats, inst.lam)
+    inv = O.separable_inverse_factors(mats, inst.lam, shift, half_band=3)
     minv = lambda r: O.apply_separable(r, inv)
     for k in (1, 2, 3, 4, 5, 7):
         x = empty_dev(inst.shape, dt)
@@ -258,3 +261,24 @@ def test_banded_pcg_batched_matches_single_solves():
         xr = empty_dev(inst.shape, np.float32)
         st1, info1 = plan.solve(bs[i], xr, rtol=1e-6, max_iter=5000, precond="separable_banded")
         assert st1 == tca.OK and abs(infos[i]["iters"] - info1["iters"]) <= 3
+
+
+@pytest.mark.parametrize("lam", [1e-4, 1e-2])
+@pytest.mark.parametrize("pc", ["separable", "separable_banded"])
+def test_default_shift_follows_lambda(lam, pc):
+    """With no shift given the preconditioner takes the plan's corner-model shift (equal to the
+    oracle's model; 128 at lambda = 1e-4, 5.7 at 1e-2 on this instance, against 16 fixed): the solve
+    meets 1e-6 in no more iterations than at s = 16."""
+    tca = lib()
+    inst = _inst("bspline", (24, 20, 22, 8), 720, lam)
+    mats = [f.dense() for f in inst.factors]
+    b = (O.apply(inst.x_true, mats) + inst.noise).astype(np.float32)
+    plan = tca.plan_from_instance(inst, precision="f32")
+    shift = plan.precond_default_shift()
+    assert shift == O.corner_model_shift(mats, lam)
+    x = empty_dev(inst.shape, np.float32)
+    st, info = plan.solve(to_dev(b, np.float32), x, rtol=1e-6, precond=pc)
+    assert st == tca.OK and info["rel_res_true"] <= 1e-6
+    st16, info16 = plan.solve(to_dev(b, np.float32), x, rtol=1e-6, precond=pc, precond_shift=16.0)
+    assert st16 == tca.OK
+    assert info["iters"] <= info16["iters"], (shift, info["iters"], info16["iters"])
