@@ -415,6 +415,11 @@ static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
     TCA_LAUNCH_CHECK();
     return TCA_OK;
   }
+  if constexpr (sizeof(T) == 4) {
+    // The banded preconditioner's fused sweep forms <r, z> and the scalars itself.
+    const tca_status fd = apply_precond_dot(p, (const float*)p->r, (float*)p->z, init, s);
+    if (fd != TCA_ERR_UNSUPPORTED) return fd;
+  }
   TCA_TRY(apply_precond<T>(p, (const T*)p->r, (T*)p->z, s));
   if (init)
     cg_precond_dot_kernel<T, true><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->z, p->N, p->scal,

@@ -509,6 +509,12 @@ tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s) {
   }
   return TCA_OK;
 }
+tca_status apply_precond_dot(tca_plan_s* p, const float* r, float* z, bool init, cudaStream_t s) {
+  if (p->pc_kind != TCA_PRECOND_SEPARABLE_BANDED || !p->fused_ok || (uintptr_t)r % 16 != 0)
+    return TCA_ERR_UNSUPPORTED;
+  return normal_fused_f32(p, nullptr, r, nullptr, z, false, s, &p->pcb_fused, p->scal, init ? 1 : 2);
+}
+
 template tca_status apply_precond<float>(tca_plan_s*, const float*, float*, cudaStream_t);
 template tca_status apply_precond<double>(tca_plan_s*, const double*, double*, cudaStream_t);
 

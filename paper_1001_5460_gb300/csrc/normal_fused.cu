@@ -62,6 +62,8 @@ struct FusedArgs {
   CUtensorMap tm_p;
   int* timeout_flag;
   const Scalars* stop;  // plain sweep as a CG preconditioner: no work once these stop flags are set
+  int pdot;             // plain warp-specialised sweep as the preconditioner of PCG: 1 / 2 also forms
+                        // rho1 = <input, output> and the PCG scalars (1: a fresh start, beta = 0)
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -638,7 +640,7 @@ __device__ __forceinline__ void bar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <bool CG, bool TMA>
+template <bool CG, bool TMA, bool PDOT>
 __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int N4 = 8, T2 = 16, T3 = 16, T3P = 2, STAGES = 3;
   using C = Cfg<N4, T2, T3, T3P, NB, STAGES, true>;  // smem layout of the CG configuration (P tiles, ring)
@@ -1102,12 +1104,14 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
             lin2[k][h] = lin;
             pc2[k][h] = h ? make_float2(pv.z, pv.w) : make_float2(pv.x, pv.y);
           }
-          if constexpr (CG) {
+          if constexpr (CG || PDOT) {
             const float4 pc4 = make_float4(pc2[k][0].x, pc2[k][0].y, pc2[k][1].x, pc2[k][1].y);
             float* ring = s_ring + (j & 3) * C::CORE;
             reinterpret_cast<float4*>(ring)[k * NB + tb] = pc4;
-            if (own_plane && (k ? ok1 : ok0))
-              *reinterpret_cast<float4*>(a.pnew + (int64_t)j * plane + out_base + k * row_step) = pc4;
+            if constexpr (CG) {
+              if (own_plane && (k ? ok1 : ok0))
+                *reinterpret_cast<float4*>(a.pnew + (int64_t)j * plane + out_base + k * row_step) = pc4;
+            }
           }
         }
       }
@@ -1140,7 +1144,7 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
             if (k ? ok1 : ok0) {
               const float4 qv = make_float4(acc[k][0][E].x, acc[k][0][E].y, acc[k][1][E].x, acc[k][1][E].y);
               *reinterpret_cast<float4*>(qo + k * row_step) = qv;
-              if constexpr (CG) {
+              if constexpr (CG || PDOT) {
                 const float4 pv = ring[k * NB + tb];
                 part = fmaf(qv.x, pv.x, part);
                 part = fmaf(qv.y, pv.y, part);
@@ -1180,6 +1184,17 @@ __global__ void __launch_bounds__(NT, 1) fused_ws_kernel(const __grid_constant__
       } else {
         sc->alpha = alpha;
       }
+    }
+  } else if constexpr (PDOT) {
+    // rho1 = <r, z> of the preconditioned CG (r the input, z = M^-1 r the output),
+    // with the scalar logic of the separate preconditioner dot.
+    double total;
+    if (dev::grid_sum_last_at(dot, a.red, &total, s_red, s_last)) {
+      Scalars* sc = a.scal;
+      const bool bad = !isfinite(total) || (!(total > 0.0) && sc->rho_new > 0.0);
+      if (bad) sc->breakdown = 1;
+      sc->beta = a.pdot == 1 ? 0.0 : total / sc->rho;
+      sc->rho = total;
     }
   }
 }
@@ -1240,16 +1255,18 @@ tca_status launch_fused(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   return TCA_OK;
 }
 
-template <bool CG>
+template <bool CG, bool PDOT>
 tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
   constexpr size_t bytes = ws::ws_bytes();
   static_assert(bytes <= 227 * 1024, "shared memory budget");
+  static_assert(!(CG && PDOT), "the preconditioner dot belongs to the plain sweep");
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(ws::fused_ws_kernel<CG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(ws::fused_ws_kernel<CG, false, PDOT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ws::fused_ws_kernel<CG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      e = cudaFuncSetAttribute(ws::fused_ws_kernel<CG, true, PDOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bytes);
     if (e != cudaSuccess) {
       set_cuda_error(e);
       return TCA_ERR_CUDA;
@@ -1271,7 +1288,7 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
     if (tma && CG) tma = encode_tmap_f32(&a.tm_r, a.r, 3, dims, strides, box);
   }
   a.timeout_flag = wait_timeout_flag();
-  auto kfn = tma ? ws::fused_ws_kernel<CG, true> : ws::fused_ws_kernel<CG, false>;
+  auto kfn = tma ? ws::fused_ws_kernel<CG, true, PDOT> : ws::fused_ws_kernel<CG, false, PDOT>;
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
   const int tiles2 = (n2 + 15) / 16, tiles3 = (n3 + 15) / 16;
   const int tiles = tiles2 * tiles3;
@@ -1306,8 +1323,9 @@ tca_status launch_ws(tca_plan_s* p, const FusedArgs& base, cudaStream_t s) {
 }  // namespace
 
 tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, float* p_new, float* q,
-                            bool cg_mode, cudaStream_t s, const FusedBands* bands, const Scalars* stop) {
+                            bool cg_mode, cudaStream_t s, const FusedBands* bands, const Scalars* stop, int pdot) {
   if (!p->fused_ok) return TCA_ERR_UNSUPPORTED;
+  if (pdot && (cg_mode || p->d != 4 || p->n[3] != 8)) return TCA_ERR_UNSUPPORTED;
   FusedArgs a{};
   a.r = r;
   a.pold = p_old;
@@ -1321,6 +1339,7 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
     a.l[k] = bands ? bands->l[k] : p->mode[k].lap.w32;
   }
   a.stop = stop;
+  a.pdot = pdot;
   for (int k = d; k < 4; ++k) {
     a.g[k] = nullptr;
     a.l[k] = nullptr;
@@ -1339,7 +1358,8 @@ tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, f
       for (int e = 0; e < 7; ++e) a.g4c[e * 8 + i4] = g4[i4 * 7 + e];
       for (int e = 0; e < 5; ++e) a.l4c[e * 8 + i4] = l4[i4 * 5 + e];
     }
-    return cg_mode ? launch_ws<true>(p, a, s) : launch_ws<false>(p, a, s);
+    if (cg_mode) return launch_ws<true, false>(p, a, s);
+    return pdot ? launch_ws<false, true>(p, a, s) : launch_ws<false, false>(p, a, s);
   } else if (n4 == 4) {
     return cg_mode ? launch_fused<4, 16, 32, 4, 256, 3, true>(p, a, s) : launch_fused<4, 16, 32, 4, 256, 3, false>(p, a, s);
   } else if (n4 == 1) {

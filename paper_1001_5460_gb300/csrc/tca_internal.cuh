@@ -286,6 +286,10 @@ tca_status ensure_jacobi(tca_plan_s* p);
 tca_status ensure_precond_banded(tca_plan_s* p, double shift);
 template <typename T>
 tca_status apply_precond(tca_plan_s* p, const T* r, T* z, cudaStream_t s);
+// The banded separable preconditioner and rho1 = <r, z> with the PCG scalars in
+// one fused sweep (init: a fresh start); TCA_ERR_UNSUPPORTED where the fused
+// sweep cannot do both (the caller applies M^-1 and forms the dot apart).
+tca_status apply_precond_dot(tca_plan_s* p, const float* r, float* z, bool init, cudaStream_t s);
 // Largest 3xTF32 / TF32 split the tensor-core dense kernel takes for an
 // n_out x n_in factor (2, 1, or 0 when it takes none).
 int dense_tc_max_split(int64_t n_in, int64_t n_out);
@@ -305,10 +309,13 @@ tca_status apply_chain(tca_plan_s* p, bool transpose, const Tin* x, Tout* y, voi
                        int64_t ws_elems, cudaStream_t s);
 
 // Fused FP32 sweep (fused_ok): optionally p_new = r + beta p_old, q = K p_new,
-// <p_new, q> reduced to alpha.  Returns TCA_ERR_UNSUPPORTED if not applicable.
+// <p_new, q> reduced to alpha.  pdot (plain sweep, n4 = 8 only): also
+// rho1 = <p_old, q> and the PCG scalars (1: a fresh start, 2: an update), the
+// sweep then being the preconditioner z = M^-1 r.  Returns
+// TCA_ERR_UNSUPPORTED if not applicable.
 tca_status normal_fused_f32(tca_plan_s* p, const float* r, const float* p_old, float* p_new,
                             float* q, bool cg_mode, cudaStream_t s, const FusedBands* bands = nullptr,
-                            const Scalars* stop = nullptr);
+                            const Scalars* stop = nullptr, int pdot = 0);
 
 // Blocks used by grid-stride vector kernels.
 int vector_grid(const tca_plan_s* p, int64_t n);
