@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
     ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
     ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "bf16sweep", "dense", "batched", "learned",
-                             "netfwd", "scattered"],
+                             "netfwd", "scattered", "pcg"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -158,6 +158,17 @@ def run_case(args, local):
                                    profile=True)
         ms = info["sweep_ms"] / max(info["sweep_launches"], 1)
         print(json.dumps({"case": args.case, "ms": round(ms, 5), "gbs": round(4 * N * 2 / ms / 1e6, 1)}), flush=True)
+        return
+    if args.case == "pcg":
+        # Profiled solves (one graph launch per pass, so profilers see every kernel) of the
+        # bench workload preconditioned by the banded separable inverse at the default shift.
+        inst_t, plan_t, b = make_problem(shape, SEED, device)
+        xz = torch.zeros(shape, dtype=torch.float32, device=device)
+        for _ in range(args.warmup + args.steps):
+            st, info = plan_t.solve(b, xz, rtol=RTOL, precond="separable_banded", profile=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "status": int(st), "cg_iters": info["iters"],
+                          "rel_res_true": info["rel_res_true"], "shift": plan_t.precond_default_shift()}), flush=True)
         return
     if args.case == "cgsweep":
         # A few CG iterations on random data: the CG-mode fused sweep in its solve context.
