@@ -101,6 +101,15 @@ def test_plan_rejects_bad_arguments_before_device_work(tca):
     # entry points reject a null plan
     assert tca._lib.tca_apply(None, None, None, None) == tca.ERR_INVALID_ARG
     assert tca._lib.tca_solve(None, None, None, None, None, None) == tca.ERR_INVALID_ARG
+    shift = ctypes.c_double(0.0)
+    assert tca._lib.tca_precond_default_shift(None, ctypes.byref(shift)) == tca.ERR_INVALID_ARG
+    # scattered plans: order, negative sample count, precision
+    assert tca._lib.tca_plan_scattered(ctypes.byref(h), 2, n, 5, fac, ctypes.byref(reg), tca.F64,
+                                       None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_plan_scattered(ctypes.byref(h), 3, n, -1, fac, ctypes.byref(reg), tca.F64,
+                                       None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_plan_scattered(ctypes.byref(h), 3, n, 5, fac, ctypes.byref(reg), tca.BF16_IR,
+                                       None) == tca.ERR_UNSUPPORTED
     tca._lib.tca_destroy(None)  # NULL is ignored
 
 
