@@ -141,10 +141,33 @@ __global__ void __launch_bounds__(kVecThreads) cg_flush_x_kernel(T* __restrict__
   __shared__ double sh[kVecThreads / 32];
   const int np = sc->npend;
   if (np > 0) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      T xv = x[i];
-      for (int k = 0; k < np; ++k) xv = fma((T)sc->alpha_hist[k], pb.p[k + 1][i], xv);
-      x[i] = xv;
+    // 16-byte vectors (allocation-aligned buffers), the scalar tail by block 0;
+    // per element the pending terms in iteration order, as the update applies them.
+    T ah[kDirBufs - 1];
+#pragma unroll
+    for (int k = 0; k < kDirBufs - 1; ++k) ah[k] = k < np ? (T)sc->alpha_hist[k] : T(0);
+    using VT = typename V2<T>::t;
+    constexpr int VN = V2<T>::n;
+    const int64_t nv = n / VN;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+      VT xv = reinterpret_cast<VT*>(x)[i];
+      T* xs = reinterpret_cast<T*>(&xv);
+#pragma unroll
+      for (int k = 0; k < kDirBufs - 1; ++k) {
+        if (k >= np) break;
+        const VT pv = reinterpret_cast<const VT*>(pb.p[k + 1])[i];
+        const T* ps = reinterpret_cast<const T*>(&pv);
+#pragma unroll
+        for (int c = 0; c < VN; ++c) xs[c] = fma(ah[k], ps[c], xs[c]);
+      }
+      reinterpret_cast<VT*>(x)[i] = xv;
+    }
+    if (blockIdx.x == 0) {
+      for (int64_t i = nv * VN + threadIdx.x; i < n; i += blockDim.x) {
+        T xv = x[i];
+        for (int k = 0; k < np; ++k) xv = fma(ah[k], pb.p[k + 1][i], xv);
+        x[i] = xv;
+      }
     }
   }
   double total;
