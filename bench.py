@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
     ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
     ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "bf16sweep", "dense", "batched", "learned",
-                             "netfwd", "scattered", "pcg"],
+                             "netfwd", "scattered", "pcg", "tmg"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -169,6 +169,17 @@ def run_case(args, local):
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "status": int(st), "cg_iters": info["iters"],
                           "rel_res_true": info["rel_res_true"], "shift": plan_t.precond_default_shift()}), flush=True)
+        return
+    if args.case == "tmg":
+        # Solves of the bench workload preconditioned by the two-grid tensor multigrid cycle
+        # (every default), timed with CUDA events on the solve's stream.
+        inst_t, plan_t, b = make_problem(shape, SEED, device)
+        xz = torch.zeros(shape, dtype=torch.float32, device=device)
+        ms, info = timed_solve(plan_t, b, xz, max(1, args.steps), torch.cuda.current_stream(), precond="tmg")
+        st_t = plan_t.tmg_info()
+        print(json.dumps({"case": args.case, "ms": round(ms, 3), "cg_iters": info["iters"],
+                          "rel_res_true": info["rel_res_true"], "coarse_cg_iters": st_t["coarse_iters"],
+                          "lambda_max": st_t["lambda_max"]}), flush=True)
         return
     if args.case == "cgsweep":
         # A few CG iterations on random data: the CG-mode fused sweep in its solve context.
@@ -898,6 +909,22 @@ def run_tca(args, rank, world, local):
             "what": f"CG preconditioned by the separable tensor inverse (x)_k (G_k + s lambda L_k)^-1, s = {used:g}"
                     + (" (the plan's corner-model default)" if shift <= 0 else "")
                     + f" ({how}), same tolerance on the FP64 true residual"}
+
+    if not args.no_variants:
+        # The same solve preconditioned by the two-grid tensor multigrid cycle (Sec. 4.2,
+        # Fig. 3) with every default: modes 1-3 coarsened, two Chebyshev steps, coarse CG to 0.1.
+        try:
+            tmg_ms, tmg_info = timed_solve(plan, b, x, max(1, min(args.steps, 5)), s, precond="tmg")
+            st_t = plan.tmg_info()
+            variants["tmg_pcg"] = {
+                "ms": round(max_over_ranks(tmg_ms, world), 3), "cg_iters": tmg_info["iters"],
+                "restarts": tmg_info["refinements"], "rel_res_true": tmg_info["rel_res_true"],
+                "coarse_cg_iters": st_t["coarse_iters"], "lambda_max_DinvK": round(st_t["lambda_max"], 4),
+                "what": "CG preconditioned by a two-grid tensor multigrid cycle: Chebyshev smoothing on "
+                        "D^-1 K (2 steps before and after), separable linear-interpolation transfers on "
+                        "modes 1-3, Galerkin coarse operator P^T K P solved by CG to 0.1 (host-steered)"}
+        except Exception as exc:
+            variants["tmg_pcg"] = {"error": repr(exc)[:300]}
 
     peaks, peak_src = measured_peaks()
     if not args.no_variants:

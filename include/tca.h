@@ -196,11 +196,20 @@ typedef struct {
   int32_t precond;      /* TCA_PRECOND_NONE: the CG of Fig. 2; TCA_PRECOND_SEPARABLE: the same CG with
                            Z = M^-1 R, M = (G_1 + s lambda L_1) x ... x (G_d + s lambda L_d);
                            TCA_PRECOND_JACOBI: M = diag(K); TCA_PRECOND_SEPARABLE_BANDED: the
-                           separable inverse cut to 7-band factors (see below) */
+                           separable inverse cut to 7-band factors; TCA_PRECOND_TMG: a two-grid
+                           tensor multigrid cycle (see below) */
   double precond_shift; /* s, the regulariser weight folded into each mode of M (0: the plan's
                            tca_precond_default_shift).  The best s depends on lambda and the
                            factors (32 for the B-spline workload at lambda = 1e-3, 128 at 1e-4,
                            8 at 1e-2). */
+  /* TCA_PRECOND_TMG (the tensor multigrid cycle below); zero selects each default. */
+  double tmg_coarse_rtol;   /* relative tolerance ||r_c|| / ||b_c|| of the coarse CG (0: 0.1) */
+  double tmg_lambda_max;    /* largest eigenvalue of D^-1 K, D = diag(K), for the Chebyshev
+                               smoother (0: estimated on the device by 60 power steps from a
+                               fixed pseudo-random start, once per plan) */
+  int32_t tmg_nu;           /* Chebyshev smoothing steps before and after the coarse correction
+                               (0: 2; a negative value: none, the bare coarse-grid correction) */
+  int32_t tmg_coarsen_mask; /* bit k set: mode k is coarsened by 2 (0: every mode with n_k >= 16) */
 } tca_solve_opts;
 
 /* Preconditioner choice (tca_solve_opts.precond).  TCA_PRECOND_SEPARABLE_BANDED
@@ -231,7 +240,27 @@ typedef struct {
  * one inner product per iteration, and one n_k x n_k dense factor per mode;
  * the tensor-core products of an iteration that starts after the stop flags
  * are set return at entry, like the CG kernels. */
-enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1, TCA_PRECOND_JACOBI = 2, TCA_PRECOND_SEPARABLE_BANDED = 3 };
+enum { TCA_PRECOND_NONE = 0, TCA_PRECOND_SEPARABLE = 1, TCA_PRECOND_JACOBI = 2, TCA_PRECOND_SEPARABLE_BANDED = 3,
+       TCA_PRECOND_TMG = 4 };
+
+/* TCA_PRECOND_TMG: one two-grid tensor multigrid cycle (Sec. 4.2, Fig. 3) per
+ * iteration, z = V r, on TCA_F32 and TCA_F64 plans with Gram-form (not
+ * scattered) operators.  The transfers are separable: a coarsened mode k keeps
+ * its even points, ceil(n_k / 2) of them, and P_k is linear interpolation back
+ * to n_k points (Table 1's up-sampling; restriction = P_k^T); the coarse
+ * operator is the Galerkin K_c = P^T K P with P = P_1 kron .. kron P_d (the
+ * identity on modes that are kept), applied without being formed: prolong,
+ * the fine K, restrict.  The cycle:
+ *   z = S(0);  z += P K_c^-1 P^T (r - K z);  z = S(z)
+ * where S is nu steps of Chebyshev iteration for K z = r preconditioned by
+ * D = diag(K) over the interval [lambda_max / 30, 1.05 lambda_max] of D^-1 K,
+ * the same polynomial before and after (so V is symmetric), and K_c^-1 is CG
+ * to tmg_coarse_rtol (the direct solve at the coarsest scale of Fig. 3,
+ * reached here by iteration; a loose tolerance makes V vary slightly from one
+ * call to the next).  The CG iteration around it is the preconditioned CG of
+ * TCA_PRECOND_SEPARABLE; the cycle's coarse solve is steered from the host
+ * (one synchronisation per coarse iteration), so these solves run without the
+ * device-side loop.  Not for tca_solve_batched (TCA_ERR_UNSUPPORTED). */
 
 typedef struct {
   int32_t iters;             /* CG iterations run (all inner solves summed) */
@@ -283,6 +312,23 @@ TCA_API tca_status tca_solve(tca_plan_t plan, const void* b, void* x, const tca_
  * Synchronises the device (copies of the bands).  TCA_ERR_UNSUPPORTED for
  * scattered-sample plans. */
 TCA_API tca_status tca_precond_default_shift(tca_plan_t plan, double* shift);
+
+/* One tensor multigrid cycle z = V r (TCA_PRECOND_TMG above) with the options'
+ * tmg_* fields: r and z n-shaped device buffers of the plan's element type
+ * (TCA_F32: float, TCA_F64: double), not aliased.  Builds on first use, and
+ * keeps with the plan, the transfers, the cycle's vectors (three n-shaped and
+ * four coarse) and 1 / diag(K).  TCA_ERR_INVALID_ARG for a null pointer, a
+ * negative tolerance or lambda_max, or a mask bit for a mode the plan lacks
+ * or one with n_k < 2; TCA_ERR_UNSUPPORTED for scattered-sample plans and the
+ * _IR precisions.  Synchronises the stream. */
+TCA_API tca_status tca_tmg_apply(tca_plan_t plan, const void* r, void* z, const tca_solve_opts* opts,
+                                 cudaStream_t stream);
+
+/* The tensor multigrid state of the plan: the lambda_max of D^-1 K its
+ * smoother uses (given or estimated; 0 before the first cycle) and the coarse
+ * CG iterations run since the last tca_solve started (or since the last
+ * tca_tmg_apply call).  Either pointer may be NULL. */
+TCA_API tca_status tca_tmg_info(tca_plan_t plan, double* lambda_max, int64_t* coarse_iters);
 
 /* Solve `count` independent systems (A_i^T A_i + lambda_i R_i) x_i = A_i^T b_i,
  * each by the CG of Sec. 4.1, Fig. 2, in one CUDA graph launch.  Many small

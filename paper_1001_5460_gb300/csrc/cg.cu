@@ -438,12 +438,17 @@ static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
     TCA_LAUNCH_CHECK();
     return TCA_OK;
   }
-  if constexpr (sizeof(T) == 4) {
-    // The banded preconditioner's fused sweep forms <r, z> and the scalars itself.
-    const tca_status fd = apply_precond_dot(p, (const float*)p->r, (float*)p->z, init, s);
-    if (fd != TCA_ERR_UNSUPPORTED) return fd;
+  if (p->pc_kind == TCA_PRECOND_TMG) {
+    // One tensor multigrid cycle (host-steered; nothing to do after the stop).
+    TCA_TRY(tmg_cycle<T>(p, (const T*)p->r, (T*)p->z, true, s));
+  } else {
+    if constexpr (sizeof(T) == 4) {
+      // The banded preconditioner's fused sweep forms <r, z> and the scalars itself.
+      const tca_status fd = apply_precond_dot(p, (const float*)p->r, (float*)p->z, init, s);
+      if (fd != TCA_ERR_UNSUPPORTED) return fd;
+    }
+    TCA_TRY(apply_precond<T>(p, (const T*)p->r, (T*)p->z, s));
   }
-  TCA_TRY(apply_precond<T>(p, (const T*)p->r, (T*)p->z, s));
   if (init)
     cg_precond_dot_kernel<T, true><<<grid, kVecThreads, 0, s>>>((const T*)p->r, (const T*)p->z, p->N, p->scal,
                                                                  first_reduce(p));
@@ -457,7 +462,7 @@ static tca_status enqueue_precond(tca_plan_s* p, bool init, cudaStream_t s) {
 // The preconditioner a solve asks for: validates the options, builds the
 // factors for the shift (by default the plan's corner-model shift) and marks
 // the plan's iteration as preconditioned (or not).
-static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
+static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o, cudaStream_t s) {
   p->pc_on = false;
   p->pc_kind = TCA_PRECOND_NONE;
   const int kind = o ? o->precond : TCA_PRECOND_NONE;
@@ -468,6 +473,9 @@ static tca_status setup_precond(tca_plan_s* p, const tca_solve_opts* o) {
   }
   if (kind == TCA_PRECOND_JACOBI) {
     TCA_TRY(ensure_jacobi(p));
+  } else if (kind == TCA_PRECOND_TMG) {
+    TCA_TRY(tmg_setup(p, o, s));
+    tmg_reset_count(p);
   } else {
     if ((kind != TCA_PRECOND_SEPARABLE && kind != TCA_PRECOND_SEPARABLE_BANDED) || o->precond_shift < 0.0)
       return TCA_ERR_INVALID_ARG;
@@ -761,6 +769,24 @@ static tca_status true_residual(tca_plan_s* p, const T* x, bool write_r, cudaStr
   return TCA_OK;
 }
 
+// The iteration steered from the host (preconditioners that synchronise, the
+// tensor multigrid cycle): one iteration at a time, the scalar record read
+// after each, until the same stop conditions as cg_iterate.
+template <typename T>
+static tca_status cg_iterate_host(tca_plan_s* p, T* x, double rtol, int max_iter, cudaStream_t s) {
+  Scalars* hs = p->scal_host;
+  TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  TCA_CUDA_TRY(cudaStreamSynchronize(s));
+  bool conv = hs->bnorm == 0.0 || std::sqrt(hs->rho_new) <= rtol * hs->bnorm;
+  for (int it = 0; !conv && !hs->breakdown && hs->iters < max_iter; ++it) {
+    TCA_TRY(enqueue_iteration<T>(p, x, it, s, nullptr, nullptr));
+    TCA_CUDA_TRY(cudaMemcpyAsync(hs, p->scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    TCA_CUDA_TRY(cudaStreamSynchronize(s));
+    conv = hs->converged != 0;
+  }
+  return TCA_OK;
+}
+
 // Replay the cached CG graph until the recursive residual meets rtol, CG
 // breaks down or the device iteration count reaches max_iter.  The scalar
 // record is left in p->scal_host.
@@ -841,7 +867,7 @@ static tca_status solve_ir(tca_plan_s* p, const void* b_in, float* x, const tca_
     set_error_message("TCA_BF16_IR plans take no preconditioner");
     return TCA_ERR_UNSUPPORTED;
   }
-  TCA_TRY(setup_precond(p, o));
+  TCA_TRY(setup_precond(p, o, s));
   TCA_TRY(chain_ff(p, true, false, (const float*)b_in, reinterpret_cast<float2*>(p->rhs64), (float*)p->rhs,
                    reinterpret_cast<float2* const*>(p->ws64), p->ws64_elems, s));
   if (!(o && o->x0_given)) TCA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * N, s));
@@ -936,7 +962,7 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   const bool profile = o && o->profile;
   if (profile) every = std::min(every, kMaxProfiledIters);
   if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
-  TCA_TRY(setup_precond(p, o));
+  TCA_TRY(setup_precond(p, o, s));
   double sweep_ms = 0.0;
   int sweep_n = 0;
 
@@ -1001,13 +1027,15 @@ static tca_status solve_impl(tca_plan_s* p, const void* b_in, T* x, const tca_so
   }
   TCA_LAUNCH_CHECK();
   if (p->pc_on) TCA_TRY(enqueue_precond<T>(p, true, s));
-  TCA_TRY(get_graph<T>(p, x, every, profile, s));
+  const bool host_loop = p->pc_on && p->pc_kind == TCA_PRECOND_TMG;
+  if (!host_loop) TCA_TRY(get_graph<T>(p, x, every, profile, s));
 
   tca_status status = TCA_OK;
   int restarts = 0;
   Scalars* hs = p->scal_host;
   for (;;) {
-    TCA_TRY(cg_iterate(p, rtol, max_iter, every, profile, &sweep_ms, &sweep_n, s));
+    if (host_loop) TCA_TRY(cg_iterate_host<T>(p, x, rtol, max_iter, s));
+    else TCA_TRY(cg_iterate(p, rtol, max_iter, every, profile, &sweep_ms, &sweep_n, s));
     TCA_TRY(flush_pending_x<T>(p, x, s));
     if (x_host) {
       // x is final for this pass: copy it to the host on a side stream while
@@ -1288,10 +1316,14 @@ static tca_status solve_batched_impl(int count, tca_plan_s** plans, const float*
   int every = (o && o->check_every > 0) ? o->check_every : 16;
   every = std::max(kDirBufs, (every + kDirBufs - 1) / kDirBufs * kDirBufs);
   if (!(rtol > 0.0)) return TCA_ERR_INVALID_ARG;
+  if (o && o->precond == TCA_PRECOND_TMG) {
+    set_error_message("the tensor multigrid cycle is steered from the host: not in a batched graph");
+    return TCA_ERR_UNSUPPORTED;
+  }
   for (int i = 0; i < count; ++i) {
     TCA_TRY(ensure_solver_buffers<float>(plans[i]));
     TCA_TRY(ensure_ws64_public(plans[i]));
-    TCA_TRY(setup_precond(plans[i], o));
+    TCA_TRY(setup_precond(plans[i], o, s));
   }
   std::lock_guard<std::mutex> lock(g_batch_mutex);
   TCA_TRY(ensure_pool());

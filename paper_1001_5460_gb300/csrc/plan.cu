@@ -780,6 +780,7 @@ static void destroy_plan(tca_plan_s* p) {
   for (cudaEvent_t& ev : p->sweep_ev)
     if (ev) cudaEventDestroy(ev);
   bf16_release(p);
+  tmg_release(p);
   scattered_release(p);
   cudaFree(p->scal);
   if (p->scal_host) cudaFreeHost(p->scal_host);

@@ -134,6 +134,8 @@ struct Bf16State {
   CUtensorMap tm_r, tm_x, tm_p[kDirBufs];
 };
 
+struct TmgState;  // tensor multigrid preconditioner (tmg.cu)
+
 }  // namespace tca
 
 struct tca_plan_s {
@@ -183,6 +185,7 @@ struct tca_plan_s {
   double pcb_shift = 0.0;
   double pc_model_shift = 0.0;  // corner-model shift of the separable preconditioners (0: not yet formed)
   void* pc_dinv = nullptr;  // Jacobi: 1 / diag(K), n-shaped, element type of the plan (built on first use)
+  tca::TmgState* tmg = nullptr;  // tensor multigrid cycle: transfers, vectors, smoother interval
   void* stage_x = nullptr;  // host-pointer staging (n-shaped)
   void* stage_b = nullptr;  // host-pointer staging (m-shaped)
   cudaStream_t copy_stream = nullptr;  // host-pointer solves: b uploaded under A^T b, x copied back
@@ -374,6 +377,15 @@ tca_status scattered_gather(const tca_plan_s* p, const T* x, T* y, bool perm, cu
 template <typename T>
 tca_status scattered_scatter(const tca_plan_s* p, const T* y, T* x, bool perm, cudaStream_t s);
 void scattered_release(tca_plan_s* p);
+
+// Tensor multigrid preconditioner (tmg.cu): set up (or keep) the cycle for the
+// options' tmg_* fields; z = V r (returns at once when the CG stop flags of
+// p->scal are set and skip_if_done); free the state with the plan.
+tca_status tmg_setup(tca_plan_s* p, const tca_solve_opts* o, cudaStream_t s);
+template <typename T>
+tca_status tmg_cycle(tca_plan_s* p, const T* r, T* z, bool skip_if_done, cudaStream_t s);
+void tmg_reset_count(tca_plan_s* p);
+void tmg_release(tca_plan_s* p);
 
 bool is_device_ptr(const void* ptr);
 tca_status ensure_stage(tca_plan_s* p);

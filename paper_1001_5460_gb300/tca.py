@@ -55,16 +55,19 @@ class tca_reg(ctypes.Structure):
 class tca_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("x0_given", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_shift", ctypes.c_double)]
+                ("profile", ctypes.c_int32), ("precond", ctypes.c_int32), ("precond_shift", ctypes.c_double),
+                ("tmg_coarse_rtol", ctypes.c_double), ("tmg_lambda_max", ctypes.c_double),
+                ("tmg_nu", ctypes.c_int32), ("tmg_coarsen_mask", ctypes.c_int32)]
 
 
-PRECOND_NONE, PRECOND_SEPARABLE, PRECOND_JACOBI, PRECOND_SEPARABLE_BANDED = 0, 1, 2, 3
+PRECOND_NONE, PRECOND_SEPARABLE, PRECOND_JACOBI, PRECOND_SEPARABLE_BANDED, PRECOND_TMG = 0, 1, 2, 3, 4
 
 
 def _precond_code(precond) -> int:
     """None / "none" -> plain CG (Fig. 2); "separable" -> CG with the separable tensor-inverse
     preconditioner; "separable_banded" -> the same with 7-band truncated factors (one fused
-    sweep per application); "jacobi" -> CG with the point-Jacobi preconditioner diag(K)."""
+    sweep per application); "jacobi" -> CG with the point-Jacobi preconditioner diag(K);
+    "tmg" -> CG with one two-grid tensor multigrid cycle per iteration."""
     if precond in (None, "none", PRECOND_NONE):
         return PRECOND_NONE
     if precond in ("separable", PRECOND_SEPARABLE):
@@ -73,6 +76,8 @@ def _precond_code(precond) -> int:
         return PRECOND_JACOBI
     if precond in ("separable_banded", PRECOND_SEPARABLE_BANDED):
         return PRECOND_SEPARABLE_BANDED
+    if precond in ("tmg", PRECOND_TMG):
+        return PRECOND_TMG
     raise ValueError(f"unknown preconditioner {precond!r}")
 
 
@@ -111,6 +116,10 @@ _lib.tca_autotuned_rows.argtypes = [_vp]
 _lib.tca_autotuned_rows.restype = ctypes.c_int
 _lib.tca_precond_default_shift.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
 _lib.tca_precond_default_shift.restype = ctypes.c_int
+_lib.tca_tmg_apply.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), _vp]
+_lib.tca_tmg_apply.restype = ctypes.c_int
+_lib.tca_tmg_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _i64p]
+_lib.tca_tmg_info.restype = ctypes.c_int
 _lib.tca_net_param_count.argtypes = []
 _lib.tca_net_param_count.restype = ctypes.c_int64
 _lib.tca_net_create.argtypes = [ctypes.POINTER(_vp), _vp, _vp]
@@ -270,7 +279,7 @@ def vec_dot(a, b, out, stream=None):
 
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_plan_scattered", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_tmg_apply", "tca_tmg_info", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",
@@ -357,14 +366,19 @@ class Plan:
 
     def solve(self, b, x, rtol: float = 1e-6, max_iter: int = 10000, x0_given: bool = False,
               check_every: int = 0, inner_rtol: float = 0.0, max_refine: int = 0, stream=None,
-              raise_on_error: bool = True, profile: bool = False, precond=None, precond_shift: float = 0.0):
+              raise_on_error: bool = True, profile: bool = False, precond=None, precond_shift: float = 0.0,
+              tmg_nu: int = 0, tmg_coarse_rtol: float = 0.0, tmg_lambda_max: float = 0.0,
+              tmg_coarsen_mask: int = 0):
         """Solve (A^T A + lambda R) x = A^T b; returns (status, info dict).
 
-        precond: None (the CG of Fig. 2) or "separable" (the separable tensor-inverse
-        preconditioner, shift ``precond_shift``, 0 for the plan's corner-model default)."""
+        precond: None (the CG of Fig. 2), "jacobi", "separable" / "separable_banded" (the separable
+        tensor-inverse preconditioner, shift ``precond_shift``, 0 for the plan's corner-model
+        default) or "tmg" (a two-grid tensor multigrid cycle; the tmg_* arguments, 0 for each
+        default)."""
         opts = tca_solve_opts(float(rtol), int(max_iter), 1 if x0_given else 0, float(inner_rtol),
                               int(max_refine), int(check_every), 1 if profile else 0, _precond_code(precond),
-                              float(precond_shift))
+                              float(precond_shift), float(tmg_coarse_rtol), float(tmg_lambda_max), int(tmg_nu),
+                              int(tmg_coarsen_mask))
         info = tca_solve_info()
         st = _lib.tca_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
         if raise_on_error:
@@ -386,6 +400,22 @@ class Plan:
         v = ctypes.c_double(0.0)
         _check(_lib.tca_precond_default_shift(self._h, ctypes.byref(v)), "tca_precond_default_shift")
         return float(v.value)
+
+    def tmg_apply(self, r, z, nu: int = 0, coarse_rtol: float = 0.0, lambda_max: float = 0.0,
+                  coarsen_mask: int = 0, stream=None):
+        """One tensor multigrid cycle z = V r (device buffers of the plan's element type)."""
+        opts = tca_solve_opts(tmg_coarse_rtol=float(coarse_rtol), tmg_lambda_max=float(lambda_max),
+                              tmg_nu=int(nu), tmg_coarsen_mask=int(coarsen_mask))
+        _check(_lib.tca_tmg_apply(self._h, _ptr(r), _ptr(z), ctypes.byref(opts), _stream(stream)), "tca_tmg_apply")
+        return z
+
+    def tmg_info(self) -> dict:
+        """lambda_max of D^-1 K the multigrid smoother uses and the coarse CG iterations since the
+        last solve (or cycle) started."""
+        lam = ctypes.c_double(0.0)
+        its = ctypes.c_int64(0)
+        _check(_lib.tca_tmg_info(self._h, ctypes.byref(lam), ctypes.byref(its)), "tca_tmg_info")
+        return {"lambda_max": float(lam.value), "coarse_iters": int(its.value)}
 
 
 class ScatteredPlan(Plan):

@@ -65,6 +65,7 @@ def test_precond_names(tca):
     assert tca._precond_code(None) == tca.PRECOND_NONE
     assert tca._precond_code("separable") == tca.PRECOND_SEPARABLE
     assert tca._precond_code("jacobi") == tca.PRECOND_JACOBI
+    assert tca._precond_code("tmg") == tca.PRECOND_TMG
     with pytest.raises(ValueError):
         tca._precond_code("multigrid-typo")
 
@@ -103,6 +104,9 @@ def test_plan_rejects_bad_arguments_before_device_work(tca):
     assert tca._lib.tca_solve(None, None, None, None, None, None) == tca.ERR_INVALID_ARG
     shift = ctypes.c_double(0.0)
     assert tca._lib.tca_precond_default_shift(None, ctypes.byref(shift)) == tca.ERR_INVALID_ARG
+    opts = tca.tca_solve_opts()
+    assert tca._lib.tca_tmg_apply(None, None, None, ctypes.byref(opts), None) == tca.ERR_INVALID_ARG
+    assert tca._lib.tca_tmg_info(None, ctypes.byref(shift), None) == tca.ERR_INVALID_ARG
     # scattered plans: order, negative sample count, precision
     assert tca._lib.tca_plan_scattered(ctypes.byref(h), 2, n, 5, fac, ctypes.byref(reg), tca.F64,
                                        None) == tca.ERR_INVALID_ARG
