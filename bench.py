@@ -19,6 +19,8 @@ the solve's stream (one graph pass per launch, the host reading the events).
   separable_pcg_s16 / _s32  the separable tensor-inverse preconditioner;
   separable_banded_pcg_*    the same with 7-band truncated factors (one fused sweep),
                             at s = 16, 32 and at the plan's corner-model default;
+  tmg_pcg                   the two-grid tensor multigrid cycle (Sec. 4.2, Fig. 3),
+                            every default, with its coarse CG steps and lambda_max;
   jacobi_pcg                point Jacobi, M = diag(K);
   bf16_ir                   the bfloat16 mixed-precision form (tensor-core sweep,
                             double-float refinement), autotuned, with its sweep's
