@@ -173,15 +173,21 @@ def run_case(args, local):
                           "rel_res_true": info["rel_res_true"], "shift": plan_t.precond_default_shift()}), flush=True)
         return
     if args.case == "tmg":
-        # Solves of the bench workload preconditioned by the two-grid tensor multigrid cycle
-        # (every default), timed with CUDA events on the solve's stream.
+        # Solves of the bench workload preconditioned by the two-grid tensor multigrid cycle,
+        # timed with CUDA events on the solve's stream: every default, then more smoothing
+        # steps and a looser coarse solve.
         inst_t, plan_t, b = make_problem(shape, SEED, device)
         xz = torch.zeros(shape, dtype=torch.float32, device=device)
-        ms, info = timed_solve(plan_t, b, xz, max(1, args.steps), torch.cuda.current_stream(), precond="tmg")
-        st_t = plan_t.tmg_info()
-        print(json.dumps({"case": args.case, "ms": round(ms, 3), "cg_iters": info["iters"],
-                          "rel_res_true": info["rel_res_true"], "coarse_cg_iters": st_t["coarse_iters"],
-                          "lambda_max": st_t["lambda_max"]}), flush=True)
+        for nu, crt in ((0, 0.0), (3, 0.0), (2, 0.3), (3, 0.3)):
+            ms, info = timed_solve(plan_t, b, xz, max(1, args.steps), torch.cuda.current_stream(), precond="tmg",
+                                   tmg_nu=nu, tmg_coarse_rtol=crt)
+            st_t = plan_t.tmg_info()
+            print(json.dumps({"case": args.case, "nu": nu or 2, "coarse_rtol": crt or 0.1, "ms": round(ms, 3),
+                              "cg_iters": info["iters"], "rel_res_true": info["rel_res_true"],
+                              "coarse_cg_iters": st_t["coarse_iters"], "lambda_max": st_t["lambda_max"]}),
+                  flush=True)
+            if args.steps <= 1:
+                break
         return
     if args.case == "cgsweep":
         # A few CG iterations on random data: the CG-mode fused sweep in its solve context.
