@@ -203,12 +203,12 @@ typedef struct {
                            factors (32 for the B-spline workload at lambda = 1e-3, 128 at 1e-4,
                            8 at 1e-2). */
   /* TCA_PRECOND_TMG (the tensor multigrid cycle below); zero selects each default. */
-  double tmg_coarse_rtol;   /* relative tolerance ||r_c|| / ||b_c|| of the coarse CG (0: 0.1) */
+  double tmg_coarse_rtol;   /* relative tolerance ||r_c|| / ||b_c|| of the coarse CG (0: 0.3) */
   double tmg_lambda_max;    /* largest eigenvalue of D^-1 K, D = diag(K), for the Chebyshev
                                smoother (0: estimated on the device by 60 power steps from a
                                fixed pseudo-random start, once per plan) */
   int32_t tmg_nu;           /* Chebyshev smoothing steps before and after the coarse correction
-                               (0: 2; a negative value: none, the bare coarse-grid correction) */
+                               (0: 3; a negative value: none, the bare coarse-grid correction) */
   int32_t tmg_coarsen_mask; /* bit k set: mode k is coarsened by 2 (0: every mode with n_k >= 16) */
 } tca_solve_opts;
 

@@ -33,8 +33,8 @@ constexpr int kTmgThreads = 256;
 constexpr int kPowerSteps = 60;         // power steps of the lambda_max estimate
 constexpr int kMaxCoarseIters = 2000;   // cap on the coarse CG of one cycle
 constexpr int kMaxNu = 64;
-constexpr double kDefaultCoarseRtol = 0.1;
-constexpr int kDefaultNu = 2;
+constexpr double kDefaultCoarseRtol = 0.3;
+constexpr int kDefaultNu = 3;
 constexpr int64_t kCoarsenMin = 16;     // default mask: modes at least this long
 
 struct TmgState {

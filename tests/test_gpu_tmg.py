@@ -5,7 +5,7 @@ One cycle z = V r through ``tca_tmg_apply`` is compared element by element with
 Chebyshev interval (lambda_max of D^-1 K from power steps of the oracle's own operator,
 passed to both sides); then the preconditioned CG iterate by iterate against ``oracle.pcg``
 driven by that cycle, and a solve with every default (the library's own lambda_max estimate,
-coarse tolerance 0.1) against the oracle's verdict on its residual.
+coarse tolerance 0.3) against the oracle's verdict on its residual.
 
 Tolerances.  FP64 plans: both sides solve the coarse system to 1e-13, so their cycles differ
 by at most that residual times cond(K_c) (555 for the (9, 8, 7, 4) case): 1e-8.  FP32 plans:
@@ -113,8 +113,8 @@ def test_tmg_pcg_partial_iterates_match_oracle(kind, shape, mask):
 
 
 def test_tmg_solve_meets_tolerance_in_fewer_iterations():
-    """FP32 plan, every default (modes of at least 16 points coarsened, two smoothing steps, the
-    library's own lambda_max estimate, coarse tolerance 0.1): the solve meets a true relative
+    """FP32 plan, every default (modes of at least 16 points coarsened, three smoothing steps, the
+    library's own lambda_max estimate, coarse tolerance 0.3): the solve meets a true relative
     residual of 1e-6 by the oracle's verdict in under half the plain CG's iterations (the TMA halo
     path of the fused sweep: n2, n3 >= 22), and the estimate lies within 5 % of the oracle's."""
     tca = lib()
