@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--rhs-per-instance", type=int, default=20, help="learned case: right-hand sides per instance")
     ap.add_argument("--epochs", type=float, default=2.0, help="learned case: passes over the training pairs")
     ap.add_argument("--case", default=None, choices=["normal", "gram", "collocation", "cgsweep", "bf16sweep", "dense", "batched", "learned",
-                             "netfwd", "scattered", "pcg", "tmg"],
+                             "netfwd", "scattered", "pcg", "tmg", "shear"],
                     help="time one sweep kernel alone on the full-size tensors (profiling runs; no bench line)")
     return ap.parse_args()
 
@@ -171,6 +171,32 @@ def run_case(args, local):
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "status": int(st), "cg_iters": info["iters"],
                           "rel_res_true": info["rel_res_true"], "shift": plan_t.precond_default_shift()}), flush=True)
+        return
+    if args.case == "shear":
+        # Shears of the 160^3 x 8 volume (FP32), each kernel alone (inputs larger than L2): along
+        # mode 1 driven by mode 2 (linear and cubic), along mode 2 driven by mode 1, and along the
+        # fastest mode driven by mode 1 (slope tan 15 degrees about the centre of mode 2).
+        xs = torch.randn(shape, dtype=torch.float32, device=device)
+        ys = torch.empty_like(xs)
+        N = xs.numel()
+        c = (shape[1] - 1) / 2.0
+        for (ma, mb), kind in (((0, 1), "linear"), ((0, 1), "cubic"), ((1, 0), "cubic"), ((3, 0), "cubic")):
+            for _ in range(3):
+                tca.apply_shear(xs, ys, ma, mb, 0.2679, c, kind=kind)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(5, args.steps)
+            e0.record()
+            for _ in range(reps):
+                tca.apply_shear(xs, ys, ma, mb, 0.2679, c, kind=kind)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = 8 * N / ms / 1e6
+            peaks, _ = measured_peaks()
+            print(json.dumps({"case": "shear", "modes": [ma, mb], "kind": kind, "ms": round(ms, 5),
+                              "gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4)}),
+                  flush=True)
         return
     if args.case == "tmg":
         # Solves of the bench workload preconditioned by the two-grid tensor multigrid cycle,

@@ -273,6 +273,28 @@ typedef struct {
   int32_t reserved;
 } tca_solve_info;
 
+/* One-dimensional shear transform (Table 1: rotation as a product of 1D shear
+ * transforms).  Every line along mode_a is resampled at positions moved in
+ * proportion to the index along mode_b:
+ *   y[.., i_a, .., i_b, ..] = sum_j h(i_a - slope (i_b - center) - j) x[.., j, .., i_b, ..]
+ * with j over the line's dims[mode_a] points (nothing is read outside them;
+ * points whose taps all fall outside come out 0) and h the interpolation kernel:
+ * TCA_SHEAR_LINEAR the hat max(0, 1 - |u|) (2 taps), TCA_SHEAR_CUBIC cubic
+ * convolution with a = -1/2 (4 taps; reproduces quadratics; the paper names no
+ * interpolation).  Three shears with slopes tan(t/2) (mode a by mode b),
+ * -sin(t) (b by a), tan(t/2) (a by b) about the plane's centre sample x at
+ * c + R(t)(i - c), R(t) the rotation by t.  x, y: device buffers of dims
+ * (C order, order 2 to 4), float for TCA_F32 and double for TCA_F64, not
+ * aliased.  TCA_ERR_INVALID_ARG for null or host pointers, x == y, an order
+ * or mode out of range, mode_a == mode_b, another kind or precision or a slope
+ * or centre that is not finite; TCA_ERR_SHAPE for a non-positive size;
+ * TCA_ERR_UNSUPPORTED for dims[mode_b] > 65535, dims[mode_a] >= 2^30 or more
+ * than 2^40 elements.  Asynchronous on the stream. */
+typedef enum { TCA_SHEAR_LINEAR = 1, TCA_SHEAR_CUBIC = 3 } tca_shear_kind;
+TCA_API tca_status tca_apply_shear(int order, const int64_t* dims, int mode_a, int mode_b, double slope,
+                                   double center, int kind, tca_precision prec, const void* x, void* y,
+                                   cudaStream_t stream);
+
 /* Solve (A^T A + lambda R) x = A^T b by the tensor CG of Sec. 4.1, Fig. 2:
  * R = B - A.C, P = R, rho = <R,R>; repeat Q = A.P, alpha = rho/<P,Q>,
  * C += alpha P, R -= alpha Q, rho1 = <R,R>, P = R + (rho1/rho) P.  The

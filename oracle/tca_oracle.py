@@ -52,6 +52,10 @@ Structured Problems with Computational Tensor Algebra"):
   preconditioner (Sec. 4.2, Fig. 3): separable linear-interpolation transfers (Table 1
   upsampling and its transpose), Galerkin coarse operator, Chebyshev smoothing on the
   Jacobi-scaled operator (the smoother is a reading: the paper names none).
+* ``shear_kernel`` / ``shear`` - the one-dimensional shear transform of Table 1's rotation
+  row: every line along one mode resampled at positions moved in proportion to the index of
+  another mode, by linear interpolation or cubic convolution (the interpolation is a reading:
+  the paper names none).
 * ``kron_matrix`` / ``dense_normal_matrix`` / ``direct_solve`` - the
   equivalent matrix form of a tensor equation "with proper reshaping" (Sec. 3,
   after Eq. TensorEq), solved by a direct (Cholesky) method - the direct-solver
@@ -97,6 +101,8 @@ __all__ = [
     "corner_model_shift",
     "tmg_prolongation",
     "tmg_vcycle",
+    "shear_kernel",
+    "shear",
 ]
 
 
@@ -485,6 +491,45 @@ def tmg_vcycle(r: np.ndarray, kop, diag: np.ndarray, prolongs, nu: int, lam_lo: 
     zc = cg(lambda v: apply_T(kop(apply(v, prolongs)), prolongs), rc, rtol=coarse_rtol, max_iter=100000).x
     z = z + apply(zc, prolongs)
     return smooth(z) if nu > 0 else z
+
+
+def shear_kernel(u, kind: int) -> np.ndarray:
+    """Interpolation kernel h(u) of a one-dimensional shear transform: kind 1 the linear (hat)
+    kernel max(0, 1 - |u|); kind 3 cubic convolution with a = -1/2 (Keys 1981):
+    (a + 2)|u|^3 - (a + 3)|u|^2 + 1 on |u| <= 1, a|u|^3 - 5a|u|^2 + 8a|u| - 4a on 1 < |u| < 2,
+    0 beyond.  Both are interpolating: h(0) = 1 and h vanishes at the other integers."""
+    u = np.abs(np.asarray(u, dtype=np.float64))
+    if kind == 1:
+        return np.maximum(0.0, 1.0 - u)
+    if kind == 3:
+        a = -0.5
+        near = (a + 2.0) * u**3 - (a + 3.0) * u**2 + 1.0
+        far = a * u**3 - 5.0 * a * u**2 + 8.0 * a * u - 4.0 * a
+        return np.where(u <= 1.0, near, np.where(u < 2.0, far, 0.0))
+    raise ValueError("kind must be 1 (linear) or 3 (cubic convolution)")
+
+
+def shear(x: np.ndarray, mode_a: int, mode_b: int, slope: float, center: float, kind: int = 1) -> np.ndarray:
+    """One-dimensional shear transform along mode a driven by mode b (Table 1: rotation as a
+    product of 1D shear transforms).  Each line along mode a is resampled at positions moved by
+    slope * (i_b - center):
+
+        Y[.., i_a, .., i_b, ..] = sum_j h(i_a - slope * (i_b - center) - j) X[.., j, .., i_b, ..]
+
+    with j over the line's n_a points (nothing outside them) and h = ``shear_kernel``.  Written
+    as one explicit n_a x n_a matrix per value of i_b."""
+    x = np.asarray(x, dtype=np.float64)
+    if mode_a == mode_b:
+        raise ValueError("a shear needs two different modes")
+    xm = np.moveaxis(x, (mode_a, mode_b), (0, 1))
+    n_a, n_b = xm.shape[0], xm.shape[1]
+    y = np.zeros_like(xm)
+    idx = np.arange(n_a, dtype=np.float64)
+    for ib in range(n_b):
+        pos = idx - slope * (ib - center)
+        h = shear_kernel(pos[:, None] - idx[None, :], kind)
+        y[:, ib] = np.tensordot(h, xm[:, ib], axes=(1, 0))
+    return np.moveaxis(y, (0, 1), (mode_a, mode_b))
 
 
 def kron_matrix(mats) -> np.ndarray:

@@ -116,6 +116,9 @@ _lib.tca_autotuned_rows.argtypes = [_vp]
 _lib.tca_autotuned_rows.restype = ctypes.c_int
 _lib.tca_precond_default_shift.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
 _lib.tca_precond_default_shift.restype = ctypes.c_int
+_lib.tca_apply_shear.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+_lib.tca_apply_shear.restype = ctypes.c_int
 _lib.tca_tmg_apply.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), _vp]
 _lib.tca_tmg_apply.restype = ctypes.c_int
 _lib.tca_tmg_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _i64p]
@@ -277,9 +280,31 @@ def vec_dot(a, b, out, stream=None):
     return out
 
 
+SHEAR_KINDS = {"linear": 1, "cubic": 3}
+
+
+def apply_shear(x, y, mode_a: int, mode_b: int, slope: float, center: float, kind="linear", stream=None):
+    """y = the 1D shear transform of x along mode_a driven by mode_b (tca_apply_shear): every line
+    along mode_a resampled at i_a - slope (i_b - center), linear or cubic-convolution kernel.
+    x, y: contiguous CUDA tensors of one shape, both float32 or both float64."""
+    if tuple(x.shape) != tuple(y.shape) or x.dtype != y.dtype:
+        raise ValueError("x and y must have the same shape and dtype")
+    if not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous")
+    name = str(x.dtype)
+    if name not in ("torch.float32", "torch.float64"):
+        raise ValueError("float32 or float64 tensors")
+    prec = F64 if name == "torch.float64" else F32
+    dims = (ctypes.c_int64 * x.dim())(*[int(v) for v in x.shape])
+    code = SHEAR_KINDS.get(kind, kind)
+    _check(_lib.tca_apply_shear(x.dim(), dims, int(mode_a), int(mode_b), float(slope), float(center), int(code), prec,
+                                _ptr(x), _ptr(y), _stream(stream)), "tca_apply_shear")
+    return y
+
+
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_plan_scattered", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_tmg_apply", "tca_tmg_info", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_tmg_apply", "tca_tmg_info", "tca_apply_shear", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",

@@ -107,6 +107,20 @@ def test_plan_rejects_bad_arguments_before_device_work(tca):
     opts = tca.tca_solve_opts()
     assert tca._lib.tca_tmg_apply(None, None, None, ctypes.byref(opts), None) == tca.ERR_INVALID_ARG
     assert tca._lib.tca_tmg_info(None, ctypes.byref(shift), None) == tca.ERR_INVALID_ARG
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    bad = ctypes.c_void_p(16)
+    other = ctypes.c_void_p(32)
+    shear = tca._lib.tca_apply_shear
+    assert shear(3, dims, 0, 1, 0.5, 2.0, 1, tca.F32, None, other, None) == tca.ERR_INVALID_ARG
+    assert shear(3, dims, 0, 1, 0.5, 2.0, 1, tca.F32, bad, bad, None) == tca.ERR_INVALID_ARG    # aliased
+    assert shear(1, dims, 0, 1, 0.5, 2.0, 1, tca.F32, bad, other, None) == tca.ERR_INVALID_ARG  # order
+    assert shear(3, dims, 1, 1, 0.5, 2.0, 1, tca.F32, bad, other, None) == tca.ERR_INVALID_ARG  # same mode
+    assert shear(3, dims, 0, 3, 0.5, 2.0, 1, tca.F32, bad, other, None) == tca.ERR_INVALID_ARG  # mode range
+    assert shear(3, dims, 0, 1, 0.5, 2.0, 2, tca.F32, bad, other, None) == tca.ERR_INVALID_ARG  # kind
+    assert shear(3, dims, 0, 1, float("nan"), 2.0, 1, tca.F32, bad, other, None) == tca.ERR_INVALID_ARG
+    assert shear(3, dims, 0, 1, 0.5, 2.0, 1, tca.BF16_IR, bad, other, None) == tca.ERR_INVALID_ARG
+    zero = (ctypes.c_int64 * 3)(4, 0, 6)
+    assert shear(3, zero, 0, 1, 0.5, 2.0, 1, tca.F32, bad, other, None) == tca.ERR_SHAPE
     # scattered plans: order, negative sample count, precision
     assert tca._lib.tca_plan_scattered(ctypes.byref(h), 2, n, 5, fac, ctypes.byref(reg), tca.F64,
                                        None) == tca.ERR_INVALID_ARG

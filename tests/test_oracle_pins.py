@@ -650,3 +650,70 @@ def test_corner_model_shift_is_near_the_best_shift(kind, lam):
     s_model = O.corner_model_shift(mats, lam)
     best = min(_pcg_iters(mats, lam, 2.0 ** j, rhs) for j in range(9))
     assert _pcg_iters(mats, lam, s_model, rhs) <= best + 2
+
+
+# ---- one-dimensional shear transforms (Table 1 rotation) ------------------------------
+
+@pytest.mark.parametrize("kind", [1, 3])
+def test_shear_by_integer_steps_moves_lines_exactly(kind):
+    """Slope 1 about an integer centre moves line i_b by i_b - centre whole points: an exact shift
+    with zeros entering (both kernels interpolate: h(0) = 1, h = 0 at the other integers)."""
+    x = np.random.default_rng(50).standard_normal((7, 6, 3))
+    y = O.shear(x, 0, 1, slope=1.0, center=2.0, kind=kind)
+    ref = np.zeros_like(x)
+    for ib in range(6):
+        k = ib - 2
+        for ia in range(7):
+            if 0 <= ia - k < 7:
+                ref[ia, ib] = x[ia - k, ib]
+    np.testing.assert_allclose(y, ref, atol=1e-15)
+
+
+def test_shear_reproduces_low_order_polynomials_inside():
+    """Linear interpolation reproduces linear lines and cubic convolution (a = -1/2) quadratic ones
+    exactly wherever every tap lies on the line; the resampling point is i_a - slope (i_b - c)."""
+    n_a, n_b, slope, c = 24, 5, 0.37, 1.5
+    ia = np.arange(n_a, dtype=np.float64)
+    for kind, f, reach in ((1, lambda p: 2.0 * p + 1.0, 1), (3, lambda p: 0.5 * p * p - p + 3.0, 2)):
+        x = np.stack([f(ia)] * n_b, axis=1)
+        y = O.shear(x, 0, 1, slope=slope, center=c, kind=kind)
+        for ib in range(n_b):
+            pos = ia - slope * (ib - c)
+            inside = (np.floor(pos) - (reach - 1) >= 0) & (np.floor(pos) + reach <= n_a - 1)
+            np.testing.assert_allclose(y[inside, ib], f(pos[inside]), rtol=1e-12, atol=1e-12)
+
+
+def test_three_shears_rotate_a_linear_image():
+    """Shears with slopes tan(t/2) (mode 0 by mode 1), -sin t (mode 1 by mode 0), tan(t/2) (mode 0
+    by mode 1), each about the centre, compose to sampling at c + R(t)(i - c) with R the rotation
+    by t: exact for a linear image (linear interpolation) near the centre, where no tap leaves the
+    grid in any of the three passes."""
+    n, t = 41, np.deg2rad(30.0)
+    c = (n - 1) / 2.0
+    g = np.arange(n, dtype=np.float64)
+    xx, yy = np.meshgrid(g, g, indexing="ij")
+    f = lambda u, v: 0.7 * u - 1.3 * v + 4.0
+    img = f(xx, yy)
+    out = O.shear(img, 0, 1, np.tan(t / 2), c, kind=1)
+    out = O.shear(out, 1, 0, -np.sin(t), c, kind=1)
+    out = O.shear(out, 0, 1, np.tan(t / 2), c, kind=1)
+    u = c + np.cos(t) * (xx - c) - np.sin(t) * (yy - c)
+    v = c + np.sin(t) * (xx - c) + np.cos(t) * (yy - c)
+    near = (xx - c) ** 2 + (yy - c) ** 2 <= 6.0 ** 2
+    np.testing.assert_allclose(out[near], f(u, v)[near], rtol=1e-12, atol=1e-11)
+
+
+@pytest.mark.parametrize("kind", [1, 3])
+def test_three_shears_by_ninety_degrees_permute_exactly(kind):
+    """At t = 90 degrees the slopes are 1, -1, 1 and every shift is whole: the three passes move
+    point (i, j) to (2c - j, i) exactly near the centre, for either kernel."""
+    n = 41
+    c = (n - 1) // 2
+    x = np.random.default_rng(51).standard_normal((n, n))
+    out = O.shear(x, 0, 1, 1.0, c, kind=kind)
+    out = O.shear(out, 1, 0, -1.0, c, kind=kind)
+    out = O.shear(out, 0, 1, 1.0, c, kind=kind)
+    for i in range(c - 4, c + 5):
+        for j in range(c - 4, c + 5):
+            if (i - c) ** 2 + (j - c) ** 2 <= 16:
+                assert out[i, j] == x[2 * c - j, i]
