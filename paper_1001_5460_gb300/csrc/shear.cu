@@ -13,7 +13,8 @@
 // Layout: the grid's y dimension is i_b; each block forms the shift of its
 // lines once (FP64 position, its integer part and the tap weights from the
 // fraction) and then streams the elements with that i_b in storage order
-// (32-bit index arithmetic below 2^31 elements).  HBM-bound: each element is
+// (32-bit index arithmetic below 2^31 elements), 16-byte vectors along the
+// fastest mode where it is neither of the two.  HBM-bound: each element is
 // read up to four times from nearby addresses (L1/L2) and written once.
 #include <algorithm>
 #include <cmath>
@@ -43,7 +44,16 @@ struct ShearGeom {
   I per_b;          // elements with one value of i_b: N / n_b
 };
 
-template <typename T, typename I>
+// 16-byte vectors along the fastest mode (float4 / double2).
+template <typename T> struct ShearVec;
+template <> struct ShearVec<float> { using t = float4; static constexpr int n = 4; };
+template <> struct ShearVec<double> { using t = double2; static constexpr int n = 2; };
+
+// VEC: neither mode a nor mode b is the fastest mode, whose length is a
+// multiple of the vector width, and x, y are 16-byte aligned: the VN
+// consecutive outputs along the fastest mode share i_a, i_b and the taps, so
+// one thread forms them from VN-wide loads of the same taps.
+template <typename T, typename I, bool VEC>
 __global__ void __launch_bounds__(kShearThreads) shear_kernel(const T* __restrict__ x, T* __restrict__ y,
                                                               ShearGeom<I> g, double slope, double center, int kind) {
   __shared__ int s_k0;
@@ -65,18 +75,40 @@ __global__ void __launch_bounds__(kShearThreads) shear_kernel(const T* __restric
   T w[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) w[m] = s_w[m];
-  for (I e = (I)(blockIdx.x * blockDim.x + threadIdx.x); e < g.per_b; e += (I)(gridDim.x * blockDim.x)) {
+  constexpr int VN = VEC ? ShearVec<T>::n : 1;
+  using VT = typename ShearVec<T>::t;
+  const I groups = g.per_b / (I)VN;
+  for (I e4 = (I)(blockIdx.x * blockDim.x + threadIdx.x); e4 < groups; e4 += (I)(gridDim.x * blockDim.x)) {
+    const I e = e4 * (I)VN;
     const I outer = e / g.inner_b, r = e - outer * g.inner_b;
     const I gi = (outer * g.n_b + ib) * g.inner_b + r;
     const I ia = (gi / g.stride_a) % g.n_a;
     const I base = gi - ia * g.stride_a;
-    T acc = T(0);
+    if constexpr (VEC) {
+      VT acc;
+      T* as = reinterpret_cast<T*>(&acc);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const long long j = (long long)ia + k0 + (m - 1);
-      if (w[m] != T(0) && j >= 0 && j < (long long)g.n_a) acc += w[m] * x[base + (I)j * g.stride_a];
+      for (int c = 0; c < VN; ++c) as[c] = T(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const long long j = (long long)ia + k0 + (m - 1);
+        if (w[m] != T(0) && j >= 0 && j < (long long)g.n_a) {
+          const VT v = reinterpret_cast<const VT*>(x)[(base + (I)j * g.stride_a) / (I)VN];
+          const T* vs = reinterpret_cast<const T*>(&v);
+#pragma unroll
+          for (int c = 0; c < VN; ++c) as[c] += w[m] * vs[c];
+        }
+      }
+      reinterpret_cast<VT*>(y)[gi / (I)VN] = acc;
+    } else {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const long long j = (long long)ia + k0 + (m - 1);
+        if (w[m] != T(0) && j >= 0 && j < (long long)g.n_a) acc += w[m] * x[base + (I)j * g.stride_a];
+      }
+      y[gi] = acc;
     }
-    y[gi] = acc;
   }
 }
 
@@ -97,10 +129,16 @@ tca_status launch_shear_as(const int64_t* dims, int order, int mode_a, int mode_
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // About eight resident blocks per SM over all lines, at least one per line.
-  const int64_t want_x = (N / dims[mode_b] + kShearThreads - 1) / kShearThreads;
+  const int last = order - 1;
+  constexpr int VW = ShearVec<T>::n;
+  const bool vec = mode_a != last && mode_b != last && dims[last] % VW == 0 && (uintptr_t)x % 16 == 0 &&
+                   (uintptr_t)y % 16 == 0;
+  const int64_t per_thread = vec ? VW : 1;
+  const int64_t want_x = (N / dims[mode_b] / per_thread + kShearThreads - 1) / kShearThreads;
   const int64_t cap_x = std::max<int64_t>(1, (int64_t)sms * 8 / dims[mode_b] + 1);
   const dim3 grid((unsigned)std::min(want_x, cap_x), (unsigned)dims[mode_b]);
-  shear_kernel<T, I><<<grid, kShearThreads, 0, s>>>(x, y, g, slope, center, kind);
+  if (vec) shear_kernel<T, I, true><<<grid, kShearThreads, 0, s>>>(x, y, g, slope, center, kind);
+  else shear_kernel<T, I, false><<<grid, kShearThreads, 0, s>>>(x, y, g, slope, center, kind);
   TCA_LAUNCH_CHECK();
   return TCA_OK;
 }

@@ -24,7 +24,9 @@ CASES = [
     ((7, 8, 5, 6), 1, 3, 0.5, 0.0),
     ((7, 8, 5, 6), 3, 1, 2.75, 3.0),     # shifts past the line's end for most i_b
     ((5, 1, 9), 1, 2, 0.3, 4.0),         # lines of one point
-    ((12, 10, 8, 4), 2, 1, -0.125, 4.5),
+    ((12, 10, 8, 4), 2, 1, -0.125, 4.5),  # 16-byte vectors along the fastest mode
+    ((6, 9, 12), 0, 1, 0.6, 3.0),
+    ((10, 7, 5, 8), 1, 0, -0.45, 2.0),
 ]
 
 
