@@ -295,6 +295,25 @@ TCA_API tca_status tca_apply_shear(int order, const int64_t* dims, int mode_a, i
                                    double center, int kind, tca_precision prec, const void* x, void* y,
                                    cudaStream_t stream);
 
+/* Discrete Fourier transform over the modes set in mode_mask (Table 1: F = E G H C
+ * with one-dimensional DFT transforms) of the complex tensor re_in + i im_in,
+ * as the separable transformation itself: along each selected mode k the data
+ * are multiplied by F_k[j][i] = exp(-2 pi i j i / n_k) (inverse != 0:
+ * exp(+2 pi i j i / n_k) / n_k, so that the inverse undoes the forward), four
+ * real dense mode products per mode (O(n_k) work per output; this is the
+ * definition, not an FFT).  re_in, im_in (NULL: a real input), re_out, im_out:
+ * device buffers of dims (C order, order 1 to 4), float for TCA_F32 and double
+ * for TCA_F64; no output may alias an input or the other output.  Builds two
+ * plans of dense factors per call and about three n-shaped scratch tensors, and
+ * synchronises the stream.  TCA_ERR_INVALID_ARG for null or host pointers,
+ * aliasing, an empty mask or one naming a mode past order, another precision;
+ * TCA_ERR_SHAPE for a non-positive size; TCA_ERR_UNSUPPORTED for a transformed
+ * mode longer than 256, another mode longer than 2^24 or more than 2^40
+ * elements, and where the dense mode product takes no such shape. */
+TCA_API tca_status tca_apply_dft(int order, const int64_t* dims, uint32_t mode_mask, int inverse,
+                                 tca_precision prec, const void* re_in, const void* im_in, void* re_out,
+                                 void* im_out, cudaStream_t stream);
+
 /* Solve (A^T A + lambda R) x = A^T b by the tensor CG of Sec. 4.1, Fig. 2:
  * R = B - A.C, P = R, rho = <R,R>; repeat Q = A.P, alpha = rho/<P,Q>,
  * C += alpha P, R -= alpha Q, rho1 = <R,R>, P = R + (rho1/rho) P.  The

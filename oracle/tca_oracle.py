@@ -56,6 +56,8 @@ Structured Problems with Computational Tensor Algebra"):
   row: every line along one mode resampled at positions moved in proportion to the index of
   another mode, by linear interpolation or cubic convolution (the interpolation is a reading:
   the paper names none).
+* ``dft`` - the discrete Fourier transform of Table 1 over several modes: the complex
+  tensor multiplied along each mode by its DFT matrix (the definition, not an FFT).
 * ``kron_matrix`` / ``dense_normal_matrix`` / ``direct_solve`` - the
   equivalent matrix form of a tensor equation "with proper reshaping" (Sec. 3,
   after Eq. TensorEq), solved by a direct (Cholesky) method - the direct-solver
@@ -103,6 +105,7 @@ __all__ = [
     "tmg_vcycle",
     "shear_kernel",
     "shear",
+    "dft",
 ]
 
 
@@ -530,6 +533,23 @@ def shear(x: np.ndarray, mode_a: int, mode_b: int, slope: float, center: float, 
         h = shear_kernel(pos[:, None] - idx[None, :], kind)
         y[:, ib] = np.tensordot(h, xm[:, ib], axes=(1, 0))
     return np.moveaxis(y, (0, 1), (mode_a, mode_b))
+
+
+def dft(re: np.ndarray, im: np.ndarray | None, modes, inverse: bool = False):
+    """Discrete Fourier transform over the given modes as a separable transformation (Table 1:
+    F = E G H C with one-dimensional DFT transforms): the complex tensor re + i im multiplied along
+    each listed mode k by the n_k x n_k matrix F_k[j, i] = exp(-2 pi i j i / n_k) (inverse:
+    exp(+2 pi i j i / n_k) / n_k).  Returns the real and imaginary parts."""
+    z = np.asarray(re, dtype=np.float64) + (0.0 if im is None else 1j * np.asarray(im, dtype=np.float64))
+    z = z.astype(np.complex128)
+    for k in modes:
+        n = z.shape[k]
+        jk = np.outer(np.arange(n), np.arange(n))
+        f = np.exp((2j if inverse else -2j) * np.pi * jk / n)
+        if inverse:
+            f = f / n
+        z = np.moveaxis(np.tensordot(f, np.moveaxis(z, k, 0), axes=(1, 0)), 0, k)
+    return z.real.copy(), z.imag.copy()
 
 
 def kron_matrix(mats) -> np.ndarray:

@@ -119,6 +119,9 @@ _lib.tca_precond_default_shift.restype = ctypes.c_int
 _lib.tca_apply_shear.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
 _lib.tca_apply_shear.restype = ctypes.c_int
+_lib.tca_apply_dft.argtypes = [ctypes.c_int, _i64p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                               _vp]
+_lib.tca_apply_dft.restype = ctypes.c_int
 _lib.tca_tmg_apply.argtypes = [_vp, _vp, _vp, ctypes.POINTER(tca_solve_opts), _vp]
 _lib.tca_tmg_apply.restype = ctypes.c_int
 _lib.tca_tmg_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _i64p]
@@ -302,9 +305,29 @@ def apply_shear(x, y, mode_a: int, mode_b: int, slope: float, center: float, kin
     return y
 
 
+def apply_dft(re, im, re_out, im_out, modes, inverse: bool = False, stream=None):
+    """(re_out, im_out) = the DFT of re + i im over ``modes`` (tca_apply_dft; im may be None for a
+    real input): contiguous CUDA tensors of one shape, all float32 or all float64."""
+    bufs = [t for t in (re, im, re_out, im_out) if t is not None]
+    if any(tuple(t.shape) != tuple(re.shape) or t.dtype != re.dtype or not t.is_contiguous() for t in bufs):
+        raise ValueError("re, im, re_out and im_out must be contiguous tensors of one shape and dtype")
+    name = str(re.dtype)
+    if name not in ("torch.float32", "torch.float64"):
+        raise ValueError("float32 or float64 tensors")
+    prec = F64 if name == "torch.float64" else F32
+    mask = 0
+    for k in modes:
+        mask |= 1 << int(k)
+    dims = (ctypes.c_int64 * re.dim())(*[int(v) for v in re.shape])
+    _check(_lib.tca_apply_dft(re.dim(), dims, mask, 1 if inverse else 0, prec, _ptr(re),
+                              None if im is None else _ptr(im), _ptr(re_out), _ptr(im_out), _stream(stream)),
+           "tca_apply_dft")
+    return re_out, im_out
+
+
 def exported_symbols() -> list[str]:
     return ["tca_plan", "tca_plan_scattered", "tca_apply", "tca_apply_T", "tca_apply_normal", "tca_apply_mode", "tca_solve",
-            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_tmg_apply", "tca_tmg_info", "tca_apply_shear", "tca_rel_residual_noalloc", "tca_destroy",
+            "tca_solve_batched", "tca_autotune_batched", "tca_autotune", "tca_autotuned_chunks", "tca_autotuned_rows", "tca_precond_default_shift", "tca_tmg_apply", "tca_tmg_info", "tca_apply_shear", "tca_apply_dft", "tca_rel_residual_noalloc", "tca_destroy",
             "tca_net_param_count", "tca_net_create", "tca_net_set_params", "tca_net_get_params", "tca_net_get_grads",
             "tca_net_forward", "tca_net_accumulate", "tca_net_take_loss", "tca_net_adam", "tca_solve_net",
             "tca_net_use_tensor_cores", "tca_net_destroy", "tca_check_timeout", "tca_wait_selftest",

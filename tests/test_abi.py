@@ -121,6 +121,16 @@ def test_plan_rejects_bad_arguments_before_device_work(tca):
     assert shear(3, dims, 0, 1, 0.5, 2.0, 1, tca.BF16_IR, bad, other, None) == tca.ERR_INVALID_ARG
     zero = (ctypes.c_int64 * 3)(4, 0, 6)
     assert shear(3, zero, 0, 1, 0.5, 2.0, 1, tca.F32, bad, other, None) == tca.ERR_SHAPE
+    dft = tca._lib.tca_apply_dft
+    third = ctypes.c_void_p(48)
+    fourth = ctypes.c_void_p(64)
+    assert dft(3, dims, 0b011, 0, tca.F32, None, None, other, third, None) == tca.ERR_INVALID_ARG
+    assert dft(3, dims, 0, 0, tca.F32, bad, None, other, third, None) == tca.ERR_INVALID_ARG       # empty mask
+    assert dft(3, dims, 0b1000, 0, tca.F32, bad, None, other, third, None) == tca.ERR_INVALID_ARG  # past order
+    assert dft(3, dims, 0b001, 0, tca.F32, bad, other, other, third, None) == tca.ERR_INVALID_ARG  # aliasing
+    assert dft(3, dims, 0b001, 0, tca.F32, bad, None, other, other, None) == tca.ERR_INVALID_ARG
+    assert dft(3, dims, 0b001, 0, tca.TF32_IR, bad, fourth, other, third, None) == tca.ERR_INVALID_ARG
+    assert dft(3, zero, 0b001, 0, tca.F32, bad, fourth, other, third, None) == tca.ERR_SHAPE
     # scattered plans: order, negative sample count, precision
     assert tca._lib.tca_plan_scattered(ctypes.byref(h), 2, n, 5, fac, ctypes.byref(reg), tca.F64,
                                        None) == tca.ERR_INVALID_ARG

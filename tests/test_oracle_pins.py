@@ -717,3 +717,23 @@ def test_three_shears_by_ninety_degrees_permute_exactly(kind):
         for j in range(c - 4, c + 5):
             if (i - c) ** 2 + (j - c) ** 2 <= 16:
                 assert out[i, j] == x[2 * c - j, i]
+
+
+# ---- discrete Fourier transform over several modes (Table 1) -----------------------------
+
+@pytest.mark.parametrize("modes", [(0,), (1, 2), (0, 1, 2, 3), (3, 1)])
+def test_dft_equals_numpy_fft(modes):
+    """The separable DFT (one DFT matrix per listed mode) equals numpy's FFT over those axes, for a
+    complex input and for a real one; the inverse equals numpy's ifftn and undoes the forward."""
+    rng = np.random.default_rng(70)
+    shape = (6, 5, 8, 3)
+    re, im = rng.standard_normal(shape), rng.standard_normal(shape)
+    fr, fi = O.dft(re, im, modes)
+    ref = np.fft.fftn(re + 1j * im, axes=modes)
+    np.testing.assert_allclose(fr + 1j * fi, ref, rtol=1e-12, atol=1e-12)
+    fr0, fi0 = O.dft(re, None, modes)
+    np.testing.assert_allclose(fr0 + 1j * fi0, np.fft.fftn(re, axes=modes), rtol=1e-12, atol=1e-12)
+    br, bi = O.dft(fr, fi, modes, inverse=True)
+    np.testing.assert_allclose(br + 1j * bi, np.fft.ifftn(fr + 1j * fi, axes=modes), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(br, re, atol=1e-12)
+    np.testing.assert_allclose(bi, im, atol=1e-12)
