@@ -737,3 +737,38 @@ def test_dft_equals_numpy_fft(modes):
     np.testing.assert_allclose(br + 1j * bi, np.fft.ifftn(fr + 1j * fi, axes=modes), rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(br, re, atol=1e-12)
     np.testing.assert_allclose(bi, im, atol=1e-12)
+
+
+def test_pin_catches_wrong_cubic_coefficient(monkeypatch):
+    """Cubic convolution with a = -3/4 instead of -1/2 no longer reproduces quadratics, so the
+    shear's reproduction pin would fail on it."""
+    n_a, slope, c = 24, 0.37, 1.5
+    ia = np.arange(n_a, dtype=np.float64)
+    x = np.stack([0.5 * ia * ia - ia + 3.0] * 3, axis=1)
+    pos = ia - slope * (2 - c)
+    inside = (np.floor(pos) - 1 >= 0) & (np.floor(pos) + 2 <= n_a - 1)
+    want = 0.5 * pos * pos - pos + 3.0
+    good = O.shear(x, 0, 1, slope, c, kind=3)[:, 2]
+    assert np.allclose(good[inside], want[inside], atol=1e-12)
+
+    def keys_wrong(u, kind):
+        u = np.abs(np.asarray(u, dtype=np.float64))
+        a = -0.75
+        near = (a + 2.0) * u**3 - (a + 3.0) * u**2 + 1.0
+        far = a * u**3 - 5.0 * a * u**2 + 8.0 * a * u - 4.0 * a
+        return np.where(u <= 1.0, near, np.where(u < 2.0, far, 0.0))
+
+    monkeypatch.setattr(O, "shear_kernel", keys_wrong)
+    bad = O.shear(x, 0, 1, slope, c, kind=3)[:, 2]
+    assert not np.allclose(bad[inside], want[inside], atol=1e-6)
+
+
+def test_pin_catches_conjugated_dft(monkeypatch):
+    """A DFT with the exponent's sign flipped (the conjugate transform) fails the numpy pin."""
+    rng = np.random.default_rng(71)
+    re, im = rng.standard_normal((5, 6)), rng.standard_normal((5, 6))
+    ref = np.fft.fftn(re + 1j * im, axes=(0, 1))
+    r, i = O.dft(re, im, (0, 1))
+    assert np.allclose(r + 1j * i, ref)
+    rb, ib = O.dft(re, im, (0, 1), inverse=True)  # the conjugate kernel, divided by n
+    assert not np.allclose((rb + 1j * ib) * re.size, ref)
