@@ -215,3 +215,31 @@ def test_noalloc_binding_rejects_bad_buffers_before_the_call(tca):
         tca.rel_residual_noalloc(good, FakeDev(8, device="cuda:1"), FakeDev(1))
     with pytest.raises(ValueError, match="contiguous"):
         tca.rel_residual_noalloc(good, FakeDev(8, contiguous=False), FakeDev(1))
+
+
+def test_shear_and_dft_bindings_check_buffers_in_python(tca):
+    """apply_shear and apply_dft refuse mismatched shapes, dtypes and non-contiguous buffers in
+    Python; host tensors that pass those checks are refused by the library (host memory) before
+    any device work."""
+    import torch
+
+    x = torch.zeros((4, 6), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        tca.apply_shear(x, torch.zeros((6, 4), dtype=torch.float32), 0, 1, 0.5, 2.0)
+    with pytest.raises(ValueError):
+        tca.apply_shear(x, torch.zeros((4, 6), dtype=torch.float64), 0, 1, 0.5, 2.0)
+    with pytest.raises(ValueError):
+        tca.apply_shear(x, torch.zeros((6, 4), dtype=torch.float32).t(), 0, 1, 0.5, 2.0)
+    with pytest.raises(ValueError):
+        tca.apply_shear(x.to(torch.int32), torch.zeros((4, 6), dtype=torch.int32), 0, 1, 0.5, 2.0)
+    with pytest.raises(tca.TcaError) as e:
+        tca.apply_shear(x, torch.zeros((4, 6), dtype=torch.float32), 0, 1, 0.5, 2.0)
+    assert e.value.status == tca.ERR_INVALID_ARG
+    y, z = torch.zeros((4, 6)), torch.zeros((4, 6))
+    with pytest.raises(ValueError):
+        tca.apply_dft(x, None, y, torch.zeros((4, 7)), (0,))
+    with pytest.raises(ValueError):
+        tca.apply_dft(x, torch.zeros((4, 6), dtype=torch.float64), y, z, (0,))
+    with pytest.raises(tca.TcaError) as e:
+        tca.apply_dft(x, None, y, z, (0, 1))
+    assert e.value.status == tca.ERR_INVALID_ARG
