@@ -365,7 +365,8 @@ TCA_API tca_status tca_precond_default_shift(tca_plan_t plan, double* shift);
 TCA_API tca_status tca_tmg_apply(tca_plan_t plan, const void* r, void* z, const tca_solve_opts* opts,
                                  cudaStream_t stream);
 
-/* The tensor multigrid state of the plan: the lambda_max of D^-1 K its
+/* The tensor multigrid state of the plan (Sec. 4.2, Fig. 3; no counterpart in
+ * the paper, which reports no cycle statistics): the lambda_max of D^-1 K its
  * smoother uses (given or estimated; 0 before the first cycle) and the coarse
  * CG iterations run since the last tca_solve started (or since the last
  * tca_tmg_apply call).  Either pointer may be NULL. */
