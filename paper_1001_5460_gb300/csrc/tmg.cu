@@ -22,7 +22,6 @@
 // updates and inner products are the kernels below (FP64 reductions).
 #include <algorithm>
 #include <cmath>
-#include <cstdio>
 #include <vector>
 
 #include "tca_internal.cuh"
